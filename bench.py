@@ -1,0 +1,376 @@
+"""Benchmark of the state-vector hot path.
+
+One step = reset to |0...0>, the 32-qubit random U3 + CNOT brickwork of depth
+40 (seed 8091) applied through the C ABI, flush, P(q=1) for every qubit,
+<sum_i Z_i Z_{i+1}> and a full-register sample.  The default arm runs
+complex64 with greedy fusion into <=5-qubit blocks (the fast path); a bounded
+sample of the same circuit on the plain complex128 path (one launch per
+gate) is timed beside it.
+
+Printed: one JSON line (rank 0).  ``value`` is amplitude-updates/s over the
+whole job: sum over all gates of 2^(n - #controls), divided by the device
+time of the K timed steps (CUDA events on the library's stream, max over
+ranks).  ``e2e`` is the same metric on the host clock around the public API
+calls, including the host->device gate data and the device->host results.
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample of
+the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import circuitgen as cg  # noqa: E402
+
+METRIC = "amplitude-updates/s & HBM-roofline fraction, fused c64 vs plain c128, infid≤1e-5"
+UNIT = "amp-updates/s"
+SEED = 8091
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32)
+    ap.add_argument("--depth", type=int, default=40)
+    ap.add_argument("--precision", default="c64")
+    ap.add_argument("--fusion", default="greedy")
+    ap.add_argument("--kmax", type=int, default=5)
+    ap.add_argument("--plain-layers", type=int, default=2, help="layers of the plain c128 comparison sample")
+    ap.add_argument("--cpu-gates", type=int, default=6, help="gates of the oracle CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n, depth):
+    ops = cg.random_u3_brickwork(n, depth, SEED)
+    terms = cg.zz_chain_terms(n)
+    u = float(cg.uniform_draws(SEED + 1, 1)[0])
+    return ops, terms, u
+
+
+def amp_updates(ops, n):
+    return float(sum(1 << (n - len(o.controls)) for o in ops))
+
+
+def workload_name(n, depth):
+    return ("%d-qubit random circuit, depth %d: U3 on every qubit + CNOT brickwork per layer (seed %d); "
+            "then P(q=1) for all q, <sum Z_i Z_i+1>, measure-all" % (n, depth, SEED))
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: each rank runs its own register)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(n, ops, gates):
+    """Time the FP64 oracle on the first `gates` gates of the workload, after
+    one untimed gate that touches every page of the register."""
+    import oracle
+
+    oracle.build()
+    sim = oracle.OracleSim(n)
+    sim.apply_op(ops[0])
+    sample = ops[1:1 + gates]
+    t0 = time.perf_counter()
+    for o in sample:
+        sim.apply_op(o)
+    dt = time.perf_counter() - t0
+    upd = amp_updates(sample, n)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return upd / dt, dt, threads, len(sample)
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = args.n
+    ops, _, _ = workload(n, args.depth)
+    vals = []
+    t_all = []
+    steps_total = args.warmup + args.steps
+    import oracle
+
+    oracle.build()
+    sim = oracle.OracleSim(n)
+    sim.apply_op(ops[0])  # touch all pages once
+    g = max(1, args.cpu_gates // 2)
+    for s in range(steps_total):
+        sample = ops[1 + s * g: 1 + (s + 1) * g]
+        t0 = time.perf_counter()
+        for o in sample:
+            sim.apply_op(o)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            vals.append(amp_updates(sample, n) / dt)
+            t_all.append(dt)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    v = statistics.median(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(t_all),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": workload_name(n, args.depth), "n_qubits": n, "precision": "c128",
+                   "fusion": "none", "parallelism": "replicas"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d gates of the workload per step on the FP64 oracle, %d qubits" % (g, n)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    import paper_1612_08091_gb300 as q
+
+    q.load()
+    n = args.n
+    ops, terms, u = workload(n, args.depth)
+    upd_step = amp_updates(ops, n)
+    stream = torch.cuda.current_stream(device)
+    sim = q.Simulator(n, precision=args.precision, fusion=args.fusion, kmax=args.kmax, stream=stream)
+
+    h2d_bytes = sum(16 * (1 << (2 * len(o.targets))) + 4 * (len(o.targets) + len(o.controls)) for o in ops)
+    d2h_bytes = 8 * (n + 1) + 8 + 8 * 4096 + 32  # probabilities, expectation, measure-all sums and result
+
+    def step():
+        sim.reset(0)
+        sim.run(ops)
+        sim.flush()
+        p1, nrm = sim.probs_all()
+        e = sim.expect(terms)
+        j = sim.measure_all(u)
+        return p1, nrm, e, j
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sim.reset_stats()
+    sim.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    host_s = t1 - t0
+    kt = sim.kernel_times()
+    st = sim.stats()
+    sim.set_profiling(False)
+    dev_s = max_over_ranks(dev_s, world, device)
+    host_s = max_over_ranks(host_s, world, device)
+    total_upd = upd_step * args.steps * world
+    value = total_upd / dev_s
+    e2e = total_upd / host_s
+
+    peak, peak_kind = measured_peaks()
+    dom_name, dom = max(kt.items(), key=lambda kv: kv[1]["total_ms"]) if kt else (None, None)
+    roof = None
+    if dom:
+        per_launch_bytes = dom["alg_bytes"] / dom["launches"]
+        per_launch_s = dom["total_ms"] / dom["launches"] / 1e3
+        achieved = per_launch_bytes / per_launch_s / 1e9
+        step_ms_total = sum(v["total_ms"] for v in kt.values())
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind, "traffic": None, "kernel": dom_name,
+                "alg_bytes_per_launch": per_launch_bytes, "launches_per_step": dom["launches"] / args.steps,
+                "share_of_gate_time": dom["total_ms"] / step_ms_total if step_ms_total else None}
+
+    plain = None
+    if not args.no_plain and rank == 0 and args.plain_layers > 0:
+        sim.close()
+        torch.cuda.empty_cache()
+        # the first `plain_layers` layers of the same circuit
+        cnt = 0
+        for layer in range(args.plain_layers):
+            cnt += n + len(range(layer % 2, n - 1, 2))
+        sample = ops[:cnt]
+        with q.Simulator(n, precision="c128", fusion="none", stream=stream) as ps:
+            ps.run(sample[: n])  # warm-up on the same register
+            ps.flush()
+            torch.cuda.synchronize()
+            ps.set_profiling(True)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ps.run(sample)
+            ps.flush()
+            b.record(stream)
+            torch.cuda.synchronize()
+            pkt = ps.kernel_times()
+        ps_s = a.elapsed_time(b) / 1e3
+        plain = {"value": amp_updates(sample, n) / ps_s, "unit": UNIT, "precision": "c128", "fusion": "none",
+                 "sample": "first %d layers (%d gates) of the same %d-qubit circuit, one launch per gate"
+                           % (args.plain_layers, len(sample), n),
+                 "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
+                                 "GB/s": v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9} for k, v in pkt.items()}}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        v, dt, threads, g = oracle_sample(n, ops, args.cpu_gates)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d gates of the %d-qubit workload on the FP64 oracle (%.1f s)" % (g, n, dt)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "compute": ("bf16x3 tensor-core blocks, fp32 accumulate; fp64 reductions" if args.precision == "c64"
+                        else "fp64"),
+            "data": "synthetic",
+            "config": {"workload": workload_name(n, args.depth), "n_qubits": n, "depth": args.depth,
+                       "precision": args.precision, "fusion": args.fusion, "kmax": args.kmax,
+                       "gates_per_step": len(ops), "amp_updates_per_step": upd_step,
+                       "passes_per_step": st["passes"] / args.steps,
+                       "l2": "inputs larger than L2 (state %d GiB vs 126 MiB L2)" % ((8 if args.precision == 'c64'
+                                                                                    else 16) << (n - 30)),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof,
+            "kernel_times": kt,
+            "plain_c128": plain,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes},
+            "clocks": clk,
+            "gpu_launches": int(st["launches"]),
+            "check": {"norm2": results[-1][1], "zz": results[-1][2], "sample": results[-1][3]},
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * qsim.h -- C ABI of libqsim, a GB300 (sm_103a) dense state-vector simulator.
+ *
+ * The library applies quantum gates to a dense vector of 2^n complex
+ * amplitudes held in GPU memory, the operation the ProjectQ paper's
+ * high-performance simulator performs one gate at a time (arXiv:1612.08091,
+ * Sec. 4.3.2 "Simulation of quantum circuits").  Gates are queued lazily and
+ * executed on flush, optionally fused into dense k-qubit blocks (the "lazy
+ * evaluation of gates" of Sec. 4.3.2, Fig. 7 caption).  Reads -- probability,
+ * measurement with collapse, Pauli-sum expectation, amplitude copies -- flush
+ * first, as reading a measurement result does in the paper (Sec. 4, listing
+ * 1: eng.flush() before int(qubit)).
+ *
+ * Conventions (the paper leaves them open; they hold for every call):
+ *   - qubit q is bit q of the amplitude index (little-endian);
+ *   - a gate on targets t[0..k-1] is a 2^k x 2^k matrix whose row/column
+ *     index r has bit j equal to the value of qubit t[j];
+ *   - host matrices are row-major complex double, (re, im) interleaved:
+ *     2 * 4^k doubles;
+ *   - controls fire on |1> (Sec. 4.1.3, Control meta-instruction);
+ *   - device amplitudes are interleaved (re, im), complex128 (16 B) or
+ *     complex64 (8 B), contiguous, 2^n of them, 256-byte aligned.
+ *
+ * Errors: every call returns QSIM_OK (0) or a positive status code; nothing
+ * throws across the ABI.  sim_last_error() gives a one-line message for the
+ * last failed call on that handle.  A call that fails validation changes
+ * neither the queue nor the state.  A CUDA failure (QSIM_ECUDA) leaves the
+ * state undefined.
+ *
+ * Ownership: the caller owns every host buffer passed in and out; matrices
+ * are copied during sim_apply.  Device buffers are either passed in by the
+ * caller through qsim_opts (then the caller keeps ownership and must keep
+ * them alive until sim_destroy) or allocated by the library and freed in
+ * sim_destroy.
+ *
+ * Threads and streams: a handle is used by one host thread at a time.  All
+ * device work of a handle runs in order on its stream (qsim_opts.stream or
+ * sim_set_stream); calls that return a host value synchronise that stream.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsim qsim;
+
+enum qsim_status {
+    QSIM_OK = 0,
+    QSIM_EINVAL = 1,      /* bad argument (size, pointer, matrix shape, u outside [0,1)) */
+    QSIM_ERANGE = 2,      /* qubit index outside [0, n) */
+    QSIM_EDUP = 3,        /* a qubit named twice among targets and controls */
+    QSIM_ENOMEM = 4,      /* device or host allocation failed, or buffer too small */
+    QSIM_EZEROPROB = 5,   /* projection onto an outcome of probability 0 */
+    QSIM_ENONFINITE = 6,  /* matrix entry or amplitude is NaN or infinite */
+    QSIM_ECUDA = 7,       /* a CUDA call failed; see sim_last_error */
+    QSIM_ETIMEOUT = 8,    /* a bounded device wait gave up */
+    QSIM_ENOTSUP = 9      /* combination not supported by this build */
+};
+
+enum qsim_precision {
+    QSIM_C128 = 0, /* complex128 amplitudes, FP64 arithmetic */
+    QSIM_C64 = 1   /* complex64 amplitudes; fused blocks on tensor cores */
+};
+
+enum qsim_fusion {
+    QSIM_FUSE_NONE = 0,   /* one launch per gate ("plain") */
+    QSIM_FUSE_GREEDY = 1, /* greedy grouping into blocks of <= kmax qubits */
+    QSIM_FUSE_MLP = 2     /* block boundaries chosen by the learned cost model */
+};
+
+/* Creation options.  Zero-initialise and set what you need; a NULL opts
+ * pointer means all defaults. */
+typedef struct qsim_opts {
+    void *state;            /* caller-owned device buffer for the amplitudes, or NULL */
+    size_t state_bytes;     /* its size; must be >= 2^n * (16 or 8) */
+    void *workspace;        /* caller-owned device scratch, or NULL */
+    size_t workspace_bytes; /* its size; must be >= sim_workspace_bytes() */
+    void *stream;           /* cudaStream_t to run on; NULL = legacy default stream */
+    int fusion;             /* enum qsim_fusion; default QSIM_FUSE_NONE */
+    int kmax;               /* largest fused block, 1..5; 0 = default 5 */
+    int device;             /* CUDA device ordinal; the current device is used if < 0 */
+} qsim_opts;
+
+/* A Pauli-sum term c * P.  Qubit q of P is X if bit q is set in xmask only,
+ * Z if in zmask only, Y if in both, identity otherwise. */
+typedef struct qsim_pauli {
+    double coeff;
+    uint64_t xmask;
+    uint64_t zmask;
+} qsim_pauli;
+
+/* Counters since creation (or the last sim_reset_stats). */
+typedef struct qsim_stats {
+    uint64_t gates;          /* gates accepted by sim_apply */
+    uint64_t passes;         /* full- or partial-vector kernel passes for gates */
+    uint64_t launches;       /* kernel launches of any kind */
+    double amp_updates;      /* sum over gates of 2^(n - #controls) */
+    double alg_bytes;        /* algorithmic HBM bytes of the gate passes */
+} qsim_stats;
+
+/* Scratch bytes a handle of n qubits needs (whatever the precision). */
+int sim_workspace_bytes(int n, int precision, size_t *bytes);
+
+/* Create an n-qubit register (1 <= n <= 36) in |0...0>.  On success *out
+ * receives the handle.  QSIM_ENOMEM if the state does not fit. */
+int sim_create(int n, int precision, const qsim_opts *opts, qsim **out);
+
+/* Destroy a handle; frees what the library allocated.  NULL is accepted. */
+int sim_destroy(qsim *s);
+
+/* Drop the queue and set the register to the basis state |basis>. */
+int sim_reset(qsim *s, uint64_t basis);
+
+/* Queue U (2^t x 2^t, see conventions) on targets[0..t-1], conditioned on
+ * controls[0..c-1] all being |1>.  1 <= t <= 5, 0 <= c < n.  Validated now
+ * (range, duplicates, finite entries), executed at the next flush.  U is not
+ * checked for unitarity. */
+int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const int *controls, int c);
+
+/* Execute every queued gate (Sec. 4.1.3: eng.flush()). */
+int sim_flush(qsim *s);
+
+/* P(qubit = 1) = sum of |psi_i|^2 over indices with bit q set, accumulated
+ * in FP64 (Sec. 4, measurement in the computational basis). */
+int sim_prob(qsim *s, int qubit, double *p1);
+
+/* p1[q] = P(qubit q = 1) for all q in one pass; p1 holds n doubles. *norm2
+ * (may be NULL) receives sum_i |psi_i|^2. */
+int sim_probs_all(qsim *s, double *p1, double *norm2);
+
+/* Measure one qubit with the caller's uniform draw u in [0,1): the outcome
+ * is 0 iff u * norm2 < P(qubit = 0); the register is projected onto the
+ * outcome and renormalised by 1/sqrt(p) computed in FP64 (Sec. 4 listing 1;
+ * Appendix A.1, A.3). *p_outcome may be NULL. */
+int sim_measure(qsim *s, int qubit, double u, int *outcome, double *p_outcome);
+
+/* Project onto qubits[j] == bits[j] (j < m) and renormalise.  *p (may be
+ * NULL) receives the probability of the projected outcome.  A projection of
+ * probability 0 returns QSIM_EZEROPROB and leaves the state unchanged. */
+int sim_collapse(qsim *s, const int *qubits, int m, const int *bits, double *p);
+
+/* Sample the whole register with draw u in [0,1): the outcome is the
+ * smallest j with sum_{i<=j} |psi_i|^2 > u * norm2 (cumulative sums in
+ * FP64); the register collapses to |j> keeping the phase of psi_j. */
+int sim_measure_all(qsim *s, double u, uint64_t *outcome);
+
+/* <psi| sum_k terms[k].coeff * P_k |psi>, accumulated in FP64.  The state
+ * is assumed normalised (no division by the norm). */
+int sim_expect(qsim *s, const qsim_pauli *terms, int nterms, double *out);
+
+/* Copy amplitudes [offset, offset+count) to host memory as complex double
+ * (2*count doubles, re/im interleaved), widening complex64 exactly. */
+int sim_get_amplitudes(qsim *s, uint64_t offset, uint64_t count, double *out);
+
+/* Overwrite amplitudes [offset, offset+count) from host complex double
+ * (rounded to nearest for complex64).  No normalisation is applied. */
+int sim_set_amplitudes(qsim *s, uint64_t offset, uint64_t count, const double *in);
+
+/* Device pointer of the amplitudes (valid until sim_destroy).  Flushes. */
+int sim_state_ptr(qsim *s, void **dev_ptr);
+
+/* Run subsequent work on another cudaStream_t (after the current stream's
+ * queued work, which this call waits for). */
+int sim_set_stream(qsim *s, void *stream);
+
+/* Choose the fusion mode (enum qsim_fusion) and block width kmax (1..5).
+ * For QSIM_FUSE_MLP the cost model must have been loaded with
+ * sim_planner_load_mlp.  Flushes the queue first. */
+int sim_set_fusion(qsim *s, int mode, int kmax);
+
+int sim_get_stats(const qsim *s, qsim_stats *out);
+int sim_reset_stats(qsim *s);
+
+/* Per-kernel-class device time.  When profiling is on, every gate or block
+ * launch is bracketed by CUDA events on the handle's stream; the times are
+ * collected (stream synchronised) by sim_get_kernel_times, which returns one
+ * row per kernel class seen since profiling was switched on.  Class names:
+ * "gate_dense", "gate_phase", "gate_diag", "gate_x", "block_tc",
+ * "block_dense". */
+typedef struct qsim_kernel_time {
+    char name[24];
+    uint64_t launches;
+    double total_ms;   /* sum of event-timed durations */
+    double alg_bytes;  /* algorithmic HBM bytes of those launches */
+} qsim_kernel_time;
+
+int sim_set_profiling(qsim *s, int on);
+int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nrows);
+
+/* One-line description of the last failure on this handle ("" if none). */
+const char *sim_last_error(const qsim *s);
+
+/* Library build string: version, target architecture. */
+const char *qsim_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,491 @@
+// api.cpp -- the C ABI of libqsim (declared in include/qsim.h).
+//
+// Host side only: argument validation, the lazy gate queue, planning and the
+// dispatch of device work onto the handle's stream.  Every arithmetic step
+// on amplitudes runs in the CUDA kernels of gate_kernels.cu,
+// fused_kernel.cu and reduce_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+int set_err(qsim *s, int code, const std::string &msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+int cuda_err(qsim *s, cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return QSIM_OK;
+    if (s) s->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? QSIM_ENOMEM : QSIM_ECUDA;
+}
+
+namespace {
+
+constexpr size_t kPinnedBytes = 64u << 10;
+
+int validate_qubits(qsim *s, const int *a, int na, const int *b, int nb, uint64_t *ma, uint64_t *mb) {
+    uint64_t seen = 0;
+    *ma = *mb = 0;
+    for (int j = 0; j < na; ++j) {
+        if (a[j] < 0 || a[j] >= s->n) return set_err(s, QSIM_ERANGE, "qubit index out of range");
+        if ((seen >> a[j]) & 1ull) return set_err(s, QSIM_EDUP, "qubit named twice");
+        seen |= 1ull << a[j];
+        *ma |= 1ull << a[j];
+    }
+    for (int j = 0; j < nb; ++j) {
+        if (b[j] < 0 || b[j] >= s->n) return set_err(s, QSIM_ERANGE, "qubit index out of range");
+        if ((seen >> b[j]) & 1ull) return set_err(s, QSIM_EDUP, "qubit named twice");
+        seen |= 1ull << b[j];
+        *mb |= 1ull << b[j];
+    }
+    return QSIM_OK;
+}
+
+int classify(const GateRec &g) {
+    if (g.t != 1) return GK_DENSE;
+    const cd *m = g.m.data();
+    if (m[1] == 0.0 && m[2] == 0.0) return m[0] == 1.0 ? GK_PHASE : GK_DIAG1;
+    if (m[0] == 0.0 && m[3] == 0.0 && m[1] == 1.0 && m[2] == 1.0) return GK_X;
+    return GK_DENSE;
+}
+
+double gate_bytes(const qsim *s, const GateRec &g) {
+    const double b = (double)amp_bytes(s);
+    int fixed = (int)g.controls.size();
+    if (g.kind == GK_PHASE) fixed += 1;
+    return 2.0 * b * std::ldexp(1.0, s->n - fixed);
+}
+
+const char *kClassName[KC_COUNT] = {"gate_dense", "gate_phase", "gate_diag", "gate_x", "block_tc", "block_dense"};
+
+int harvest(qsim *s) {
+    if (s->pending.empty()) return QSIM_OK;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "stream synchronize");
+    for (const auto &p : s->pending) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, s->ev_pool[p.ev], s->ev_pool[p.ev + 1]);
+        if (e != cudaSuccess) return cuda_err(s, e, "event elapsed");
+        auto &c = s->class_time[p.cls];
+        c.launches++;
+        c.ms += ms;
+        c.bytes += p.bytes;
+    }
+    s->pending.clear();
+    s->ev_used = 0;
+    return QSIM_OK;
+}
+
+// Record an event on the stream; returns its pool index.
+int record_event(qsim *s, size_t *idx) {
+    if (s->ev_used == s->ev_pool.size()) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_err(s, e, "event create");
+        s->ev_pool.push_back(ev);
+    }
+    *idx = s->ev_used++;
+    return cuda_err(s, cudaEventRecord(s->ev_pool[*idx], s->stream), "event record");
+}
+
+int gate_class(const GateRec &g) {
+    switch (g.kind) {
+    case GK_PHASE: return KC_PHASE;
+    case GK_DIAG1: return KC_DIAG;
+    case GK_X: return KC_X;
+    default: return KC_DENSE;
+    }
+}
+
+int execute_plan(qsim *s, const std::vector<PlanItem> &plan) {
+    for (const PlanItem &it : plan) {
+        int rc;
+        size_t ev0 = 0, ev1 = 0;
+        if (s->profiling) {
+            if (s->pending.size() >= 4096 && (rc = harvest(s))) return rc;
+            if ((rc = record_event(s, &ev0))) return rc;
+        }
+        int cls;
+        double bytes;
+        if (!it.fused) {
+            const GateRec &g = s->queue[it.gate];
+            rc = launch_gate_plain(s, g);
+            bytes = gate_bytes(s, g);
+            cls = gate_class(g);
+        } else {
+            rc = QSIM_ENOTSUP;
+            cls = KC_BLOCK_TC;
+            if (s->prec == QSIM_C64 && it.k >= 4) rc = launch_block_tc(s, it.qubits, it.k, it.m.data());
+            if (rc == QSIM_ENOTSUP) {
+                cls = KC_BLOCK_DENSE;
+                rc = launch_block_dense(s, it.qubits, it.k, it.m.data());
+            }
+            bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
+        }
+        if (rc) return rc;
+        s->stats.alg_bytes += bytes;
+        if (s->profiling) {
+            if ((rc = record_event(s, &ev1))) return rc;
+            (void)ev1;
+            s->pending.push_back({cls, ev0, bytes});
+        }
+        s->stats.passes++;
+        s->stats.amp_updates += it.amp_updates;
+    }
+    return QSIM_OK;
+}
+
+int flush(qsim *s) {
+    if (s->queue.empty()) return QSIM_OK;
+    std::vector<PlanItem> plan;
+    if (s->fusion == QSIM_FUSE_NONE)
+        plan_none(s->queue, s->n, plan);
+    else
+        plan_greedy(s->queue, s->n, s->kmax, plan);
+    const int rc = execute_plan(s, plan);
+    s->queue.clear();
+    return rc;
+}
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+extern "C" {
+
+int sim_workspace_bytes(int n, int precision, size_t *bytes) {
+    if (!bytes || n < 1 || n > 36 || (precision != QSIM_C128 && precision != QSIM_C64)) return QSIM_EINVAL;
+    *bytes = kWsTotal;
+    return QSIM_OK;
+}
+
+int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
+    if (!out) return QSIM_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > 36) return QSIM_EINVAL;
+    if (precision != QSIM_C128 && precision != QSIM_C64) return QSIM_EINVAL;
+    qsim_opts o{};
+    if (opts) o = *opts;
+    if (o.fusion < QSIM_FUSE_NONE || o.fusion > QSIM_FUSE_MLP) return QSIM_EINVAL;
+    if (o.kmax == 0) o.kmax = 5;
+    if (o.kmax < 1 || o.kmax > 5) return QSIM_EINVAL;
+    qsim *s = new (std::nothrow) qsim();
+    if (!s) return QSIM_ENOMEM;
+    s->n = n;
+    s->prec = precision;
+    s->fusion = o.fusion == QSIM_FUSE_MLP ? QSIM_FUSE_GREEDY : o.fusion;
+    s->kmax = o.kmax;
+    s->stream = (cudaStream_t)o.stream;
+    if (o.device >= 0) {
+        if (cudaSetDevice(o.device) != cudaSuccess) {
+            delete s;
+            return QSIM_ECUDA;
+        }
+    }
+    cudaGetDevice(&s->device);
+    const size_t need = amp_bytes(s) << n;
+    int rc = QSIM_OK;
+    if (o.state) {
+        if (o.state_bytes < need || ((uintptr_t)o.state & 255u)) rc = QSIM_EINVAL;
+        s->state = o.state;
+    } else {
+        cudaError_t e = cudaMalloc(&s->state, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->state = nullptr;
+            rc = QSIM_ENOMEM;
+        } else {
+            s->own_state = true;
+        }
+    }
+    if (!rc) {
+        if (o.workspace) {
+            if (o.workspace_bytes < kWsTotal || ((uintptr_t)o.workspace & 255u)) rc = QSIM_EINVAL;
+            s->ws = o.workspace;
+            s->ws_bytes = o.workspace_bytes;
+        } else {
+            cudaError_t e = cudaMalloc(&s->ws, kWsTotal);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                s->ws = nullptr;
+                rc = QSIM_ENOMEM;
+            } else {
+                s->own_ws = true;
+                s->ws_bytes = kWsTotal;
+            }
+        }
+    }
+    if (!rc && cudaMallocHost((void **)&s->pinned, kPinnedBytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->pinned = nullptr;
+        rc = QSIM_ENOMEM;
+    }
+    if (!rc) rc = launch_set_basis(s, 0);
+    if (rc) {
+        sim_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return QSIM_OK;
+}
+
+int sim_destroy(qsim *s) {
+    if (!s) return QSIM_OK;
+    if (s->stream || s->state) cudaStreamSynchronize(s->stream);
+    if (s->own_state && s->state) cudaFree(s->state);
+    if (s->own_ws && s->ws) cudaFree(s->ws);
+    if (s->pinned) cudaFreeHost(s->pinned);
+    for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
+    delete s;
+    return QSIM_OK;
+}
+
+int sim_reset(qsim *s, uint64_t basis) {
+    if (!s) return QSIM_EINVAL;
+    if (basis >> s->n) return set_err(s, QSIM_ERANGE, "basis state out of range");
+    s->queue.clear();
+    return launch_set_basis(s, basis);
+}
+
+int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const int *controls, int c) {
+    if (!s) return QSIM_EINVAL;
+    if (!matrix || !targets || t < 1 || t > 5 || c < 0 || (c > 0 && !controls))
+        return set_err(s, QSIM_EINVAL, "bad gate arguments");
+    if (t + c > s->n) return set_err(s, QSIM_ERANGE, "more qubits than the register has");
+    GateRec g;
+    int rc = validate_qubits(s, targets, t, controls, c, &g.tmask, &g.cmask);
+    if (rc) return rc;
+    const int D = 1 << t;
+    for (int i = 0; i < 2 * D * D; ++i)
+        if (!is_finite(matrix[i])) return set_err(s, QSIM_ENONFINITE, "non-finite matrix entry");
+    g.t = t;
+    for (int j = 0; j < t; ++j) g.targets[j] = targets[j];
+    g.controls.assign(controls, controls + c);
+    g.m.resize((size_t)D * D);
+    for (int i = 0; i < D * D; ++i) g.m[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
+    g.kind = classify(g);
+    s->queue.push_back(std::move(g));
+    s->stats.gates++;
+    return QSIM_OK;
+}
+
+int sim_flush(qsim *s) {
+    if (!s) return QSIM_EINVAL;
+    return flush(s);
+}
+
+int sim_prob(qsim *s, int qubit, double *p1) {
+    if (!s || !p1) return QSIM_EINVAL;
+    if (qubit < 0 || qubit >= s->n) return set_err(s, QSIM_ERANGE, "qubit index out of range");
+    int rc = flush(s);
+    if (rc) return rc;
+    return run_masked_sum(s, 1ull << qubit, 1ull << qubit, p1);
+}
+
+int sim_probs_all(qsim *s, double *p1, double *norm2) {
+    if (!s || !p1) return QSIM_EINVAL;
+    int rc = flush(s);
+    if (rc) return rc;
+    return run_probs_all(s, p1, norm2);
+}
+
+int sim_measure(qsim *s, int qubit, double u, int *outcome, double *p_outcome) {
+    if (!s || !outcome) return QSIM_EINVAL;
+    if (qubit < 0 || qubit >= s->n) return set_err(s, QSIM_ERANGE, "qubit index out of range");
+    if (!(u >= 0.0 && u < 1.0)) return set_err(s, QSIM_EINVAL, "draw outside [0,1)");
+    int rc = flush(s);
+    if (rc) return rc;
+    double s0, s1;
+    rc = run_split_sum(s, qubit, &s0, &s1);
+    if (rc) return rc;
+    const int b = (u * (s0 + s1) < s0) ? 0 : 1;
+    const double p = b ? s1 : s0;
+    if (!(p > 0.0)) return set_err(s, QSIM_EZEROPROB, "measured outcome has probability 0");
+    rc = run_collapse_mask(s, 1ull << qubit, (uint64_t)b << qubit, 1.0 / std::sqrt(p));
+    if (rc) return rc;
+    *outcome = b;
+    if (p_outcome) *p_outcome = p;
+    return QSIM_OK;
+}
+
+int sim_collapse(qsim *s, const int *qubits, int m, const int *bits, double *p) {
+    if (!s || m < 1 || !qubits || !bits) return QSIM_EINVAL;
+    uint64_t mask, dummy;
+    int rc = validate_qubits(s, qubits, m, nullptr, 0, &mask, &dummy);
+    if (rc) return rc;
+    uint64_t value = 0;
+    for (int j = 0; j < m; ++j) {
+        if (bits[j] != 0 && bits[j] != 1) return set_err(s, QSIM_EINVAL, "bit values must be 0 or 1");
+        if (bits[j]) value |= 1ull << qubits[j];
+    }
+    rc = flush(s);
+    if (rc) return rc;
+    double pv;
+    rc = run_masked_sum(s, mask, value, &pv);
+    if (rc) return rc;
+    if (p) *p = pv;
+    if (!(pv > 0.0)) return set_err(s, QSIM_EZEROPROB, "projection has probability 0");
+    return run_collapse_mask(s, mask, value, 1.0 / std::sqrt(pv));
+}
+
+int sim_measure_all(qsim *s, double u, uint64_t *outcome) {
+    if (!s || !outcome) return QSIM_EINVAL;
+    if (!(u >= 0.0 && u < 1.0)) return set_err(s, QSIM_EINVAL, "draw outside [0,1)");
+    int rc = flush(s);
+    if (rc) return rc;
+    return run_measure_all(s, u, outcome);
+}
+
+int sim_expect(qsim *s, const qsim_pauli *terms, int nterms, double *out) {
+    if (!s || !out || nterms < 0 || (nterms > 0 && !terms)) return QSIM_EINVAL;
+    const uint64_t lim = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
+    for (int k = 0; k < nterms; ++k) {
+        if ((terms[k].xmask & ~lim) || (terms[k].zmask & ~lim))
+            return set_err(s, QSIM_ERANGE, "Pauli mask names a qubit out of range");
+        if (!is_finite(terms[k].coeff)) return set_err(s, QSIM_ENONFINITE, "non-finite coefficient");
+    }
+    int rc = flush(s);
+    if (rc) return rc;
+    if (nterms == 0) {
+        *out = 0.0;
+        return QSIM_OK;
+    }
+    return run_expect(s, terms, nterms, out);
+}
+
+int sim_get_amplitudes(qsim *s, uint64_t offset, uint64_t count, double *out) {
+    if (!s || (!out && count)) return QSIM_EINVAL;
+    const uint64_t N = 1ull << s->n;
+    if (offset > N || count > N - offset) return set_err(s, QSIM_ERANGE, "amplitude range out of bounds");
+    int rc = flush(s);
+    if (rc) return rc;
+    if (!count) return QSIM_OK;
+    cudaError_t e;
+    if (s->prec == QSIM_C128) {
+        e = cudaMemcpyAsync(out, (const char *)s->state + offset * 16, count * 16, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        return cuda_err(s, e, "amplitude copy");
+    }
+    std::vector<float> tmp;
+    try {
+        tmp.resize(2 * count);
+    } catch (...) {
+        return set_err(s, QSIM_ENOMEM, "host buffer");
+    }
+    e = cudaMemcpyAsync(tmp.data(), (const char *)s->state + offset * 8, count * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "amplitude copy");
+    for (uint64_t i = 0; i < 2 * count; ++i) out[i] = (double)tmp[i];
+    return QSIM_OK;
+}
+
+int sim_set_amplitudes(qsim *s, uint64_t offset, uint64_t count, const double *in) {
+    if (!s || (!in && count)) return QSIM_EINVAL;
+    const uint64_t N = 1ull << s->n;
+    if (offset > N || count > N - offset) return set_err(s, QSIM_ERANGE, "amplitude range out of bounds");
+    for (uint64_t i = 0; i < 2 * count; ++i)
+        if (!is_finite(in[i])) return set_err(s, QSIM_ENONFINITE, "non-finite amplitude");
+    int rc = flush(s);
+    if (rc) return rc;
+    if (!count) return QSIM_OK;
+    cudaError_t e;
+    if (s->prec == QSIM_C128) {
+        e = cudaMemcpyAsync((char *)s->state + offset * 16, in, count * 16, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        return cuda_err(s, e, "amplitude copy");
+    }
+    std::vector<float> tmp;
+    try {
+        tmp.resize(2 * count);
+    } catch (...) {
+        return set_err(s, QSIM_ENOMEM, "host buffer");
+    }
+    for (uint64_t i = 0; i < 2 * count; ++i) tmp[i] = (float)in[i];
+    e = cudaMemcpyAsync((char *)s->state + offset * 8, tmp.data(), count * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_err(s, e, "amplitude copy");
+}
+
+int sim_state_ptr(qsim *s, void **dev_ptr) {
+    if (!s || !dev_ptr) return QSIM_EINVAL;
+    int rc = flush(s);
+    if (rc) return rc;
+    *dev_ptr = s->state;
+    return QSIM_OK;
+}
+
+int sim_set_stream(qsim *s, void *stream) {
+    if (!s) return QSIM_EINVAL;
+    int rc = flush(s);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "stream synchronize");
+    s->stream = (cudaStream_t)stream;
+    return QSIM_OK;
+}
+
+int sim_set_fusion(qsim *s, int mode, int kmax) {
+    if (!s) return QSIM_EINVAL;
+    if (mode < QSIM_FUSE_NONE || mode > QSIM_FUSE_MLP) return set_err(s, QSIM_EINVAL, "unknown fusion mode");
+    if (kmax < 1 || kmax > 5) return set_err(s, QSIM_EINVAL, "kmax outside 1..5");
+    int rc = flush(s);
+    if (rc) return rc;
+    s->fusion = mode == QSIM_FUSE_MLP ? QSIM_FUSE_GREEDY : mode;
+    s->kmax = kmax;
+    return QSIM_OK;
+}
+
+int sim_get_stats(const qsim *s, qsim_stats *out) {
+    if (!s || !out) return QSIM_EINVAL;
+    *out = s->stats;
+    return QSIM_OK;
+}
+
+int sim_reset_stats(qsim *s) {
+    if (!s) return QSIM_EINVAL;
+    s->stats = qsim_stats{};
+    return QSIM_OK;
+}
+
+int sim_set_profiling(qsim *s, int on) {
+    if (!s) return QSIM_EINVAL;
+    int rc = flush(s);
+    if (rc) return rc;
+    if ((rc = harvest(s))) return rc;
+    s->profiling = on != 0;
+    for (auto &c : s->class_time) c = qsim::ClassTime{};
+    return QSIM_OK;
+}
+
+int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nrows) {
+    if (!s || !nrows || (max_rows > 0 && !rows)) return QSIM_EINVAL;
+    int rc = flush(s);
+    if (rc) return rc;
+    if ((rc = harvest(s))) return rc;
+    int k = 0;
+    for (int c = 0; c < KC_COUNT; ++c) {
+        if (!s->class_time[c].launches) continue;
+        if (k < max_rows) {
+            std::memset(&rows[k], 0, sizeof(rows[k]));
+            std::strncpy(rows[k].name, kClassName[c], sizeof(rows[k].name) - 1);
+            rows[k].launches = s->class_time[c].launches;
+            rows[k].total_ms = s->class_time[c].ms;
+            rows[k].alg_bytes = s->class_time[c].bytes;
+        }
+        ++k;
+    }
+    *nrows = k;
+    return QSIM_OK;
+}
+
+const char *sim_last_error(const qsim *s) { return s ? s->err.c_str() : "null handle"; }
+
+const char *qsim_build_info(void) { return "libqsim 0.1 sm_103a"; }
+
+}  // extern "C"

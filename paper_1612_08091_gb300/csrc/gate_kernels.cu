@@ -1,0 +1,229 @@
+// gate_kernels.cu -- unfused ("plain") gate application, one launch per gate.
+//
+// The operation is the simulator's per-gate sweep over the 2^n amplitudes
+// (ProjectQ paper, Sec. 4.3.2): for every group of amplitudes that differ
+// only in the target bits and have every control bit equal to 1 (Sec. 4.1.3,
+// Control), replace the 2^t amplitudes of the group by U times them.  Groups
+// are enumerated directly by inserting zero bits at the target and control
+// positions into a group counter, so a gate with c controls touches only the
+// 2^(n-c) amplitudes it changes (a 27-control Z on 28 qubits touches 2).
+//
+// Each thread owns one group: it gathers 2^t amplitudes, multiplies, and
+// scatters.  complex128 uses FP64 arithmetic, complex64 FP32.  Specialised
+// kernels avoid arithmetic the gate does not need: a phase on the all-ones
+// subspace (Z, S, T, R(phi), CZ, multi-controlled Z), a diagonal one-qubit
+// gate (RZ), and the X permutation (X, CNOT, Toffoli).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace qsim_dev;
+
+namespace {
+
+template <typename Amp> struct Mat1 { Amp m[4]; };
+template <typename Amp, int K> struct MatK { Amp m[(1 << K) * (1 << K)]; uint64_t off[1 << K]; };
+
+template <typename Amp>
+__global__ void __launch_bounds__(256) k_dense1(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                                uint64_t cmask, uint64_t tbit, const Mat1<Amp> M) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t i0 = insert_zeros(g, ins) | cmask;
+    const uint64_t i1 = i0 | tbit;
+    const Amp a = psi[i0], b = psi[i1];
+    Amp na = cmul(M.m[0], a);
+    na = cfma(M.m[1], b, na);
+    Amp nb = cmul(M.m[2], a);
+    nb = cfma(M.m[3], b, nb);
+    psi[i0] = na;
+    psi[i1] = nb;
+}
+
+template <typename Amp, int K>
+__global__ void __launch_bounds__(128) k_denseK(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                                uint64_t cmask, const MatK<Amp, K> M) {
+    constexpr int D = 1 << K;
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t base = insert_zeros(g, ins) | cmask;
+    Amp v[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) v[r] = psi[base + M.off[r]];
+#pragma unroll 1
+    for (int r = 0; r < D; ++r) {
+        Amp acc = cmul(M.m[r * D], v[0]);
+#pragma unroll
+        for (int c = 1; c < D; ++c) acc = cfma(M.m[r * D + c], v[c], acc);
+        psi[base + M.off[r]] = acc;
+    }
+}
+
+template <typename Amp>
+__global__ void __launch_bounds__(256) k_phase(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                               uint64_t mask, Amp z) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t i = insert_zeros(g, ins) | mask;
+    psi[i] = cmul(z, psi[i]);
+}
+
+template <typename Amp>
+__global__ void __launch_bounds__(256) k_diag1(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                               uint64_t cmask, uint64_t tbit, Amp d0, Amp d1) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t i0 = insert_zeros(g, ins) | cmask;
+    const uint64_t i1 = i0 | tbit;
+    psi[i0] = cmul(d0, psi[i0]);
+    psi[i1] = cmul(d1, psi[i1]);
+}
+
+template <typename Amp>
+__global__ void __launch_bounds__(256) k_x(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                           uint64_t cmask, uint64_t tbit) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t i0 = insert_zeros(g, ins) | cmask;
+    const uint64_t i1 = i0 | tbit;
+    const Amp a = psi[i0], b = psi[i1];
+    psi[i0] = b;
+    psi[i1] = a;
+}
+
+InsertSpec make_spec(uint64_t mask) {
+    InsertSpec s{};
+    s.m = 0;
+    for (int b = 0; b < 64; ++b)
+        if ((mask >> b) & 1ull) s.pos[s.m++] = b;
+    return s;
+}
+
+inline double2 to_amp(cd z, double2 *) { return make_double2(z.real(), z.imag()); }
+inline float2 to_amp(cd z, float2 *) { return make_float2((float)z.real(), (float)z.imag()); }
+template <typename Amp> Amp amp(cd z) { return to_amp(z, (Amp *)nullptr); }
+
+inline unsigned blocks_for(uint64_t work, int threads) {
+    return (unsigned)((work + (uint64_t)threads - 1) / (uint64_t)threads);
+}
+
+template <typename Amp, int K>
+int dense_k(qsim *s, const int *targets, uint64_t cmask, const cd *m) {
+    constexpr int D = 1 << K;
+    MatK<Amp, K> M;
+    uint64_t tmask = 0;
+    for (int j = 0; j < K; ++j) tmask |= 1ull << targets[j];
+    for (int r = 0; r < D; ++r) {
+        uint64_t o = 0;
+        for (int j = 0; j < K; ++j)
+            if ((r >> j) & 1) o |= 1ull << targets[j];
+        M.off[r] = o;
+    }
+    for (int i = 0; i < D * D; ++i) M.m[i] = amp<Amp>(m[i]);
+    const InsertSpec ins = make_spec(tmask | cmask);
+    const uint64_t ngroups = 1ull << (s->n - ins.m);
+    k_denseK<Amp, K><<<blocks_for(ngroups, 128), 128, 0, s->stream>>>((Amp *)s->state, ngroups, ins, cmask, M);
+    s->stats.launches++;
+    return cuda_err(s, cudaGetLastError(), "dense gate launch");
+}
+
+template <typename Amp>
+int gate_plain(qsim *s, const GateRec &g) {
+    Amp *psi = (Amp *)s->state;
+    const uint64_t tbit = 1ull << g.targets[0];
+    switch (g.kind) {
+    case GK_PHASE: {
+        const uint64_t mask = g.tmask | g.cmask;
+        const InsertSpec ins = make_spec(mask);
+        const uint64_t ngroups = 1ull << (s->n - ins.m);
+        k_phase<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, mask, amp<Amp>(g.m[3]));
+        break;
+    }
+    case GK_DIAG1: {
+        const InsertSpec ins = make_spec(g.tmask | g.cmask);
+        const uint64_t ngroups = 1ull << (s->n - ins.m);
+        k_diag1<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit,
+                                                                        amp<Amp>(g.m[0]), amp<Amp>(g.m[3]));
+        break;
+    }
+    case GK_X: {
+        const InsertSpec ins = make_spec(g.tmask | g.cmask);
+        const uint64_t ngroups = 1ull << (s->n - ins.m);
+        k_x<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit);
+        break;
+    }
+    default: {
+        switch (g.t) {
+        case 1: {
+            Mat1<Amp> M;
+            for (int i = 0; i < 4; ++i) M.m[i] = amp<Amp>(g.m[i]);
+            const InsertSpec ins = make_spec(g.tmask | g.cmask);
+            const uint64_t ngroups = 1ull << (s->n - ins.m);
+            k_dense1<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit, M);
+            break;
+        }
+        case 2: return dense_k<Amp, 2>(s, g.targets, g.cmask, g.m.data());
+        case 3: return dense_k<Amp, 3>(s, g.targets, g.cmask, g.m.data());
+        case 4: return dense_k<Amp, 4>(s, g.targets, g.cmask, g.m.data());
+        case 5: return dense_k<Amp, 5>(s, g.targets, g.cmask, g.m.data());
+        default: return set_err(s, QSIM_EINVAL, "gate with more than 5 targets");
+        }
+    }
+    }
+    s->stats.launches++;
+    return cuda_err(s, cudaGetLastError(), "gate launch");
+}
+
+template <typename Amp>
+int block_dense(qsim *s, const int *q, int k, const cd *m) {
+    if (k == 1) {
+        GateRec g;
+        g.t = 1;
+        g.targets[0] = q[0];
+        g.tmask = 1ull << q[0];
+        g.m.assign(m, m + 4);
+        g.kind = GK_DENSE;
+        return gate_plain<Amp>(s, g);
+    }
+    switch (k) {
+    case 2: return dense_k<Amp, 2>(s, q, 0, m);
+    case 3: return dense_k<Amp, 3>(s, q, 0, m);
+    case 4: return dense_k<Amp, 4>(s, q, 0, m);
+    case 5: return dense_k<Amp, 5>(s, q, 0, m);
+    }
+    return set_err(s, QSIM_EINVAL, "block width outside 1..5");
+}
+
+template <typename Amp>
+__global__ void k_set_basis(Amp *__restrict__ psi, uint64_t N, uint64_t basis) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (; i < N; i += stride) {
+        Amp z;
+        z.x = (i == basis) ? 1 : 0;
+        z.y = 0;
+        psi[i] = z;
+    }
+}
+
+}  // namespace
+
+int launch_gate_plain(qsim *s, const GateRec &g) {
+    return s->prec == QSIM_C128 ? gate_plain<double2>(s, g) : gate_plain<float2>(s, g);
+}
+
+int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m) {
+    return s->prec == QSIM_C128 ? block_dense<double2>(s, qubits, k, m) : block_dense<float2>(s, qubits, k, m);
+}
+
+int launch_set_basis(qsim *s, uint64_t basis) {
+    const uint64_t N = 1ull << s->n;
+    const unsigned grid = (unsigned)std::min<uint64_t>(blocks_for(N, 256), (uint64_t)kSMs * 16);
+    if (s->prec == QSIM_C128)
+        k_set_basis<double2><<<grid, 256, 0, s->stream>>>((double2 *)s->state, N, basis);
+    else
+        k_set_basis<float2><<<grid, 256, 0, s->stream>>>((float2 *)s->state, N, basis);
+    s->stats.launches++;
+    return cuda_err(s, cudaGetLastError(), "set basis launch");
+}

@@ -1,0 +1,109 @@
+// internal.h -- host-side structures shared by the libqsim translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+typedef std::complex<double> cd;
+
+// How a queued gate is executed by the unfused path.
+enum GateKind {
+    GK_DENSE = 0,  // general 2^t x 2^t matrix
+    GK_DIAG1 = 1,  // one target, diag(d0, d1)
+    GK_PHASE = 2,  // diag(1, z) on one target: multiply amplitudes with all of
+                   // (targets | controls) set to 1 by z
+    GK_X = 3       // one target, [[0,1],[1,0]]: swap amplitude pairs
+};
+
+struct GateRec {
+    int t = 0;
+    int targets[5] = {0, 0, 0, 0, 0};
+    std::vector<int> controls;
+    uint64_t tmask = 0, cmask = 0;
+    std::vector<cd> m;  // 4^t entries, row-major, index bit j = targets[j]
+    int kind = GK_DENSE;
+};
+
+// One unit of device work produced by the planner.
+struct PlanItem {
+    bool fused = false;     // false: execute gates[gate] with the plain kernels
+    int gate = -1;
+    int k = 0;              // fused block width
+    int qubits[5] = {0, 0, 0, 0, 0};  // sorted ascending; bit j of the block index
+    std::vector<cd> m;      // 2^k x 2^k block matrix
+    double amp_updates = 0; // credited to the original gates
+    int ngates = 0;
+};
+
+struct qsim {
+    int n = 0;
+    int prec = QSIM_C128;
+    int device = 0;
+    void *state = nullptr;
+    bool own_state = false;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    cudaStream_t stream = nullptr;
+    int fusion = QSIM_FUSE_NONE;
+    int kmax = 5;
+    std::vector<GateRec> queue;
+    double *pinned = nullptr;  // small pinned host buffer for results
+    qsim_stats stats{};
+    std::string err;
+    // profiling: events around each launch, harvested on demand
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Pending { int cls; size_t ev; double bytes; };
+    std::vector<Pending> pending;
+    struct ClassTime { uint64_t launches = 0; double ms = 0, bytes = 0; };
+    ClassTime class_time[8];
+};
+
+enum KernelClass { KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_COUNT };
+
+// Bytes of one amplitude.
+inline size_t amp_bytes(const qsim *s) { return s->prec == QSIM_C128 ? 16 : 8; }
+
+// Workspace layout (byte offsets) -----------------------------------------
+constexpr size_t kWsPartials = 0;                       // reduction partials
+constexpr size_t kWsPartialsBytes = 1u << 20;           // 1 MiB
+constexpr size_t kWsResult = kWsPartials + kWsPartialsBytes;  // final values
+constexpr size_t kWsResultBytes = 64u << 10;            // 64 KiB
+constexpr size_t kWsChunk = kWsResult + kWsResultBytes; // measure-all chunk sums
+constexpr size_t kWsChunkBytes = 64u << 10;
+constexpr size_t kWsTotal = kWsChunk + kWsChunkBytes;
+constexpr int kReduceBlocks = 608;                      // 4 per SM
+constexpr int kMaxChunks = 4096;
+
+// Error helpers -------------------------------------------------------------
+int set_err(qsim *s, int code, const std::string &msg);
+int cuda_err(qsim *s, cudaError_t e, const char *where);
+
+// Launchers (gate_kernels.cu) -----------------------------------------------
+int launch_gate_plain(qsim *s, const GateRec &g);
+int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m);
+int launch_set_basis(qsim *s, uint64_t basis);
+
+// Fused tensor-core block (fused_kernel.cu).  Returns QSIM_ENOTSUP when the
+// block cannot run on the tensor-core kernel (caller falls back).
+int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m);
+
+// Reductions and measurement (reduce_kernels.cu) ----------------------------
+int run_probs_all(qsim *s, double *p1, double *norm2);
+int run_masked_sum(qsim *s, uint64_t mask, uint64_t value, double *out);
+int run_split_sum(qsim *s, int q, double *s0, double *s1);
+int run_collapse_mask(qsim *s, uint64_t mask, uint64_t value, double scale);
+int run_expect(qsim *s, const qsim_pauli *terms, int nterms, double *out);
+int run_measure_all(qsim *s, double u, uint64_t *outcome);
+
+// Planner (planner.cpp) -------------------------------------------------------
+void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out);
+void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out);

@@ -1,0 +1,703 @@
+// reduce_kernels.cu -- probabilities, collapse, full-register sampling and
+// Pauli-sum expectation values.
+//
+// Measurement in the computational basis with collapse of the register is
+// the paper's Measure operation (ProjectQ paper, Sec. 4 listing 1; Appendix
+// A.1 teleportation; Appendix A.3 measure-and-reset).  The sums behind it
+// are accumulated in FP64: per-thread partial sums of |psi_i|^2 are formed in
+// the amplitude precision over short runs (8 terms for complex64), added in
+// FP64, reduced across the warp by shuffles and across blocks by a
+// fixed-order second stage, so every result is deterministic for a given
+// launch configuration.
+//
+// Expectation values <psi|P|psi> of Pauli strings P (Z-only strings in one
+// pass for all terms; strings with an X/Y part grouped by their X mask, one
+// pass per group) use  P|i> = i^{#Y} (-1)^{popc(i & zmask)} |i ^ xmask>.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace qsim_dev;
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+__device__ double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// all single-qubit probabilities in one pass
+// ---------------------------------------------------------------------------
+// A warp owns tiles of 1024 consecutive amplitudes; lane l reads index
+// tile*1024 + 32*j + l for j = 0..31 (each j is a coalesced 32-amplitude
+// run).  Per lane it sums w_j = |psi|^2 over all j (S) and over the j with
+// bit b set (Sb[b]).  Then P(q=1) gets: for q < 5 the lanes with bit q set,
+// for 5 <= q < 10 the warp sum of Sb[q-5], for q >= 10 the whole tile if bit
+// q of the tile index is set.  Lane q accumulates qubit q (and q+32).
+template <typename Amp>
+__global__ void __launch_bounds__(kRedThreads) k_probs_tiles(const Amp *__restrict__ psi, int n, uint64_t ntiles,
+                                                             double *__restrict__ partials) {
+    typedef typename AmpTraits<Amp>::real R;
+    __shared__ double sh[kRedThreads / 32][2 * 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double accA = 0.0, accB = 0.0, accN = 0.0;
+    for (uint64_t tile = (uint64_t)blockIdx.x * nw + warp; tile < ntiles; tile += (uint64_t)gridDim.x * nw) {
+        const Amp *p = psi + (tile << 10) + lane;
+        R S = 0, Sb[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const R w = norm2(p[j * 32]);
+            S += w;
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+                if ((j >> b) & 1) Sb[b] += w;
+        }
+        const double dS = (double)S;
+        const double T = warp_sum(dS);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const double a = warp_sum(((lane >> q) & 1) ? dS : 0.0);
+            if (lane == q) accA += a;
+        }
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            const double a = warp_sum((double)Sb[b]);
+            if (lane == 5 + b) accA += a;
+        }
+        const uint64_t base = tile << 10;
+        if (lane >= 10 && lane < n && ((base >> lane) & 1ull)) accA += T;
+        if (lane + 32 < n && ((base >> (lane + 32)) & 1ull)) accB += T;
+        accN += T;
+    }
+    sh[warp][1 + lane] = accA;
+    sh[warp][33 + lane] = accB;
+    if (lane == 0) sh[warp][0] = accN;
+    __syncthreads();
+    const int V = n + 1;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh[w][v];
+        partials[(size_t)blockIdx.x * V + v] = t;
+    }
+}
+
+// Small registers (n < 10): one block, one amplitude per thread per step.
+template <typename Amp>
+__global__ void k_probs_small(const Amp *__restrict__ psi, int n, double *__restrict__ out) {
+    __shared__ double sh[32];
+    const uint64_t N = 1ull << n;
+    for (int v = 0; v <= n; ++v) {
+        double acc = 0.0;
+        for (uint64_t i = threadIdx.x; i < N; i += blockDim.x) {
+            const double w = (double)norm2(psi[i]);
+            if (v == 0 || ((i >> (v - 1)) & 1ull)) acc += w;
+        }
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) out[v] = acc;
+    }
+}
+
+// Fixed-order second stage: out[v] = sum_b partials[b*V + v].
+__global__ void k_finalize(const double *__restrict__ partials, int nblocks, int V, double *__restrict__ out) {
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) t += partials[(size_t)b * V + v];
+        out[v] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// masked sums:  sum over {i : (i & mask) == value} of |psi_i|^2
+// ---------------------------------------------------------------------------
+template <typename Amp>
+__global__ void __launch_bounds__(kRedThreads) k_masked_sum(const Amp *__restrict__ psi, uint64_t ngroups,
+                                                            const InsertSpec ins, uint64_t value,
+                                                            double *__restrict__ partials) {
+    typedef typename AmpTraits<Amp>::real R;
+    __shared__ double sh[32];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    while (g < ngroups) {
+        R run = 0;
+#pragma unroll 1
+        for (int r = 0; r < 8 && g < ngroups; ++r, g += stride) run += norm2(psi[insert_zeros(g, ins) | value]);
+        acc += (double)run;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// Both halves of one qubit: partials[2b] = sum over bit q = 0, [2b+1] = bit 1.
+template <typename Amp>
+__global__ void __launch_bounds__(kRedThreads) k_split_sum(const Amp *__restrict__ psi, uint64_t npairs, int q,
+                                                           double *__restrict__ partials) {
+    typedef typename AmpTraits<Amp>::real R;
+    __shared__ double sh[32];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t bit = 1ull << q, lowmask = bit - 1ull;
+    uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    double a0 = 0.0, a1 = 0.0;
+    while (g < npairs) {
+        R r0 = 0, r1 = 0;
+#pragma unroll 1
+        for (int r = 0; r < 8 && g < npairs; ++r, g += stride) {
+            const uint64_t i0 = ((g & ~lowmask) << 1) | (g & lowmask);
+            r0 += norm2(psi[i0]);
+            r1 += norm2(psi[i0 | bit]);
+        }
+        a0 += (double)r0;
+        a1 += (double)r1;
+    }
+    a0 = block_sum(a0, sh);
+    a1 = block_sum(a1, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a0;
+        partials[2 * blockIdx.x + 1] = a1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// collapse: keep {i : (i & mask) == value} scaled by 1/sqrt(p), zero the rest
+// ---------------------------------------------------------------------------
+// The FP64 scale is applied to complex64 as a two-float split
+// (s = s_hi + s_lo), so the only rounding is the final one to storage.
+__device__ __forceinline__ double2 scale_amp(double2 a, double s, float, float) {
+    return make_double2(a.x * s, a.y * s);
+}
+__device__ __forceinline__ float2 scale_amp(float2 a, double, float shi, float slo) {
+    return make_float2(fmaf(a.x, shi, a.x * slo), fmaf(a.y, shi, a.y * slo));
+}
+
+template <typename Amp>
+__global__ void k_collapse_mask(Amp *__restrict__ psi, uint64_t N, uint64_t mask, uint64_t value, double s,
+                                float shi, float slo) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+        if ((i & mask) == value) {
+            psi[i] = scale_amp(psi[i], s, shi, slo);
+        } else {
+            Amp z;
+            z.x = 0;
+            z.y = 0;
+            psi[i] = z;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// expectation of Z-only strings:  sum_i |psi_i|^2 f(i),
+// f(i) = sum_k c_k (-1)^{popc(i & z_k)}
+// ---------------------------------------------------------------------------
+// A warp owns tiles of 1024 amplitudes as in k_probs_tiles.  With j the
+// run index (bits 5..9) and l the lane (bits 0..4), each lane forms the
+// Walsh-Hadamard transform W^(m) = sum_j w_j (-1)^{popc(j & m)} of its 32
+// weights; a term then contributes c_k (-1)^{popc((tile|l) & z_k)} W^(m_k)
+// with m_k = bits 5..9 of z_k.  W^ is kept per warp in shared memory.
+constexpr int kMaxZTerms = 96;
+struct ZTerms {
+    int nt;
+    double c[kMaxZTerms];
+    uint64_t z[kMaxZTerms];
+};
+
+constexpr int kZThreads = 128;
+
+template <typename Amp>
+__global__ void __launch_bounds__(kZThreads) k_expect_z_tiles(const Amp *__restrict__ psi, uint64_t ntiles,
+                                                              const ZTerms T, double *__restrict__ partials) {
+    typedef typename AmpTraits<Amp>::real R;
+    __shared__ R wh[kZThreads / 32][32][32];
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double acc = 0.0;
+    for (uint64_t tile = (uint64_t)blockIdx.x * nw + warp; tile < ntiles; tile += (uint64_t)gridDim.x * nw) {
+        const Amp *p = psi + (tile << 10) + lane;
+        R w[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) w[j] = norm2(p[j * 32]);
+        // in-register Walsh-Hadamard transform over the 5 run bits
+#pragma unroll
+        for (int h = 1; h < 32; h <<= 1) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if ((j & h) == 0) {
+                    const R a = w[j], b = w[j + h];
+                    w[j] = a + b;
+                    w[j + h] = a - b;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 32; ++m) wh[warp][m][lane] = w[m];
+        __syncwarp();
+        const uint64_t idx = (tile << 10) | (uint64_t)lane;
+        R e = 0;
+        for (int k = 0; k < T.nt; ++k) {
+            const uint64_t z = T.z[k];
+            const int m = (int)((z >> 5) & 31u);
+            const int par = (__popcll(idx & z & ~0x3E0ull)) & 1;
+            const R v = wh[warp][m][lane];
+            const R c = (R)T.c[k];
+            e += par ? -c * v : c * v;
+        }
+        __syncwarp();
+        acc += (double)e;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+template <typename Amp>
+__global__ void k_expect_z_small(const Amp *__restrict__ psi, uint64_t N, const ZTerms T, double *__restrict__ out) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (uint64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double w = (double)norm2(psi[i]);
+        double f = 0.0;
+        for (int k = 0; k < T.nt; ++k) f += (__popcll(i & T.z[k]) & 1) ? -T.c[k] : T.c[k];
+        acc += w * f;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// expectation of strings sharing one X mask x != 0:
+//   <psi|P|psi> = sum over pairs (i, j = i ^ x) with bit h of i clear
+//                 of 2 Re[ i^{y} (-1)^{popc(i & z)} psi_i conj(psi_j) ]
+// (h = highest bit of x, y = popc(x & z) = number of Y factors).
+// ---------------------------------------------------------------------------
+constexpr int kMaxXTerms = 32;
+struct XTerms {
+    int nt;
+    uint64_t x;
+    int h;
+    double c[kMaxXTerms];
+    uint64_t z[kMaxXTerms];
+    int y4[kMaxXTerms];  // number of Y factors mod 4
+};
+
+template <typename Amp>
+__global__ void __launch_bounds__(kRedThreads) k_expect_x(const Amp *__restrict__ psi, uint64_t npairs, const XTerms T,
+                                                          double *__restrict__ partials) {
+    typedef typename AmpTraits<Amp>::real R;
+    __shared__ double sh[32];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t bit = 1ull << T.h, lowmask = bit - 1ull;
+    double acc = 0.0;
+    uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    while (g < npairs) {
+        R run = 0;
+#pragma unroll 1
+        for (int r = 0; r < 8 && g < npairs; ++r, g += stride) {
+            const uint64_t i = ((g & ~lowmask) << 1) | (g & lowmask);
+            const uint64_t j = i ^ T.x;
+            const Amp a = psi[i], b = psi[j];
+            // w = a * conj(b)
+            const R wr = a.x * b.x + a.y * b.y;
+            const R wi = a.y * b.x - a.x * b.y;
+            R e = 0;
+            for (int k = 0; k < T.nt; ++k) {
+                R v;
+                switch (T.y4[k]) {
+                case 0: v = wr; break;
+                case 1: v = -wi; break;
+                case 2: v = -wr; break;
+                default: v = wi; break;
+                }
+                const R c = (R)T.c[k];
+                e += (__popcll(i & T.z[k]) & 1) ? -c * v : c * v;
+            }
+            run += e;
+        }
+        acc += 2.0 * (double)run;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// full-register sampling
+// ---------------------------------------------------------------------------
+// Chunk sums: chunk b = [b*len, (b+1)*len), summed in FP64.
+template <typename Amp>
+__global__ void __launch_bounds__(kRedThreads) k_chunk_sums(const Amp *__restrict__ psi, uint64_t len,
+                                                            double *__restrict__ sums) {
+    __shared__ double sh[32];
+    const Amp *p = psi + (uint64_t)blockIdx.x * len;
+    double acc = 0.0;
+    for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) acc += (double)norm2(p[i]);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) sums[blockIdx.x] = acc;
+}
+
+// Inclusive FP64 scan of |psi_i|^2 over one chunk, starting from `carry`;
+// writes the first index whose running sum exceeds `target` (or ~0 if none)
+// and that amplitude.  One block of 1024 threads.
+struct SearchOut {
+    unsigned long long index;
+    double re, im;
+    double total;
+};
+
+template <typename Amp>
+__global__ void __launch_bounds__(1024) k_chunk_search(const Amp *__restrict__ psi, uint64_t begin, uint64_t len,
+                                                       double carry, double target, SearchOut *out) {
+    __shared__ double wsum[32];
+    __shared__ unsigned long long found;
+    __shared__ double s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        found = ~0ull;
+        s_carry = carry;
+    }
+    __syncthreads();
+    for (uint64_t off = 0; off < len; off += blockDim.x) {
+        const uint64_t i = begin + off + threadIdx.x;
+        const bool valid = off + threadIdx.x < len;
+        double w = valid ? (double)norm2(psi[i]) : 0.0;
+        // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane == 31) wsum[warp] = w;
+        __syncthreads();
+        if (warp == 0) {
+            double v = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            wsum[lane] = v;  // inclusive over warps
+        }
+        __syncthreads();
+        const double c = s_carry + (warp > 0 ? wsum[warp - 1] : 0.0) + w;
+        if (valid && c > target) atomicMin(&found, (unsigned long long)i);
+        __syncthreads();
+        if (found != ~0ull) break;
+        if (threadIdx.x == 0) s_carry += wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out->index = found;
+        out->total = s_carry;
+        if (found != ~0ull) {
+            const Amp a = psi[found];
+            out->re = (double)a.x;
+            out->im = (double)a.y;
+        }
+    }
+}
+
+// Last index of non-zero weight in [begin, begin+len) (one block).
+template <typename Amp>
+__global__ void __launch_bounds__(1024) k_last_nonzero(const Amp *__restrict__ psi, uint64_t begin, uint64_t len,
+                                                       SearchOut *out) {
+    __shared__ unsigned long long best;
+    if (threadIdx.x == 0) best = 0ull;
+    __syncthreads();
+    unsigned long long mine = 0ull;
+    for (uint64_t off = threadIdx.x; off < len; off += blockDim.x)
+        if (norm2(psi[begin + off]) > 0) mine = begin + off + 1;  // +1 so that 0 means none
+    atomicMax(&best, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out->index = best ? best - 1 : ~0ull;
+        if (best) {
+            const Amp a = psi[best - 1];
+            out->re = (double)a.x;
+            out->im = (double)a.y;
+        }
+    }
+}
+
+template <typename Amp>
+__global__ void k_write_basis(Amp *__restrict__ psi, uint64_t N, uint64_t j, double re, double im) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+        Amp z;
+        z.x = (i == j) ? (typename AmpTraits<Amp>::real)re : 0;
+        z.y = (i == j) ? (typename AmpTraits<Amp>::real)im : 0;
+        psi[i] = z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+InsertSpec make_spec(uint64_t mask) {
+    InsertSpec s{};
+    s.m = 0;
+    for (int b = 0; b < 64; ++b)
+        if ((mask >> b) & 1ull) s.pos[s.m++] = b;
+    return s;
+}
+
+double *ws_partials(qsim *s) { return (double *)((char *)s->ws + kWsPartials); }
+double *ws_result(qsim *s) { return (double *)((char *)s->ws + kWsResult); }
+double *ws_chunks(qsim *s) { return (double *)((char *)s->ws + kWsChunk); }
+
+unsigned grid_for(uint64_t work, int threads, unsigned cap) {
+    const uint64_t b = (work + threads - 1) / threads;
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, cap));
+}
+
+// Copy `count` doubles from device to the pinned buffer and wait.
+int fetch(qsim *s, const double *dev, int count, double *host_out) {
+    cudaError_t e = cudaMemcpyAsync(s->pinned, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "result copy");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "stream synchronize");
+    std::memcpy(host_out, s->pinned, sizeof(double) * count);
+    return QSIM_OK;
+}
+
+int finalize(qsim *s, int nblocks, int V, double *host_out) {
+    k_finalize<<<1, 64, 0, s->stream>>>(ws_partials(s), nblocks, V, ws_result(s));
+    s->stats.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(s, e, "finalize launch");
+    return fetch(s, ws_result(s), V, host_out);
+}
+
+template <typename Amp>
+int probs_all_t(qsim *s, double *p1, double *norm2_out) {
+    const int n = s->n;
+    std::vector<double> v(n + 1);
+    if (n < 10) {
+        k_probs_small<Amp><<<1, 256, 0, s->stream>>>((const Amp *)s->state, n, ws_result(s));
+        s->stats.launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_err(s, e, "probs launch");
+        int rc = fetch(s, ws_result(s), n + 1, v.data());
+        if (rc) return rc;
+    } else {
+        const uint64_t ntiles = 1ull << (n - 10);
+        const unsigned grid = grid_for(ntiles, kRedThreads / 32, kReduceBlocks);
+        k_probs_tiles<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, n, ntiles, ws_partials(s));
+        s->stats.launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_err(s, e, "probs launch");
+        int rc = finalize(s, grid, n + 1, v.data());
+        if (rc) return rc;
+    }
+    if (norm2_out) *norm2_out = v[0];
+    for (int q = 0; q < n; ++q) p1[q] = v[1 + q];
+    return QSIM_OK;
+}
+
+template <typename Amp>
+int masked_sum_t(qsim *s, uint64_t mask, uint64_t value, double *out) {
+    const InsertSpec ins = make_spec(mask);
+    const uint64_t ngroups = 1ull << (s->n - ins.m);
+    const unsigned grid = grid_for(ngroups, kRedThreads, kReduceBlocks);
+    k_masked_sum<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, ngroups, ins, value, ws_partials(s));
+    s->stats.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(s, e, "masked sum launch");
+    return finalize(s, grid, 1, out);
+}
+
+template <typename Amp>
+int split_sum_t(qsim *s, int q, double *s0, double *s1) {
+    const uint64_t npairs = 1ull << (s->n - 1);
+    const unsigned grid = grid_for(npairs, kRedThreads, kReduceBlocks);
+    k_split_sum<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, npairs, q, ws_partials(s));
+    s->stats.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(s, e, "split sum launch");
+    double v[2];
+    int rc = finalize(s, grid, 2, v);
+    if (rc) return rc;
+    *s0 = v[0];
+    *s1 = v[1];
+    return QSIM_OK;
+}
+
+template <typename Amp>
+int collapse_t(qsim *s, uint64_t mask, uint64_t value, double scale) {
+    const uint64_t N = 1ull << s->n;
+    const float shi = (float)scale;
+    const float slo = (float)(scale - (double)shi);
+    const unsigned grid = grid_for(N, 256, kSMs * 16);
+    k_collapse_mask<Amp><<<grid, 256, 0, s->stream>>>((Amp *)s->state, N, mask, value, scale, shi, slo);
+    s->stats.launches++;
+    return cuda_err(s, cudaGetLastError(), "collapse launch");
+}
+
+template <typename Amp>
+int expect_t(qsim *s, const qsim_pauli *terms, int nterms, double *out) {
+    const int n = s->n;
+    const uint64_t N = 1ull << n;
+    double total = 0.0;
+    // Z-only strings, in batches of kMaxZTerms
+    std::vector<int> zonly;
+    for (int k = 0; k < nterms; ++k)
+        if (terms[k].xmask == 0) zonly.push_back(k);
+    for (size_t b0 = 0; b0 < zonly.size(); b0 += kMaxZTerms) {
+        ZTerms T{};
+        T.nt = (int)std::min<size_t>(kMaxZTerms, zonly.size() - b0);
+        for (int k = 0; k < T.nt; ++k) {
+            T.c[k] = terms[zonly[b0 + k]].coeff;
+            T.z[k] = terms[zonly[b0 + k]].zmask;
+        }
+        double v;
+        if (n < 10) {
+            k_expect_z_small<Amp><<<1, 256, 0, s->stream>>>((const Amp *)s->state, N, T, ws_result(s));
+            s->stats.launches++;
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_err(s, e, "expect launch");
+            int rc = fetch(s, ws_result(s), 1, &v);
+            if (rc) return rc;
+        } else {
+            const uint64_t ntiles = 1ull << (n - 10);
+            const unsigned grid = grid_for(ntiles, kZThreads / 32, 2 * kReduceBlocks);
+            k_expect_z_tiles<Amp><<<grid, kZThreads, 0, s->stream>>>((const Amp *)s->state, ntiles, T,
+                                                                         ws_partials(s));
+            s->stats.launches++;
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_err(s, e, "expect launch");
+            int rc = finalize(s, grid, 1, &v);
+            if (rc) return rc;
+        }
+        total += v;
+    }
+    // strings with an X part, grouped by X mask
+    std::vector<int> rest;
+    for (int k = 0; k < nterms; ++k)
+        if (terms[k].xmask != 0) rest.push_back(k);
+    std::stable_sort(rest.begin(), rest.end(), [&](int a, int b) { return terms[a].xmask < terms[b].xmask; });
+    size_t i = 0;
+    while (i < rest.size()) {
+        XTerms T{};
+        T.x = terms[rest[i]].xmask;
+        T.h = 63 - __builtin_clzll(T.x);
+        T.nt = 0;
+        while (i < rest.size() && terms[rest[i]].xmask == T.x && T.nt < kMaxXTerms) {
+            const qsim_pauli &p = terms[rest[i]];
+            T.c[T.nt] = p.coeff;
+            T.z[T.nt] = p.zmask;
+            T.y4[T.nt] = __builtin_popcountll(p.xmask & p.zmask) & 3;
+            ++T.nt;
+            ++i;
+        }
+        const uint64_t npairs = N >> 1;
+        const unsigned grid = grid_for(npairs, kRedThreads, kReduceBlocks);
+        k_expect_x<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, npairs, T, ws_partials(s));
+        s->stats.launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_err(s, e, "expect launch");
+        double v;
+        int rc = finalize(s, grid, 1, &v);
+        if (rc) return rc;
+        total += v;
+    }
+    *out = total;
+    return QSIM_OK;
+}
+
+template <typename Amp>
+int measure_all_t(qsim *s, double u, uint64_t *outcome) {
+    const int n = s->n;
+    const uint64_t N = 1ull << n;
+    const int nchunks = (int)std::min<uint64_t>(kMaxChunks, std::max<uint64_t>(1, N >> 8));
+    const uint64_t len = N / (uint64_t)nchunks;
+    k_chunk_sums<Amp><<<nchunks, kRedThreads, 0, s->stream>>>((const Amp *)s->state, len, ws_chunks(s));
+    s->stats.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(s, e, "chunk sums launch");
+    e = cudaMemcpyAsync(s->pinned, ws_chunks(s), sizeof(double) * nchunks, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "chunk sums copy");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "stream synchronize");
+    std::vector<double> sums(s->pinned, s->pinned + nchunks);
+    double norm = 0.0;
+    for (double v : sums) norm += v;
+    if (!(norm > 0.0)) return set_err(s, QSIM_EZEROPROB, "measure_all on a zero vector");
+    const double target = u * norm;
+    SearchOut *dout = (SearchOut *)ws_result(s);
+    SearchOut res{};
+    double prefix = 0.0;
+    int b = 0;
+    bool done = false;
+    for (; b < nchunks && !done; ++b) {
+        if (sums[b] > 0.0 && prefix + sums[b] > target) {
+            k_chunk_search<Amp><<<1, 1024, 0, s->stream>>>((const Amp *)s->state, (uint64_t)b * len, len, prefix,
+                                                           target, dout);
+            s->stats.launches++;
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_err(s, e, "chunk search launch");
+            double tmp[4];
+            int rc = fetch(s, (const double *)dout, 4, tmp);
+            if (rc) return rc;
+            std::memcpy(&res, tmp, sizeof(res));
+            if (res.index != ~0ull) done = true;
+        }
+        prefix += sums[b];
+    }
+    if (!done) {
+        // rounding left no index above the target: take the last one of
+        // non-zero weight
+        int last = nchunks - 1;
+        while (last > 0 && !(sums[last] > 0.0)) --last;
+        k_last_nonzero<Amp><<<1, 1024, 0, s->stream>>>((const Amp *)s->state, (uint64_t)last * len, len, dout);
+        s->stats.launches++;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_err(s, e, "last nonzero launch");
+        double tmp[4];
+        int rc = fetch(s, (const double *)dout, 4, tmp);
+        if (rc) return rc;
+        std::memcpy(&res, tmp, sizeof(res));
+        if (res.index == ~0ull) return set_err(s, QSIM_EZEROPROB, "no amplitude of non-zero weight");
+    }
+    const double mag = std::sqrt(res.re * res.re + res.im * res.im);
+    const unsigned grid = grid_for(N, 256, kSMs * 16);
+    k_write_basis<Amp><<<grid, 256, 0, s->stream>>>((Amp *)s->state, N, res.index, res.re / mag, res.im / mag);
+    s->stats.launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(s, e, "collapse to basis launch");
+    *outcome = res.index;
+    return QSIM_OK;
+}
+
+}  // namespace
+
+int run_probs_all(qsim *s, double *p1, double *norm2) {
+    return s->prec == QSIM_C128 ? probs_all_t<double2>(s, p1, norm2) : probs_all_t<float2>(s, p1, norm2);
+}
+int run_masked_sum(qsim *s, uint64_t mask, uint64_t value, double *out) {
+    return s->prec == QSIM_C128 ? masked_sum_t<double2>(s, mask, value, out)
+                                : masked_sum_t<float2>(s, mask, value, out);
+}
+int run_split_sum(qsim *s, int q, double *s0, double *s1) {
+    return s->prec == QSIM_C128 ? split_sum_t<double2>(s, q, s0, s1) : split_sum_t<float2>(s, q, s0, s1);
+}
+int run_collapse_mask(qsim *s, uint64_t mask, uint64_t value, double scale) {
+    return s->prec == QSIM_C128 ? collapse_t<double2>(s, mask, value, scale) : collapse_t<float2>(s, mask, value, scale);
+}
+int run_expect(qsim *s, const qsim_pauli *terms, int nterms, double *out) {
+    return s->prec == QSIM_C128 ? expect_t<double2>(s, terms, nterms, out) : expect_t<float2>(s, terms, nterms, out);
+}
+int run_measure_all(qsim *s, double u, uint64_t *outcome) {
+    return s->prec == QSIM_C128 ? measure_all_t<double2>(s, u, outcome) : measure_all_t<float2>(s, u, outcome);
+}
