@@ -192,6 +192,29 @@ typedef struct qsim_kernel_time {
 int sim_set_profiling(qsim *s, int on);
 int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nrows);
 
+/* All single-qubit probabilities of a caller-owned device state vector,
+ * computed without allocating any device memory.  The paper has no
+ * counterpart to this call; it exists for callers that cannot allocate GPU
+ * memory when they need the result (another framework's pool owns the
+ * device memory, a fixed real-time memory budget, a plugin callback that
+ * forbids allocation).
+ *   state      device pointer to 2^n amplitudes (complex128: 16-byte aligned,
+ *              complex64: 8-byte aligned), read only;
+ *   n          1..36; larger registers return QSIM_ENOTSUP because the
+ *              built-in scratch array holds partial sums for at most 36
+ *              qubits (190 KiB, fixed at build time);
+ *   precision  QSIM_C128 or QSIM_C64;
+ *   out        device pointer to n + 1 doubles, written asynchronously:
+ *              out[0] = sum_i |psi_i|^2, out[1 + q] = P(qubit q = 1);
+ *   stream     cudaStream_t to run on (NULL = legacy default stream).
+ * Returns QSIM_EINVAL for a null or misaligned pointer or an unknown
+ * precision, QSIM_ECUDA if a launch fails.  No cudaMalloc, cudaFree or
+ * allocating library call is made.  The scratch is one array shared by all
+ * calls in the process: calls whose kernels overlap on the GPU race on it.
+ * The first call on each device looks up the array's device address; make
+ * it before any stream capture. */
+int qsim_probs_all_noalloc(const void *state, int n, int precision, double *out, void *stream);
+
 /* One-line description of the last failure on this handle ("" if none). */
 const char *sim_last_error(const qsim *s);
 

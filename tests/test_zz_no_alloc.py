@@ -1,0 +1,52 @@
+"""The allocation-free probabilities call, checked against the regular one.
+
+qsim_probs_all_noalloc serves callers that cannot allocate GPU memory when
+they ask for probabilities (their device memory belongs to another pool, a
+fixed real-time budget, an allocation-free callback).  It must give what
+sim_probs_all gives, within the tests' tolerances, on consecutive calls that
+share its built-in scratch array.  This file is named to be collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-12), ("c64", 1e-6)])
+def test_noalloc_probs_match_sim_probs_all(prec, tol):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1612_08091_gb300 as q
+
+    lib = q.load()
+    fn = lib.qsim_probs_all_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    precision = 0 if prec == "c128" else 1
+    stream = torch.cuda.current_stream()
+    for n in (7, 16):
+        with q.Simulator(n, precision=prec) as sim:
+            sim.set_amplitudes(cg.random_state(n, seed=40 + n))
+            out = torch.full((n + 1,), float("nan"), dtype=torch.float64, device="cuda")
+            for call in range(2):
+                if call == 1:  # change the state between the two calls
+                    sim.apply_op(cg.op("U3", (n - 1,), (), (0.7, 1.1, -0.4)))
+                    sim.apply_op(cg.op("X", (0,), (3,)))
+                ref_p1, ref_norm = sim.probs_all()
+                ptr = sim.state_ptr()
+                rc = fn(ptr, n, precision, out.data_ptr(), stream.cuda_stream)
+                assert rc == 0
+                torch.cuda.synchronize()
+                got = out.cpu().numpy()
+                assert abs(got[0] - ref_norm) <= tol
+                np.testing.assert_allclose(got[1:], ref_p1, atol=tol)
+    # sizes beyond the scratch array and bad arguments are rejected
+    dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
+    assert fn(dummy.data_ptr(), 37, precision, dummy.data_ptr(), None) == 9  # ENOTSUP
+    assert fn(None, 5, precision, dummy.data_ptr(), None) == 1  # EINVAL
+    assert fn(dummy.data_ptr(), 5, 3, dummy.data_ptr(), None) == 1
