@@ -84,6 +84,11 @@ typedef struct qsim_opts {
     int fusion;             /* enum qsim_fusion; default QSIM_FUSE_NONE */
     int kmax;               /* largest fused block, 1..5; 0 = default 5 */
     int device;             /* CUDA device ordinal; the current device is used if < 0 */
+    int tc_terms;           /* complex64 tensor-core blocks: 3 = BF16x3 (default, 0 means 3),
+                               5 = five split products (gate split in three parts) */
+    int no_tensor_cores;    /* non-zero: run complex64 blocks on the CUDA cores */
+    int no_norm_tracking;   /* non-zero: do not rescale tensor-core block outputs by the
+                               previous block pass's input/output norm ratio */
 } qsim_opts;
 
 /* A Pauli-sum term c * P.  Qubit q of P is X if bit q is set in xmask only,

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -157,6 +158,46 @@ bool is_finite(double x) { return std::isfinite(x); }
 
 }  // namespace
 
+int stage_operand(qsim *s, const void *data, size_t bytes, unsigned char **dev) {
+    const size_t need = (bytes + 255) & ~(size_t)255;
+    if (need > kWsRingBytes) return set_err(s, QSIM_EINVAL, "block operand too large");
+    if (!s->stage_host) {
+        if (cudaMallocHost((void **)&s->stage_host, kWsRingBytes) != cudaSuccess) {
+            cudaGetLastError();
+            s->stage_host = nullptr;
+            return set_err(s, QSIM_ENOMEM, "pinned staging buffer");
+        }
+        s->stage_cursor = 0;
+    }
+    if (s->stage_cursor + need > kWsRingBytes) {
+        // every earlier copy out of the staging buffer must have run
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_err(s, e, "stream synchronize");
+        s->stage_cursor = 0;
+    }
+    std::memcpy(s->stage_host + s->stage_cursor, data, bytes);
+    unsigned char *d = (unsigned char *)s->ws + kWsRing + s->stage_cursor;
+    cudaError_t e = cudaMemcpyAsync(d, s->stage_host + s->stage_cursor, bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "operand copy");
+    s->stage_cursor += need;
+    *dev = d;
+    return QSIM_OK;
+}
+
+int check_device_errors(qsim *s) {
+    unsigned int *flag = (unsigned int *)((char *)s->ws + kWsErr);
+    cudaError_t e = cudaMemcpyAsync(s->pinned, flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_err(s, e, "error flag read");
+    unsigned int v;
+    std::memcpy(&v, s->pinned, sizeof(v));
+    if (v) {
+        cudaMemsetAsync(flag, 0, sizeof(unsigned int), s->stream);
+        return set_err(s, QSIM_ETIMEOUT, "a bounded device wait gave up (flag " + std::to_string(v) + ")");
+    }
+    return QSIM_OK;
+}
+
 extern "C" {
 
 int sim_workspace_bytes(int n, int precision, size_t *bytes) {
@@ -181,6 +222,13 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->prec = precision;
     s->fusion = o.fusion == QSIM_FUSE_MLP ? QSIM_FUSE_GREEDY : o.fusion;
     s->kmax = o.kmax;
+    if (o.tc_terms != 0 && o.tc_terms != 3 && o.tc_terms != 5) {
+        delete s;
+        return QSIM_EINVAL;
+    }
+    s->tc_terms = o.tc_terms == 5 ? 5 : 3;
+    s->tc_enabled = o.no_tensor_cores == 0;
+    s->norm_tracking = o.no_norm_tracking == 0;
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
@@ -226,6 +274,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
         s->pinned = nullptr;
         rc = QSIM_ENOMEM;
     }
+    if (!rc) rc = cuda_err(s, cudaMemsetAsync((char *)s->ws + kWsErr, 0, kWsErrBytes, s->stream), "clear flags");
     if (!rc) rc = launch_set_basis(s, 0);
     if (rc) {
         sim_destroy(s);
@@ -241,6 +290,7 @@ int sim_destroy(qsim *s) {
     if (s->own_state && s->state) cudaFree(s->state);
     if (s->own_ws && s->ws) cudaFree(s->ws);
     if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->stage_host) cudaFreeHost(s->stage_host);
     for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
     delete s;
     return QSIM_OK;
@@ -367,6 +417,7 @@ int sim_get_amplitudes(qsim *s, uint64_t offset, uint64_t count, double *out) {
     if (rc) return rc;
     if (!count) return QSIM_OK;
     cudaError_t e;
+    if ((rc = check_device_errors(s))) return rc;
     if (s->prec == QSIM_C128) {
         e = cudaMemcpyAsync(out, (const char *)s->state + offset * 16, count * 16, cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

@@ -57,6 +57,14 @@ struct qsim {
     double *pinned = nullptr;  // small pinned host buffer for results
     qsim_stats stats{};
     std::string err;
+    // tensor-core block path
+    bool tc_enabled = true;
+    int tc_terms = 3;
+    bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
+    uint64_t tc_passes = 0;
+    int tc_prev_grid = 0;
+    unsigned char *stage_host = nullptr;  // pinned staging for block operands
+    size_t stage_cursor = 0;
     // profiling: events around each launch, harvested on demand
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -79,7 +87,13 @@ constexpr size_t kWsResult = kWsPartials + kWsPartialsBytes;  // final values
 constexpr size_t kWsResultBytes = 64u << 10;            // 64 KiB
 constexpr size_t kWsChunk = kWsResult + kWsResultBytes; // measure-all chunk sums
 constexpr size_t kWsChunkBytes = 64u << 10;
-constexpr size_t kWsTotal = kWsChunk + kWsChunkBytes;
+constexpr size_t kWsErr = kWsChunk + kWsChunkBytes;     // device error flags
+constexpr size_t kWsErrBytes = 256;
+constexpr size_t kWsNorm = kWsErr + kWsErrBytes;        // block-pass norm partials
+constexpr size_t kWsNormBytes = 16u << 10;
+constexpr size_t kWsRing = kWsNorm + kWsNormBytes;      // block operand ring
+constexpr size_t kWsRingBytes = 16u << 20;
+constexpr size_t kWsTotal = kWsRing + kWsRingBytes;
 constexpr int kReduceBlocks = 608;                      // 4 per SM
 constexpr int kMaxChunks = 4096;
 
@@ -91,6 +105,12 @@ int cuda_err(qsim *s, cudaError_t e, const char *where);
 int launch_gate_plain(qsim *s, const GateRec &g);
 int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m);
 int launch_set_basis(qsim *s, uint64_t basis);
+
+// Copy a block operand record into the device ring (via pinned staging) on
+// the handle's stream; *dev receives its device address (api.cpp).
+int stage_operand(qsim *s, const void *data, size_t bytes, unsigned char **dev);
+// Read and clear the device error flags (synchronises the stream).
+int check_device_errors(qsim *s);
 
 // Fused tensor-core block (fused_kernel.cu).  Returns QSIM_ENOTSUP when the
 // block cannot run on the tensor-core kernel (caller falls back).

@@ -462,14 +462,15 @@ unsigned grid_for(uint64_t work, int threads, unsigned cap) {
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, cap));
 }
 
-// Copy `count` doubles from device to the pinned buffer and wait.
+// Copy `count` doubles from device to the pinned buffer and wait; also
+// reports a raised device error flag.
 int fetch(qsim *s, const double *dev, int count, double *host_out) {
     cudaError_t e = cudaMemcpyAsync(s->pinned, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, s->stream);
     if (e != cudaSuccess) return cuda_err(s, e, "result copy");
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_err(s, e, "stream synchronize");
     std::memcpy(host_out, s->pinned, sizeof(double) * count);
-    return QSIM_OK;
+    return check_device_errors(s);
 }
 
 int finalize(qsim *s, int nblocks, int V, double *host_out) {

@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("state", ctypes.c_void_p), ("state_bytes", ctypes.c_size_t),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("fusion", ctypes.c_int), ("kmax", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("tc_terms", ctypes.c_int), ("no_tensor_cores", ctypes.c_int),
+                ("no_norm_tracking", ctypes.c_int)]
 
 
 class Pauli(ctypes.Structure):
@@ -109,7 +110,8 @@ def _ints(seq):
 class Simulator:
     """An n-qubit register on the GPU behind the libqsim C ABI."""
 
-    def __init__(self, n, precision="c128", fusion="none", kmax=5, device=None, stream=None, torch_memory=True):
+    def __init__(self, n, precision="c128", fusion="none", kmax=5, device=None, stream=None, torch_memory=True,
+                 tc_terms=3, tensor_cores=True, norm_tracking=True):
         import torch
 
         if not torch.cuda.is_available():
@@ -124,6 +126,9 @@ class Simulator:
         opts.fusion = _FUSE[fusion]
         opts.kmax = int(kmax)
         opts.device = dev
+        opts.tc_terms = int(tc_terms)
+        opts.no_tensor_cores = 0 if tensor_cores else 1
+        opts.no_norm_tracking = 0 if norm_tracking else 1
         self._keep = []
         if torch_memory:
             ws = ctypes.c_size_t()
