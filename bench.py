@@ -347,8 +347,8 @@ def run_ours(args):
                        "precision": args.precision, "fusion": args.fusion, "kmax": args.kmax,
                        "gates_per_step": len(ops), "amp_updates_per_step": upd_step,
                        "passes_per_step": st["passes"] / args.steps,
-                       "l2": "inputs larger than L2 (state %d GiB vs 126 MiB L2)" % ((8 if args.precision == 'c64'
-                                                                                    else 16) << (n - 30)),
+                       "l2": "inputs larger than L2 (state %.2f GiB vs 126 MiB L2)" % (
+                           (8 if args.precision == "c64" else 16) * 2.0 ** n / 2 ** 30),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof,
             "kernel_times": kt,

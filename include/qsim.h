@@ -197,6 +197,50 @@ typedef struct qsim_kernel_time {
 int sim_set_profiling(qsim *s, int on);
 int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nrows);
 
+/* ---------------------------------------------------------------------------
+ * Batched variational sweep (not in the paper).  A batch of hardware-
+ * efficient-ansatz circuits of different sizes is evaluated in one
+ * persistent launch, captured in a CUDA graph and replayed per call.
+ * Circuit c has nqubits[c] qubits (2..24) and layers[c] layers; it starts in
+ * |0...0>, each layer applies RY(theta) to every qubit, RZ(phi) to every
+ * qubit, then CNOT(q -> q+1) for q = 0..n-2 in order.  The result is the
+ * transverse-field Ising energy of each circuit,
+ *   E = -sum_{i<n-1} <Z_i Z_{i+1}> - h sum_i <X_i>,
+ * accumulated in FP64 (amplitudes complex64, gate arithmetic FP32).
+ * --------------------------------------------------------------------------- */
+typedef struct qsim_batch qsim_batch;
+
+/* Device bytes a batch needs (angles, energies, queue, per-CTA buffers for
+ * circuits that do not fit in shared memory). */
+int sim_batch_workspace_bytes(int count, const int *nqubits, const int *layers, size_t *bytes);
+
+/* Create a batch.  stream: cudaStream_t to run on (NULL: the batch creates
+ * its own non-blocking stream; graph capture needs a non-default stream).
+ * workspace: caller-owned device memory of sim_batch_workspace_bytes bytes,
+ * 256-byte aligned, or NULL to let the library allocate.  Copies the size
+ * arrays.  QSIM_EINVAL for sizes outside the ranges above. */
+int sim_batch_create(int count, const int *nqubits, const int *layers, double h, void *stream, void *workspace,
+                     size_t workspace_bytes, qsim_batch **out);
+
+/* Evaluate all circuits.  angles (host): for each circuit in order, for each
+ * layer, n RY angles (qubit 0..n-1) then n RZ angles; energies (host):
+ * count doubles.  The first call captures the graph (angles H2D, queue
+ * reset, persistent kernel, energies D2H); later calls replay it. */
+int sim_batch_run(qsim_batch *b, const double *angles, double *energies);
+
+/* Time every candidate launch configuration (threads per CTA 256/512/1024,
+ * shared-memory threshold m = 12..14 qubits) on these angles, reps timed
+ * runs each after one warm-up, keep the fastest (median) and report it. */
+int sim_batch_autotune(qsim_batch *b, const double *angles, int reps, int *threads, int *m);
+
+/* Set the launch configuration by hand (QSIM_EINVAL if it cannot run this
+ * batch: 2^m must be <= 32 * threads, and the largest circuit must satisfy
+ * n - m <= m - 5). */
+int sim_batch_set_config(qsim_batch *b, int threads, int m);
+
+int sim_batch_destroy(qsim_batch *b);
+const char *sim_batch_last_error(const qsim_batch *b);
+
 /* All single-qubit probabilities of a caller-owned device state vector,
  * computed without allocating any device memory.  The paper has no
  * counterpart to this call; it exists for callers that cannot allocate GPU

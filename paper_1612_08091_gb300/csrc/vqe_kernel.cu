@@ -1,0 +1,593 @@
+// vqe_kernel.cu -- a batch of variational circuits in one persistent launch.
+//
+// Not a method of the paper: the serving pattern of many small
+// hardware-efficient-ansatz circuits (different qubit counts and depths)
+// evaluated together, each ending in the transverse-field Ising energy
+//   E = -sum_{i<n-1} <Z_i Z_{i+1}> - h sum_i <X_i>   (open chain).
+// A circuit starts in |0...0> and runs L layers of RY(theta_q) on every
+// qubit, RZ(phi_q) on every qubit, then CNOT(q -> q+1) for q = 0..n-2.
+//
+// Per layer the two rotations on a qubit fuse into U_q = RZ(phi) RY(theta)
+// (they commute with the rotations on the other qubits), and the CNOT
+// ladder is one permutation: applied in order it maps |b> to |b'> with
+// b'_k = b_0 ^ ... ^ b_k, i.e. psi'[y] = psi[y ^ (y << 1) mod 2^n].
+//
+// One persistent launch: every CTA takes circuit ids from an atomic counter
+// (largest circuits first) until the batch is done; there is no waiting on
+// other CTAs.  A circuit of n <= m qubits (m = 12..14, tuned) lives in the
+// CTA's shared memory; a larger one lives in a per-CTA pair of global
+// buffers and is processed in cache-blocked tiles of 2^m amplitudes: one
+// tile pass applies the gates on qubits 0..m-1, a second (tiles made of runs
+// of 2^(m-h) amplitudes times the h = n-m top qubits) applies the gates on
+// the top qubits, and a third applies the CNOT permutation into the other
+// buffer.  Amplitudes are complex64 in FP32 arithmetic; energies accumulate
+// per thread in FP32 over a few terms and in FP64 beyond.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+#include "common.cuh"
+
+using namespace qsim_dev;
+
+namespace {
+
+// amplitudes per thread held in registers for the in-place permutation
+template <int T> struct RegAmps { static constexpr int value = T >= 1024 ? 16 : 32; };
+
+struct VqeArgs {
+    const int *order;
+    const int *nq;
+    const int *nl;
+    const long long *aoff;
+    const double *angles;
+    double *energies;
+    unsigned int *counter;
+    int count;
+    int m;            // qubits held in shared memory
+    float2 *gbuf;     // per-CTA global buffers (two of gstride amplitudes each)
+    size_t gstride;
+    double h;
+};
+
+struct Gate1 {
+    float2 u00, u01, u10, u11;
+};
+
+// U = RZ(phi) RY(theta):
+// [[c e^{-i phi/2}, -s e^{-i phi/2}], [s e^{i phi/2}, c e^{i phi/2}]]
+__device__ __forceinline__ Gate1 make_gate(double theta, double phi) {
+    float s, c, sp, cp;
+    sincosf((float)(0.5 * theta), &s, &c);
+    sincosf((float)(0.5 * phi), &sp, &cp);
+    Gate1 g;
+    g.u00 = make_float2(c * cp, -c * sp);
+    g.u01 = make_float2(-s * cp, s * sp);
+    g.u10 = make_float2(s * cp, s * sp);
+    g.u11 = make_float2(c * cp, c * sp);
+    return g;
+}
+
+__device__ __forceinline__ void apply_pair(float2 *x, unsigned i0, unsigned i1, const Gate1 &g) {
+    const float2 a = x[i0], b = x[i1];
+    float2 na = cmul(g.u00, a);
+    na = cfma(g.u01, b, na);
+    float2 nb = cmul(g.u10, a);
+    nb = cfma(g.u11, b, nb);
+    x[i0] = na;
+    x[i1] = nb;
+}
+
+// Gate on bit `bit` of a 2^k-amplitude array in shared memory.
+__device__ __forceinline__ void gate_smem(float2 *x, int k, int bit, const Gate1 &g) {
+    const unsigned half = 1u << (k - 1);
+    const unsigned lowmask = (1u << bit) - 1u;
+    for (unsigned p = threadIdx.x; p < half; p += blockDim.x) {
+        const unsigned i0 = ((p & ~lowmask) << 1) | (p & lowmask);
+        apply_pair(x, i0, i0 | (1u << bit), g);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned ladder_src(unsigned y, unsigned mask) { return (y ^ (y << 1)) & mask; }
+
+__device__ double block_sum_d(double v, double *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// ZZ part of a 2^k chunk whose global index bits above k are `hi` (n qubits):
+// sum_i |psi_i|^2 * ((n-1) - 2 popc((i ^ i>>1) & (2^(n-1)-1))).
+__device__ float zz_chunk(const float2 *x, int k, unsigned long long hi, int n) {
+    const unsigned long long m1 = (n >= 2) ? ((1ull << (n - 1)) - 1ull) : 0ull;
+    float acc = 0.f;
+    for (unsigned i = threadIdx.x; i < (1u << k); i += blockDim.x) {
+        const unsigned long long gi = hi | i;
+        const float w = norm2(x[i]);
+        acc += w * (float)((n - 1) - 2 * __popcll((gi ^ (gi >> 1)) & m1));
+    }
+    return acc;
+}
+
+// sum over pairs on bit `bit` of 2 Re(conj(a) b) inside a 2^k array
+__device__ float x_chunk(const float2 *x, int k, int bit) {
+    const unsigned half = 1u << (k - 1);
+    const unsigned lowmask = (1u << bit) - 1u;
+    float acc = 0.f;
+    for (unsigned p = threadIdx.x; p < half; p += blockDim.x) {
+        const unsigned i0 = ((p & ~lowmask) << 1) | (p & lowmask);
+        const float2 a = x[i0], b = x[i0 | (1u << bit)];
+        acc += 2.f * (a.x * b.x + a.y * b.y);
+    }
+    return acc;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
+    constexpr int kRegAmps = RegAmps<T>::value;
+    extern __shared__ float2 sm[];
+    __shared__ int s_idx;
+    __shared__ double s_red[32];
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(A.counter, 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= A.count) break;
+        const int c = A.order[idx];
+        const int n = A.nq[c], L = A.nl[c];
+        const double *ang = A.angles + A.aoff[c];
+        const unsigned N = 1u << n;
+        double zz = 0.0, xx = 0.0;
+        if (n <= A.m) {
+            // --- shared-memory resident circuit -------------------------------
+            for (unsigned i = threadIdx.x; i < N; i += T) sm[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+            __syncthreads();
+            for (int l = 0; l < L; ++l) {
+                for (int q = 0; q < n; ++q) gate_smem(sm, n, q, make_gate(ang[2 * l * n + q], ang[2 * l * n + n + q]));
+                // CNOT ladder as one permutation through registers
+                float2 v[kRegAmps];
+#pragma unroll
+                for (int j = 0; j < kRegAmps; ++j) {
+                    const unsigned y = threadIdx.x + (unsigned)j * T;
+                    if (y < N) v[j] = sm[ladder_src(y, N - 1)];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < kRegAmps; ++j) {
+                    const unsigned y = threadIdx.x + (unsigned)j * T;
+                    if (y < N) sm[y] = v[j];
+                }
+                __syncthreads();
+            }
+            zz = (double)zz_chunk(sm, n, 0ull, n);
+            for (int q = 0; q < n; ++q) xx += (double)x_chunk(sm, n, q);
+        } else {
+            // --- global-memory circuit, cache-blocked tiles of 2^m --------------
+            const int m = A.m, h = n - m, lowrun = m - h;  // lowrun >= 5 by construction
+            float2 *b0 = A.gbuf + (size_t)blockIdx.x * 2 * A.gstride;
+            float2 *b1 = b0 + A.gstride;
+            for (unsigned i = threadIdx.x; i < N; i += T) b0[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+            __syncthreads();
+            const unsigned nchunks = 1u << h;
+            for (int l = 0; l < L; ++l) {
+                const double *al = ang + 2 * l * n;
+                // qubits 0..m-1: contiguous chunks
+                for (unsigned ch = 0; ch < nchunks; ++ch) {
+                    float2 *g = b0 + ((size_t)ch << m);
+                    for (unsigned i = threadIdx.x; i < (1u << m); i += T) sm[i] = g[i];
+                    __syncthreads();
+                    for (int q = 0; q < m; ++q) gate_smem(sm, m, q, make_gate(al[q], al[n + q]));
+                    for (unsigned i = threadIdx.x; i < (1u << m); i += T) g[i] = sm[i];
+                    __syncthreads();
+                }
+                // qubits m..n-1: tiles = runs of 2^lowrun amplitudes x the h top qubits
+                for (unsigned t = 0; t < nchunks; ++t) {
+                    for (unsigned e = threadIdx.x; e < (1u << m); e += T) {
+                        const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
+                        sm[e] = b0[lo | (t << lowrun) | (top << m)];
+                    }
+                    __syncthreads();
+                    for (int q = m; q < n; ++q) gate_smem(sm, m, lowrun + (q - m), make_gate(al[q], al[n + q]));
+                    for (unsigned e = threadIdx.x; e < (1u << m); e += T) {
+                        const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
+                        b0[lo | (t << lowrun) | (top << m)] = sm[e];
+                    }
+                    __syncthreads();
+                }
+                // CNOT ladder into the other buffer
+                for (unsigned y = threadIdx.x; y < N; y += T) b1[y] = b0[ladder_src(y, N - 1)];
+                __syncthreads();
+                float2 *tmp = b0;
+                b0 = b1;
+                b1 = tmp;
+            }
+            // energy: ZZ and X on qubits < m per chunk, X on the top qubits per tile
+            float zf = 0.f, xf = 0.f;
+            for (unsigned ch = 0; ch < nchunks; ++ch) {
+                const float2 *g = b0 + ((size_t)ch << m);
+                for (unsigned i = threadIdx.x; i < (1u << m); i += T) sm[i] = g[i];
+                __syncthreads();
+                zf += zz_chunk(sm, m, (unsigned long long)ch << m, n);
+                for (int q = 0; q < m; ++q) xf += x_chunk(sm, m, q);
+                __syncthreads();
+            }
+            for (unsigned t = 0; t < nchunks; ++t) {
+                for (unsigned e = threadIdx.x; e < (1u << m); e += T) {
+                    const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
+                    sm[e] = b0[lo | (t << lowrun) | (top << m)];
+                }
+                __syncthreads();
+                for (int q = m; q < n; ++q) xf += x_chunk(sm, m, lowrun + (q - m));
+                __syncthreads();
+            }
+            zz = (double)zf;
+            xx = (double)xf;
+        }
+        const double zzs = block_sum_d(zz, s_red);
+        const double xxs = block_sum_d(xx, s_red);
+        if (threadIdx.x == 0) A.energies[c] = -zzs - A.h * xxs;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side: the batch object, its graph and the tile autotuner
+// ---------------------------------------------------------------------------
+struct qsim_batch {
+    int count = 0, nmax = 0, nmin = 0;
+    long long nangles = 0;
+    double h = 0.7;
+    std::vector<int> nq, nl, order;
+    std::vector<long long> aoff;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, sms = 0;
+    // device memory
+    unsigned char *mem = nullptr;
+    size_t mem_bytes = 0;
+    bool own_mem = false;
+    double *d_angles = nullptr, *d_energies = nullptr;
+    int *d_order = nullptr, *d_nq = nullptr, *d_nl = nullptr;
+    long long *d_aoff = nullptr;
+    unsigned int *d_counter = nullptr;
+    float2 *d_gbuf = nullptr;
+    size_t gstride = 0;
+    int max_grid = 0;
+    // pinned staging
+    double *h_angles = nullptr, *h_energies = nullptr;
+    // tuned launch configuration and its graph
+    int threads = 512, m = 13, grid = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::string err;
+};
+
+namespace {
+
+constexpr int kCandidates[][2] = {{256, 12}, {256, 13}, {512, 12}, {512, 13}, {512, 14}, {1024, 13}, {1024, 14}};
+
+int reg_amps(int threads) { return threads == 256 ? RegAmps<256>::value : threads == 512 ? RegAmps<512>::value
+                                                                                       : RegAmps<1024>::value; }
+
+typedef void (*VqeKernel)(const VqeArgs);
+VqeKernel kernel_for(int threads) {
+    return threads == 256 ? k_vqe_batch<256> : threads == 512 ? k_vqe_batch<512> : k_vqe_batch<1024>;
+}
+
+bool config_valid(const qsim_batch *b, int threads, int m) {
+    if ((1 << m) > reg_amps(threads) * threads) return false;  // in-place permutation through registers
+    if (b->nmax > m && (b->nmax - m) > m - 5) return false;  // top-qubit tiles need runs of >= 32
+    return true;
+}
+
+int occupancy(const qsim_batch *b, int threads, int m, int *grid) {
+    const size_t smem = (size_t)8 << m;
+    VqeKernel k = kernel_for(threads);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return QSIM_ECUDA;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e != cudaSuccess || per_sm < 1) return QSIM_ENOTSUP;
+    *grid = std::min(b->sms * per_sm, b->max_grid);
+    return QSIM_OK;
+}
+
+int berr(qsim_batch *b, int code, const std::string &msg) {
+    b->err = msg;
+    return code;
+}
+
+int launch(qsim_batch *b, int threads, int m, int grid) {
+    VqeArgs a;
+    a.order = b->d_order;
+    a.nq = b->d_nq;
+    a.nl = b->d_nl;
+    a.aoff = b->d_aoff;
+    a.angles = b->d_angles;
+    a.energies = b->d_energies;
+    a.counter = b->d_counter;
+    a.count = b->count;
+    a.m = m;
+    a.gbuf = b->d_gbuf;
+    a.gstride = b->gstride;
+    a.h = b->h;
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream);
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    kernel_for(threads)<<<grid, threads, (size_t)8 << m, b->stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    return QSIM_OK;
+}
+
+// Capture angles H2D -> queue reset -> persistent kernel -> energies D2H.
+int build_graph(qsim_batch *b) {
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    int grid = 0;
+    int rc = occupancy(b, b->threads, b->m, &grid);
+    if (rc) return berr(b, rc, "occupancy query failed");
+    b->grid = grid;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    cudaMemcpyAsync(b->d_angles, b->h_angles, sizeof(double) * b->nangles, cudaMemcpyHostToDevice, b->stream);
+    rc = launch(b, b->threads, b->m, grid);
+    cudaMemcpyAsync(b->h_energies, b->d_energies, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->stream);
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    return QSIM_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+int sim_batch_workspace_bytes(int count, const int *nqubits, const int *layers, size_t *bytes) {
+    if (count < 1 || !nqubits || !layers || !bytes) return QSIM_EINVAL;
+    long long nang = 0;
+    int nmax = 0;
+    for (int i = 0; i < count; ++i) {
+        if (nqubits[i] < 2 || nqubits[i] > 24 || layers[i] < 0) return QSIM_EINVAL;
+        nang += 2LL * nqubits[i] * layers[i];
+        nmax = std::max(nmax, nqubits[i]);
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = kSMs;
+    const size_t max_grid = (size_t)sms * 4;
+    const size_t gstride = nmax > 12 ? ((size_t)1 << nmax) : 0;
+    size_t s = align256(sizeof(double) * nang) + align256(sizeof(double) * count) + 3 * align256(sizeof(int) * count) +
+               align256(sizeof(long long) * count) + 256 + max_grid * 2 * gstride * sizeof(float2);
+    *bytes = s;
+    return QSIM_OK;
+}
+
+int sim_batch_create(int count, const int *nqubits, const int *layers, double h, void *stream, void *workspace,
+                     size_t workspace_bytes, qsim_batch **out) {
+    if (!out) return QSIM_EINVAL;
+    *out = nullptr;
+    size_t need = 0;
+    int rc = sim_batch_workspace_bytes(count, nqubits, layers, &need);
+    if (rc) return rc;
+    if (!std::isfinite(h)) return QSIM_ENONFINITE;
+    qsim_batch *b = new (std::nothrow) qsim_batch();
+    if (!b) return QSIM_ENOMEM;
+    b->count = count;
+    b->h = h;
+    b->nq.assign(nqubits, nqubits + count);
+    b->nl.assign(layers, layers + count);
+    b->aoff.resize(count);
+    long long off = 0;
+    b->nmax = 0;
+    b->nmin = 64;
+    for (int i = 0; i < count; ++i) {
+        b->aoff[i] = off;
+        off += 2LL * nqubits[i] * layers[i];
+        b->nmax = std::max(b->nmax, nqubits[i]);
+        b->nmin = std::min(b->nmin, nqubits[i]);
+    }
+    b->nangles = off;
+    // largest (most work) first
+    b->order.resize(count);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        const double wx = std::ldexp((double)(b->nl[x] + 1), b->nq[x]);
+        const double wy = std::ldexp((double)(b->nl[y] + 1), b->nq[y]);
+        return wx > wy;
+    });
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->max_grid = b->sms * 4;
+    b->gstride = b->nmax > 12 ? ((size_t)1 << b->nmax) : 0;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return QSIM_ECUDA;
+        }
+        b->own_stream = true;
+    }
+    if (workspace) {
+        if (workspace_bytes < need || ((uintptr_t)workspace & 255u)) {
+            sim_batch_destroy(b);
+            return QSIM_EINVAL;
+        }
+        b->mem = (unsigned char *)workspace;
+    } else {
+        if (cudaMalloc((void **)&b->mem, need) != cudaSuccess) {
+            cudaGetLastError();
+            b->mem = nullptr;
+            sim_batch_destroy(b);
+            return QSIM_ENOMEM;
+        }
+        b->own_mem = true;
+    }
+    b->mem_bytes = need;
+    unsigned char *p = b->mem;
+    b->d_angles = (double *)p;
+    p += align256(sizeof(double) * b->nangles);
+    b->d_energies = (double *)p;
+    p += align256(sizeof(double) * count);
+    b->d_order = (int *)p;
+    p += align256(sizeof(int) * count);
+    b->d_nq = (int *)p;
+    p += align256(sizeof(int) * count);
+    b->d_nl = (int *)p;
+    p += align256(sizeof(int) * count);
+    b->d_aoff = (long long *)p;
+    p += align256(sizeof(long long) * count);
+    b->d_counter = (unsigned int *)p;
+    p += 256;
+    b->d_gbuf = (float2 *)p;
+    if (cudaMallocHost((void **)&b->h_angles, sizeof(double) * std::max<long long>(1, b->nangles)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_energies, sizeof(double) * count) != cudaSuccess) {
+        cudaGetLastError();
+        sim_batch_destroy(b);
+        return QSIM_ENOMEM;
+    }
+    cudaMemcpyAsync(b->d_order, b->order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(b->d_nq, b->nq.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(b->d_nl, b->nl.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(b->d_aoff, b->aoff.data(), sizeof(long long) * count, cudaMemcpyHostToDevice, b->stream);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        sim_batch_destroy(b);
+        return QSIM_ECUDA;
+    }
+    // default configuration: the largest valid shared-memory threshold
+    b->threads = 512;
+    b->m = 0;
+    for (int m = 14; m >= 12; --m)
+        if (config_valid(b, 512, m)) {
+            b->m = m;
+            break;
+        }
+    if (!b->m) {
+        sim_batch_destroy(b);
+        return QSIM_ENOTSUP;
+    }
+    *out = b;
+    return QSIM_OK;
+}
+
+int sim_batch_destroy(qsim_batch *b) {
+    if (!b) return QSIM_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->own_mem && b->mem) cudaFree(b->mem);
+    if (b->h_angles) cudaFreeHost(b->h_angles);
+    if (b->h_energies) cudaFreeHost(b->h_energies);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return QSIM_OK;
+}
+
+int sim_batch_run(qsim_batch *b, const double *angles, double *energies) {
+    if (!b || (!angles && b->nangles) || !energies) return QSIM_EINVAL;
+    for (long long i = 0; i < b->nangles; ++i)
+        if (!std::isfinite(angles[i])) return berr(b, QSIM_ENONFINITE, "non-finite angle");
+    if (!b->graph) {
+        int rc = build_graph(b);
+        if (rc) return rc;
+    }
+    std::memcpy(b->h_angles, angles, sizeof(double) * b->nangles);
+    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    std::memcpy(energies, b->h_energies, sizeof(double) * b->count);
+    return QSIM_OK;
+}
+
+int sim_batch_autotune(qsim_batch *b, const double *angles, int reps, int *threads_out, int *m_out) {
+    if (!b || (!angles && b->nangles) || reps < 1) return QSIM_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(b->d_angles, angles, sizeof(double) * b->nangles, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt = b->threads, bm = b->m;
+    for (const auto &cand : kCandidates) {
+        const int threads = cand[0], m = cand[1];
+        if (!config_valid(b, threads, m)) continue;
+        int grid = 0;
+        if (occupancy(b, threads, m, &grid)) continue;
+        std::vector<float> t;
+        for (int r = 0; r <= reps; ++r) {
+            cudaEventRecord(e0, b->stream);
+            int rc = launch(b, threads, m, grid);
+            cudaEventRecord(e1, b->stream);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) t.push_back(ms);  // first run is a warm-up
+        }
+        if ((int)t.size() != reps) continue;
+        std::sort(t.begin(), t.end());
+        const float med = t[t.size() / 2];
+        if (med < best) {
+            best = med;
+            bt = threads;
+            bm = m;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    b->threads = bt;
+    b->m = bm;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (threads_out) *threads_out = bt;
+    if (m_out) *m_out = bm;
+    return QSIM_OK;
+}
+
+int sim_batch_set_config(qsim_batch *b, int threads, int m) {
+    if (!b) return QSIM_EINVAL;
+    if (threads != 256 && threads != 512 && threads != 1024) return berr(b, QSIM_EINVAL, "threads must be 256/512/1024");
+    if (m < 12 || m > 14 || !config_valid(b, threads, m)) return berr(b, QSIM_EINVAL, "invalid tile configuration");
+    b->threads = threads;
+    b->m = m;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return QSIM_OK;
+}
+
+const char *sim_batch_last_error(const qsim_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+}  // extern "C"

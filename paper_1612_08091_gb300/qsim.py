@@ -88,12 +88,20 @@ def load():
         "sim_get_stats": [P, ctypes.POINTER(Stats)],
         "sim_reset_stats": [P],
         "sim_set_profiling": [P, I],
+        "sim_batch_workspace_bytes": [I, IP, IP, ctypes.POINTER(ctypes.c_size_t)],
+        "sim_batch_create": [I, IP, IP, D, P, P, ctypes.c_size_t, ctypes.POINTER(P)],
+        "sim_batch_run": [P, DP, DP],
+        "sim_batch_autotune": [P, DP, I, IP, IP],
+        "sim_batch_set_config": [P, I, I],
+        "sim_batch_destroy": [P],
         "sim_get_kernel_times": [P, ctypes.POINTER(KernelTime), I, IP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.sim_batch_last_error.argtypes = [P]
+    lib.sim_batch_last_error.restype = ctypes.c_char_p
     lib.sim_last_error.argtypes = [P]
     lib.sim_last_error.restype = ctypes.c_char_p
     lib.qsim_build_info.argtypes = []
@@ -277,3 +285,88 @@ class Simulator:
         self._check(self.lib.sim_get_kernel_times(self.h, rows, 16, ctypes.byref(nr)), "sim_get_kernel_times")
         return {rows[i].name.decode(): {"launches": rows[i].launches, "total_ms": rows[i].total_ms,
                                         "alg_bytes": rows[i].alg_bytes} for i in range(min(nr.value, 16))}
+
+
+class Batch:
+    """A batch of hardware-efficient-ansatz circuits evaluated in one
+    persistent launch (sim_batch_* in the C ABI)."""
+
+    def __init__(self, nqubits, layers, h=0.7, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqsim needs a CUDA GPU; none is visible")
+        self.lib = load()
+        self.count = len(nqubits)
+        self.nq = np.ascontiguousarray(nqubits, dtype=np.int32)
+        self.nl = np.ascontiguousarray(layers, dtype=np.int32)
+        self.nangles = int(np.sum(2 * self.nq.astype(np.int64) * self.nl))
+        ip = ctypes.POINTER(ctypes.c_int)
+        nbytes = ctypes.c_size_t()
+        rc = self.lib.sim_batch_workspace_bytes(self.count, self.nq.ctypes.data_as(ip), self.nl.ctypes.data_as(ip),
+                                                ctypes.byref(nbytes))
+        if rc:
+            raise QsimError(rc, "sim_batch_workspace_bytes", "")
+        self._ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        self._stream = stream if stream is not None else torch.cuda.Stream()
+        h_ = ctypes.c_void_p()
+        rc = self.lib.sim_batch_create(self.count, self.nq.ctypes.data_as(ip), self.nl.ctypes.data_as(ip), float(h),
+                                       self._stream.cuda_stream, self._ws.data_ptr(), self._ws.numel(),
+                                       ctypes.byref(h_))
+        if rc:
+            raise QsimError(rc, "sim_batch_create", "")
+        self.h = h_
+
+    def _check(self, rc, call):
+        if rc:
+            raise QsimError(rc, call, self.lib.sim_batch_last_error(self.h).decode())
+
+    def _angles(self, angles):
+        a = np.ascontiguousarray(angles, dtype=np.float64)
+        if a.size != self.nangles:
+            raise ValueError("expected %d angles, got %d" % (self.nangles, a.size))
+        return a
+
+    def run(self, angles):
+        a = self._angles(angles)
+        out = np.empty(self.count, dtype=np.float64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.sim_batch_run(self.h, a.ctypes.data_as(dp), out.ctypes.data_as(dp)), "sim_batch_run")
+        return out
+
+    def autotune(self, angles, reps=3):
+        a = self._angles(angles)
+        t, m = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.sim_batch_autotune(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(reps),
+                                                ctypes.byref(t), ctypes.byref(m)), "sim_batch_autotune")
+        return t.value, m.value
+
+    def set_config(self, threads, m):
+        self._check(self.lib.sim_batch_set_config(self.h, int(threads), int(m)), "sim_batch_set_config")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def hea_angles(circuits):
+    """Flatten circuitgen.hea_batch entries into the sim_batch_run layout."""
+    parts = []
+    for c in circuits:
+        for l in range(c["L"]):
+            parts.append(np.asarray(c["ry"][l], dtype=np.float64))
+            parts.append(np.asarray(c["rz"][l], dtype=np.float64))
+    return np.concatenate(parts) if parts else np.zeros(0)
