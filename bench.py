@@ -81,6 +81,8 @@ def dist_env():
 
 
 def max_over_ranks(x, world, device=None):
+    """Max of a host scalar over all ranks (the timed region of the slowest
+    rank).  Works with the nccl (device tensor) and gloo (CPU) backends."""
     if world == 1:
         return x
     import torch
@@ -89,6 +91,13 @@ def max_over_ranks(x, world, device=None):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds_per_rank, world, device=None):
+    """Replicas: every rank processes the same number of units; the job's
+    throughput is all ranks' units over the slowest rank's time."""
+    t = max_over_ranks(seconds_per_rank, world, device)
+    return units_per_rank * world / t, t
 
 
 # ---------------------------------------------------------------------------
@@ -281,11 +290,8 @@ def run_ours(args):
     kt = sim.kernel_times()
     st = sim.stats()
     sim.set_profiling(False)
-    dev_s = max_over_ranks(dev_s, world, device)
-    host_s = max_over_ranks(host_s, world, device)
-    total_upd = upd_step * args.steps * world
-    value = total_upd / dev_s
-    e2e = total_upd / host_s
+    value, dev_s = job_throughput(upd_step * args.steps, dev_s, world, device)
+    e2e, host_s = job_throughput(upd_step * args.steps, host_s, world, device)
 
     peak, peak_kind = measured_peaks()
     dom_name, dom = max(kt.items(), key=lambda kv: kv[1]["total_ms"]) if kt else (None, None)
@@ -300,7 +306,7 @@ def run_ours(args):
                 "alg_bytes_per_launch": per_launch_bytes, "launches_per_step": dom["launches"] / args.steps,
                 "share_of_gate_time": dom["total_ms"] / step_ms_total if step_ms_total else None}
 
-    plain = None
+    plain = plain_df = None
     if not args.no_plain and rank == 0 and args.plain_layers > 0:
         sim.close()
         torch.cuda.empty_cache()
@@ -309,25 +315,32 @@ def run_ours(args):
         for layer in range(args.plain_layers):
             cnt += n + len(range(layer % 2, n - 1, 2))
         sample = ops[:cnt]
-        with q.Simulator(n, precision="c128", fusion="none", stream=stream) as ps:
-            ps.run(sample[: n])  # warm-up on the same register
-            ps.flush()
-            torch.cuda.synchronize()
-            ps.set_profiling(True)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ps.run(sample)
-            ps.flush()
-            b.record(stream)
-            torch.cuda.synchronize()
-            pkt = ps.kernel_times()
-        ps_s = a.elapsed_time(b) / 1e3
-        plain = {"value": amp_updates(sample, n) / ps_s, "unit": UNIT, "precision": "c128", "fusion": "none",
-                 "sample": "first %d layers (%d gates) of the same %d-qubit circuit, one launch per gate"
-                           % (args.plain_layers, len(sample), n),
-                 "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
-                                 "GB/s": v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9} for k, v in pkt.items()}}
+        def plain_sample(df):
+            with q.Simulator(n, precision="c128", fusion="none", stream=stream, c128_df=df) as ps:
+                ps.run(sample[: n])  # warm-up on the same register
+                ps.flush()
+                torch.cuda.synchronize()
+                ps.set_profiling(True)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ps.run(sample)
+                ps.flush()
+                b.record(stream)
+                torch.cuda.synchronize()
+                pkt = ps.kernel_times()
+            ps_s = a.elapsed_time(b) / 1e3
+            torch.cuda.empty_cache()
+            return {"value": amp_updates(sample, n) / ps_s, "unit": UNIT, "precision": "c128",
+                    "arithmetic": "double-float (fp32 pairs, ~2^-45 relative)" if df else "fp64",
+                    "fusion": "none",
+                    "sample": "first %d layers (%d gates) of the same %d-qubit circuit, one launch per gate"
+                              % (args.plain_layers, len(sample), n),
+                    "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
+                                    "GB/s": v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9} for k, v in pkt.items()}}
+
+        plain = plain_sample(False)
+        plain_df = plain_sample(True)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -353,6 +366,7 @@ def run_ours(args):
             "roofline": roof,
             "kernel_times": kt,
             "plain_c128": plain,
+            "plain_c128_double_float": plain_df,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes},
             "clocks": clk,

@@ -89,6 +89,9 @@ typedef struct qsim_opts {
     int no_tensor_cores;    /* non-zero: run complex64 blocks on the CUDA cores */
     int no_norm_tracking;   /* non-zero: do not rescale tensor-core block outputs by the
                                previous block pass's input/output norm ratio */
+    int c128_double_float;  /* non-zero: complex128 one-qubit dense, diagonal and phase gates
+                               compute in FP32 pairs (about 2^-45 relative error per result,
+                               one FP64 add per component) instead of FP64 arithmetic */
 } qsim_opts;
 
 /* A Pauli-sum term c * P.  Qubit q of P is X if bit q is set in xmask only,
@@ -174,8 +177,8 @@ int sim_state_ptr(qsim *s, void **dev_ptr);
 int sim_set_stream(qsim *s, void *stream);
 
 /* Choose the fusion mode (enum qsim_fusion) and block width kmax (1..5).
- * For QSIM_FUSE_MLP the cost model must have been loaded with
- * sim_planner_load_mlp.  Flushes the queue first. */
+ * QSIM_FUSE_MLP uses the cost model loaded with sim_set_cost_model (greedy
+ * fusion if none is loaded).  Flushes the queue first. */
 int sim_set_fusion(qsim *s, int mode, int kmax);
 
 int sim_get_stats(const qsim *s, qsim_stats *out);
@@ -194,8 +197,53 @@ typedef struct qsim_kernel_time {
     double alg_bytes;  /* algorithmic HBM bytes of those launches */
 } qsim_kernel_time;
 
+/* on: 0 off, 1 per-class times, 2 per-class times and per-launch records
+ * (features of the planned item and its duration) for sim_get_item_times. */
 int sim_set_profiling(qsim *s, int on);
 int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nrows);
+
+/* ---------------------------------------------------------------------------
+ * Learned fusion planner (not in the paper).  With profiling mode 2 the
+ * library records, for every gate or block launch, 16 features of the
+ * planned item and its event-timed duration; a cost model trained on these
+ * records (sim_mlp_*) predicts the log of a launch's duration in ms, and
+ * QSIM_FUSE_MLP plans with it: greedy blocks for kmax = 1..5, each block
+ * either fused or left as plain gates, whichever is predicted faster; the
+ * plan with the lowest predicted total is executed.  Without a loaded model
+ * QSIM_FUSE_MLP falls back to greedy fusion.
+ * Feature order: n/32, bytes per amplitude/16, fused, on tensor cores,
+ * width/5, gates/32, plain dense, plain phase, plain diagonal, plain X,
+ * controls/8, log2(fraction of amplitudes touched)/8, lowest qubit/32,
+ * highest qubit/32, qubits below 5 /5, 1.
+ * --------------------------------------------------------------------------- */
+
+/* Copy out (and clear) the per-launch records: feats holds 16 floats per
+ * record, ms one float; *nitems receives the number of records available
+ * (records are cleared only when all of them fit in max_items). */
+int sim_get_item_times(qsim *s, float *feats, float *ms, int max_items, int *nitems);
+
+/* Load the cost model (parameter layout of sim_mlp_*: W1[h][16], b1[h],
+ * W2[h][h], b2[h], w3[h], b3); count 0 unloads it.  Copied. */
+int sim_set_cost_model(qsim *s, const float *params, int count, int hidden);
+
+/* Predicted duration (ms) of the last plan made by the learned planner. */
+int sim_plan_stats(qsim *s, double *predicted_ms);
+
+/* The cost model's network, trained on the GPU by the library's own
+ * forward, backward and Adam kernels (FP32, deterministic). */
+typedef struct qsim_mlp qsim_mlp;
+int sim_mlp_param_count(int hidden);
+int sim_mlp_create(int hidden, unsigned long long seed, void *stream, qsim_mlp **out);
+int sim_mlp_destroy(qsim_mlp *m);
+int sim_mlp_get_params(qsim_mlp *m, float *out, int count);
+int sim_mlp_set_params(qsim_mlp *m, const float *in, int count);
+/* Y[i] = network(X[i*16 .. i*16+15]); host arrays. */
+int sim_mlp_forward(qsim_mlp *m, const float *X, int n, float *Y);
+/* Gradient (parameter layout) of the mean squared error over n samples. */
+int sim_mlp_gradient(qsim_mlp *m, const float *X, const float *T, int n, float *grads, float *loss);
+/* Adam (lr, betas 0.9/0.999) on the mean squared error for `epochs` passes
+ * in minibatches of `batch`; *loss = mean squared error of the last epoch. */
+int sim_mlp_train(qsim_mlp *m, const float *X, const float *T, int n, int epochs, int batch, float lr, float *loss);
 
 /* ---------------------------------------------------------------------------
  * Batched variational sweep (not in the paper).  A batch of hardware-

@@ -77,8 +77,14 @@ int harvest(qsim *s) {
         c.launches++;
         c.ms += ms;
         c.bytes += p.bytes;
+        if (p.feat >= 0) {
+            s->item_feats.insert(s->item_feats.end(), s->pending_feats.begin() + p.feat,
+                                 s->pending_feats.begin() + p.feat + kFeatures);
+            s->item_ms.push_back(ms);
+        }
     }
     s->pending.clear();
+    s->pending_feats.clear();
     s->ev_used = 0;
     return QSIM_OK;
 }
@@ -134,7 +140,13 @@ int execute_plan(qsim *s, const std::vector<PlanItem> &plan) {
         if (s->profiling) {
             if ((rc = record_event(s, &ev1))) return rc;
             (void)ev1;
-            s->pending.push_back({cls, ev0, bytes});
+            long feat = -1;
+            if (s->record_items) {
+                feat = (long)s->pending_feats.size();
+                s->pending_feats.resize(s->pending_feats.size() + kFeatures);
+                item_features(it, s->queue, s->n, s->prec, s->tc_enabled, &s->pending_feats[feat]);
+            }
+            s->pending.push_back({cls, ev0, bytes, feat});
         }
         s->stats.passes++;
         s->stats.amp_updates += it.amp_updates;
@@ -147,6 +159,8 @@ int flush(qsim *s) {
     std::vector<PlanItem> plan;
     if (s->fusion == QSIM_FUSE_NONE)
         plan_none(s->queue, s->n, plan);
+    else if (s->fusion == QSIM_FUSE_MLP && s->cost.loaded())
+        plan_mlp(s->queue, s->n, s->prec, s->tc_enabled, s->cost, plan, &s->last_plan_predicted_ms);
     else
         plan_greedy(s->queue, s->n, s->kmax, plan);
     const int rc = execute_plan(s, plan);
@@ -220,7 +234,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     if (!s) return QSIM_ENOMEM;
     s->n = n;
     s->prec = precision;
-    s->fusion = o.fusion == QSIM_FUSE_MLP ? QSIM_FUSE_GREEDY : o.fusion;
+    s->fusion = o.fusion;
     s->kmax = o.kmax;
     if (o.tc_terms != 0 && o.tc_terms != 3 && o.tc_terms != 5) {
         delete s;
@@ -229,6 +243,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->tc_terms = o.tc_terms == 5 ? 5 : 3;
     s->tc_enabled = o.no_tensor_cores == 0;
     s->norm_tracking = o.no_norm_tracking == 0;
+    s->c128_df = o.c128_double_float != 0;
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
@@ -487,7 +502,7 @@ int sim_set_fusion(qsim *s, int mode, int kmax) {
     if (kmax < 1 || kmax > 5) return set_err(s, QSIM_EINVAL, "kmax outside 1..5");
     int rc = flush(s);
     if (rc) return rc;
-    s->fusion = mode == QSIM_FUSE_MLP ? QSIM_FUSE_GREEDY : mode;
+    s->fusion = mode;
     s->kmax = kmax;
     return QSIM_OK;
 }
@@ -510,6 +525,9 @@ int sim_set_profiling(qsim *s, int on) {
     if (rc) return rc;
     if ((rc = harvest(s))) return rc;
     s->profiling = on != 0;
+    s->record_items = on == 2;
+    s->item_feats.clear();
+    s->item_ms.clear();
     for (auto &c : s->class_time) c = qsim::ClassTime{};
     return QSIM_OK;
 }
@@ -532,6 +550,47 @@ int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nro
         ++k;
     }
     *nrows = k;
+    return QSIM_OK;
+}
+
+int sim_get_item_times(qsim *s, float *feats, float *ms, int max_items, int *nitems) {
+    if (!s || !nitems || (max_items > 0 && (!feats || !ms))) return QSIM_EINVAL;
+    int rc = flush(s);
+    if (rc) return rc;
+    if ((rc = harvest(s))) return rc;
+    const int n = (int)s->item_ms.size();
+    const int k = n < max_items ? n : max_items;
+    if (k > 0) {
+        std::memcpy(feats, s->item_feats.data(), sizeof(float) * kFeatures * k);
+        std::memcpy(ms, s->item_ms.data(), sizeof(float) * k);
+    }
+    *nitems = n;
+    if (k == n) {
+        s->item_feats.clear();
+        s->item_ms.clear();
+    }
+    return QSIM_OK;
+}
+
+int sim_set_cost_model(qsim *s, const float *params, int count, int hidden) {
+    if (!s) return QSIM_EINVAL;
+    if (count == 0) {
+        s->cost = CostModel{};
+        return QSIM_OK;
+    }
+    if (!params || hidden < 1 || hidden > 1024) return set_err(s, QSIM_EINVAL, "bad cost model");
+    const long need = (long)hidden * kFeatures + hidden + (long)hidden * hidden + hidden + hidden + 1;
+    if (count != need) return set_err(s, QSIM_EINVAL, "cost model size does not match hidden width");
+    for (int i = 0; i < count; ++i)
+        if (!std::isfinite(params[i])) return set_err(s, QSIM_ENONFINITE, "non-finite cost model parameter");
+    s->cost.hidden = hidden;
+    s->cost.p.assign(params, params + count);
+    return QSIM_OK;
+}
+
+int sim_plan_stats(qsim *s, double *predicted_ms) {
+    if (!s || !predicted_ms) return QSIM_EINVAL;
+    *predicted_ms = s->last_plan_predicted_ms;
     return QSIM_OK;
 }
 

@@ -26,22 +26,27 @@
 // V always contains qubits 0..6 (or more), so every tile is made of runs of
 // at least 128 contiguous amplitudes.
 //
-// Per CTA (persistent, 128 threads, two CTAs per SM):
+// Per CTA (persistent, 128 threads, up to four CTAs per SM, ~51 KB of shared
+// memory and 64 TMEM columns each):
 //   - one TMA bulk copy brings the gate operand R1, R2(, R3) (pre-swizzled
 //     on the host) and the tile index tables into shared memory;
-//   - each thread loads 32 amplitudes of the next tile with 16-byte loads,
-//     splits them into bf16 hi/lo and writes them to the A buffers in the
-//     128-byte-swizzled K-major layout the MMA reads;
-//   - thread 0 issues 12 (or 20) tcgen05.mma (M128 N64 K16) into one of two
-//     TMEM accumulators and commits them to an mbarrier;
-//   - while the tensor cores work and the next tile's loads are in flight,
-//     the four warps read the previous tile's accumulator with tcgen05.ld
-//     (warp w owns TMEM lanes 32w..32w+31 = tile columns) and store it.
+//   - each thread loads 32 amplitudes of a tile with 16-byte loads, splits
+//     them into bf16 hi/lo and writes them to the A operand in the
+//     128-byte-swizzled K-major layout the MMA reads (the lane mapping is
+//     chosen per block so these writes are free of bank conflicts);
+//   - thread 0 issues 12 (or 20) tcgen05.mma (M128 N64 K16) into the TMEM
+//     accumulator and commits them to an mbarrier;
+//   - the next tile's loads go out while the tensor cores work; then the
+//     four warps read the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = tile columns) and store it.  The other CTAs on the
+//     SM keep HBM busy meanwhile.
 // Every wait is bounded; on time-out the kernel raises an error flag in the
 // workspace, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -56,19 +61,28 @@ constexpr int kTcThreads = 128;
 constexpr int kTile = 4096;              // amplitudes per tile (2^12)
 constexpr int kABytes = 128 * 128;       // one bf16 split of X: 128 rows x 128 B
 constexpr int kBBytes = 64 * 128;        // one bf16 split of R: 64 rows x 128 B
-constexpr int kTablesBytes = 2560;
-constexpr uint32_t kTmemCols = 128;      // two 64-column fp32 accumulators
+constexpr int kTablesBytes = 2816;
+constexpr uint32_t kTmemCols = 64;       // one 64-column fp32 accumulator
 constexpr uint32_t kWaitLimit = 1u << 24;
-constexpr int kMaxTcGrid = 2 * kSMs;
+constexpr int kMaxTcGrid = 4 * kSMs;
 
 // Layout of the per-block operand record (host-built, copied to smem as is).
+// Thread tid loads tile elements e = e0(tid) | ei(i) | h for i < 16, h < 2
+// (bit sets of e0, ei and h disjoint): the address, block row r and tile
+// column c of e are the ORs of the parts.  The split of the 11 element bits
+// into 5 lane bits, 2 warp bits and 4 loop bits is chosen per block so that
+// a warp's writes of the bf16 operand hit 32 distinct banks and its 16-byte
+// loads fill whole 32-byte sectors.
 struct RecTables {
-    uint64_t t_lo[64];   // address bits of tile element e (low 6 bits of e)
-    uint64_t t_hi[64];   // ... (high 6 bits of e)
-    uint64_t cdep[128];  // address bits of tile column c
-    uint64_t rdep[32];   // address bits of block row r
-    uint8_t r_lo[64], r_hi[64];  // block row of element e
-    uint8_t c_lo[64], c_hi[64];  // tile column of element e
+    uint64_t a0[128];    // address bits of e0(tid)
+    uint64_t cdep[128];  // address bits of tile column c (epilogue)
+    uint64_t ai[16];     // address bits of ei(i)
+    uint64_t rdep[32];   // address bits of block row r (epilogue)
+    uint8_t r0[128], c0[128];  // row / column bits of e0(tid)
+    uint8_t ri[16], ci[16];    // row / column bits of ei(i)
+    uint8_t rh, ch;            // row / column bit of h (address bit 0)
+    uint8_t pair_r;            // 1 if rows r, r+1 are adjacent in memory (qubit 0 in S)
+    uint8_t pad[93];
 };
 static_assert(sizeof(RecTables) == kTablesBytes, "table layout");
 
@@ -184,17 +198,38 @@ __device__ __forceinline__ void put_amp(unsigned char *a_hi, unsigned char *a_lo
     *(uint32_t *)(a_lo + off) = lw;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
+// Two amplitudes of the same column at rows r (even) and r+1: one 8-byte
+// write per split.
+__device__ __forceinline__ void put_amp2(unsigned char *a_hi, unsigned char *a_lo, int c, int r, float4 v) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
+    __nv_bfloat162 p0, p1;
+    p0.x = h0;
+    p0.y = h1;
+    p1.x = h2;
+    p1.y = h3;
+    uint2 hw, lw;
+    memcpy(&hw.x, &p0, 4);
+    memcpy(&hw.y, &p1, 4);
+    lw.x = pack_bf16x2(v.x - __bfloat162float(h0), v.y - __bfloat162float(h1));
+    lw.y = pack_bf16x2(v.z - __bfloat162float(h2), v.w - __bfloat162float(h3));
+    const int off = c * 128 + ((((r >> 2) ^ c) & 7) << 4) + ((r & 3) << 2);
+    *(uint2 *)(a_hi + off) = hw;
+    *(uint2 *)(a_lo + off) = lw;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 4) k_block_tc(const TcArgs args) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *A = smem;                           // [2 buf][2 split][kABytes]
-    unsigned char *B = smem + 4 * kABytes;             // [nsplit][kBBytes] then tables
+    unsigned char *A = smem;                           // [2 split][kABytes]
+    unsigned char *B = smem + 2 * kABytes;             // [nsplit][kBBytes] then tables
     const RecTables *tab = (const RecTables *)(B + args.nsplit * kBBytes);
     uint64_t *bars = (uint64_t *)(B + args.nsplit * kBBytes + kTablesBytes);  // [0]=operand, [1],[2]=mma
     uint32_t *tmem_slot = (uint32_t *)(bars + 3);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *s_scale = (float *)(tmem_slot + 2);
     double *s_red = (double *)(bars + 5);  // [4 warps][2]
+    (void)bars[2];
 
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
@@ -249,12 +284,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
     double nrm_in = 0.0, nrm_out = 0.0;
     const float scale = *s_scale;
     if (!*abort_flag) {
-        // per-thread constants of the element mapping e = 2*(tid + 128 i) + h
-        const int elo0 = (2 * tid) & 63, elo1 = (2 * tid + 1) & 63;
-        const uint64_t toff_lo = tab->t_lo[elo0];
-        const int rl0 = tab->r_lo[elo0], rl1 = tab->r_lo[elo1];
-        const int cl0 = tab->c_lo[elo0], cl1 = tab->c_lo[elo1];
-        const int ehi0 = tid >> 5;
+        // per-thread constants of the element mapping e = e0(tid) | ei(i) | h
+        const uint64_t toff0 = tab->a0[tid];
+        const int r00 = tab->r0[tid], c00 = tab->c0[tid];
+        const int r01 = r00 | tab->rh, c01 = c00 | tab->ch;
+        const bool pair_r = tab->pair_r != 0;
         const uint64_t my_cdep = tab->cdep[tid];
         const int nterms = args.nsplit == 3 ? 5 : 3;
 
@@ -262,51 +296,65 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
         uint64_t t = blockIdx.x;
         auto load_tile = [&](uint64_t tt) {
             const uint64_t base = insert_zeros(tt, args.vspec);
-            const float2 *p = psi_in + base + toff_lo;
+            const float2 *p = psi_in + base + toff0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) regs[i] = *(const float4 *)(p + tab->t_hi[ehi0 + 4 * i]);
+            for (int i = 0; i < 16; ++i) regs[i] = *(const float4 *)(p + tab->ai[i]);
         };
         auto epilogue = [&](uint64_t tt, int j) {
-            const int buf = j & 1;
-            if (!mbar_wait(&bars[1 + buf], (uint32_t)((j >> 1) & 1))) {
+            if (!mbar_wait(&bars[1], (uint32_t)(j & 1))) {
                 atomicOr(args.err, 2u);
                 *abort_flag = 1;
                 return;
             }
             tc_fence_after();
             const uint64_t base = insert_zeros(tt, args.vspec) + my_cdep;
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 64);
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
             float ssq = 0.f;
 #pragma unroll
             for (int chunk = 0; chunk < 4; ++chunk) {
                 float v[16];
                 tmem_ld16(taddr + chunk * 16, v);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int r = chunk * 8 + q;
-                    ssq = fmaf(v[2 * q], v[2 * q], fmaf(v[2 * q + 1], v[2 * q + 1], ssq));
-                    psi[base + tab->rdep[r]] = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
+                for (int q = 0; q < 16; ++q) ssq = fmaf(v[q], v[q], ssq);
+                if (pair_r) {
+#pragma unroll
+                    for (int q = 0; q < 8; q += 2) {
+                        const int r = chunk * 8 + q;
+                        *(float4 *)(psi + base + tab->rdep[r]) = make_float4(
+                            v[2 * q] * scale, v[2 * q + 1] * scale, v[2 * q + 2] * scale, v[2 * q + 3] * scale);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int r = chunk * 8 + q;
+                        psi[base + tab->rdep[r]] = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
+                    }
                 }
             }
             nrm_out += (double)ssq;
             tc_fence_before();
         };
 
+        // One A buffer and one accumulator: tile t is converted, multiplied
+        // and stored before tile t+1 is converted; the loads of tile t+1 are
+        // in flight while the tensor cores work on tile t and while tile t is
+        // stored, and the other CTAs on the SM overlap the rest.
         if (t < args.ntiles) load_tile(t);
         int it = 0;
+        unsigned char *a_hi = A, *a_lo = A + kABytes;
         for (; t < args.ntiles; t += gridDim.x, ++it) {
-            const int buf = it & 1;
-            unsigned char *a_hi = A + (2 * buf) * kABytes;
-            unsigned char *a_lo = A + (2 * buf + 1) * kABytes;
             float xsq = 0.f;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 xsq = fmaf(regs[i].x, regs[i].x, fmaf(regs[i].y, regs[i].y, xsq));
                 xsq = fmaf(regs[i].z, regs[i].z, fmaf(regs[i].w, regs[i].w, xsq));
-                const int eh = ehi0 + 4 * i;
-                const int rh = tab->r_hi[eh], ch = tab->c_hi[eh];
-                put_amp(a_hi, a_lo, cl0 | ch, rl0 | rh, regs[i].x, regs[i].y);
-                put_amp(a_hi, a_lo, cl1 | ch, rl1 | rh, regs[i].z, regs[i].w);
+                const int ri = tab->ri[i], ci = tab->ci[i];
+                if (pair_r) {
+                    put_amp2(a_hi, a_lo, c00 | ci, r00 | ri, regs[i]);
+                } else {
+                    put_amp(a_hi, a_lo, c00 | ci, r00 | ri, regs[i].x, regs[i].y);
+                    put_amp(a_hi, a_lo, c01 | ci, r01 | ri, regs[i].z, regs[i].w);
+                }
             }
             nrm_in += (double)xsq;
             fence_proxy_async_smem();
@@ -315,7 +363,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
             if (*abort_flag) break;
             if (tid == 0) {
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * 64);
                 const uint32_t ahi = smem_u32(a_hi), alo = smem_u32(a_lo);
                 const uint32_t b0 = smem_u32(B), b1 = b0 + kBBytes, b2 = b0 + 2 * kBBytes;
                 uint32_t acc = 0;
@@ -325,17 +372,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
                     const uint32_t b = term < 2 ? b0 : (term < 4 ? b1 : b2);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        mma_bf16(d, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), acc);
+                        mma_bf16(tmem, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), acc);
                         acc = 1;
                     }
                 }
-                mma_commit(&bars[1 + buf]);
+                mma_commit(&bars[1]);
             }
             const uint64_t tn = t + gridDim.x;
             if (tn < args.ntiles) load_tile(tn);
-            if (it >= 1) epilogue(t - gridDim.x, it - 1);
+            epilogue(t, it);
+            if (*abort_flag) break;
         }
-        if (it >= 1 && !*abort_flag) epilogue(t - gridDim.x, it - 1);
     }
     // per-CTA norm sums, fixed reduction order
     nrm_in = warp_sum(nrm_in);
@@ -455,31 +502,96 @@ void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsi
             if (F[j] == bit) return j;
         return -1;
     };
-    for (int e = 0; e < 64; ++e) {
-        for (int half = 0; half < 2; ++half) {
-            uint64_t addr = 0;
-            int r = 0, c = 0;
-            for (int b = 0; b < 6; ++b) {
-                if (!((e >> b) & 1)) continue;
-                const int bit = V[6 * half + b];
-                addr |= 1ull << bit;
-                const int si = s_index(bit);
-                if (si >= 0)
-                    r |= 1 << si;
-                else
-                    c |= 1 << f_index(bit);
+    // element e (12 bits, bit b <-> qubit V[b]) -> address, row, column
+    auto addr_of = [&](unsigned e) {
+        uint64_t a = 0;
+        for (int b = 0; b < 12; ++b)
+            if ((e >> b) & 1u) a |= 1ull << V[b];
+        return a;
+    };
+    auto row_of = [&](unsigned e) {
+        int r = 0;
+        for (int b = 0; b < 12; ++b)
+            if ((e >> b) & 1u) {
+                const int si = s_index(V[b]);
+                if (si >= 0) r |= 1 << si;
             }
-            if (half == 0) {
-                T.t_lo[e] = addr;
-                T.r_lo[e] = (uint8_t)r;
-                T.c_lo[e] = (uint8_t)c;
-            } else {
-                T.t_hi[e] = addr;
-                T.r_hi[e] = (uint8_t)r;
-                T.c_hi[e] = (uint8_t)c;
+        return r;
+    };
+    auto col_of = [&](unsigned e) {
+        int c = 0;
+        for (int b = 0; b < 12; ++b)
+            if ((e >> b) & 1u) {
+                const int fi = f_index(V[b]);
+                if (fi >= 0) c |= 1 << fi;
             }
+        return c;
+    };
+    auto deposit = [](unsigned x, const int *bits, int nb) {
+        unsigned e = 0;
+        for (int j = 0; j < nb; ++j)
+            if ((x >> j) & 1u) e |= 1u << bits[j];
+        return e;
+    };
+    // choose the 5 lane bits among element bits 1..11: first minimise the
+    // bank conflicts of the operand writes, then the sectors of the loads
+    int best_lane[5] = {1, 2, 3, 4, 5};
+    int best_score = 1 << 30;
+    for (unsigned mask = 0; mask < (1u << 11); ++mask) {
+        if (__builtin_popcount(mask) != 5) continue;
+        int lb[5], k = 0;
+        for (int b = 0; b < 11; ++b)
+            if ((mask >> b) & 1u) lb[k++] = b + 1;
+        // 4-byte writes (one per amplitude) or, with qubit 0 in S, 8-byte
+        // writes of rows r, r+1: count the lanes per 4- or 8-byte slot
+        int bank_count[32] = {0};
+        uint64_t sectors[32];
+        int nsec = 0;
+        const bool paired = S[0] == 0;
+        for (unsigned lane = 0; lane < 32; ++lane) {
+            const unsigned e = deposit(lane, lb, 5);
+            const int r = row_of(e), c = col_of(e);
+            const int word = ((((r >> 2) ^ c) & 7) << 2) | (r & 3);
+            bank_count[paired ? (word >> 1) : word]++;
+            const uint64_t sec = (addr_of(e) * 8) >> 5;  // 32-byte sector of the 16-byte load
+            bool seen = false;
+            for (int j = 0; j < nsec; ++j) seen |= sectors[j] == sec;
+            if (!seen) sectors[nsec++] = sec;
+        }
+        int worst = 0;
+        for (int bnk = 0; bnk < 32; ++bnk) worst = bank_count[bnk] > worst ? bank_count[bnk] : worst;
+        if (paired) worst = (worst + 1) / 2;  // 8-byte accesses: two lanes per slot is one pass
+        const int score = worst * 64 + nsec;  // ideal: 1 * 64 + 16
+        if (score < best_score) {
+            best_score = score;
+            for (int j = 0; j < 5; ++j) best_lane[j] = lb[j];
         }
     }
+    int warp_bits[2], loop_bits[4], nw = 0, nl = 0;
+    for (int b = 1; b < 12; ++b) {
+        bool lane = false;
+        for (int j = 0; j < 5; ++j) lane |= best_lane[j] == b;
+        if (lane) continue;
+        if (nw < 2)
+            warp_bits[nw++] = b;
+        else
+            loop_bits[nl++] = b;
+    }
+    for (unsigned tid = 0; tid < 128; ++tid) {
+        const unsigned e0 = deposit(tid & 31, best_lane, 5) | deposit(tid >> 5, warp_bits, 2);
+        T.a0[tid] = addr_of(e0);
+        T.r0[tid] = (uint8_t)row_of(e0);
+        T.c0[tid] = (uint8_t)col_of(e0);
+    }
+    for (unsigned i = 0; i < 16; ++i) {
+        const unsigned ei = deposit(i, loop_bits, 4);
+        T.ai[i] = addr_of(ei);
+        T.ri[i] = (uint8_t)row_of(ei);
+        T.ci[i] = (uint8_t)col_of(ei);
+    }
+    T.rh = (uint8_t)row_of(1u);
+    T.ch = (uint8_t)col_of(1u);
+    T.pair_r = (S[0] == 0) ? 1 : 0;
     for (int c = 0; c < 128; ++c) {
         uint64_t a = 0;
         for (int j = 0; j < 7; ++j)
@@ -495,7 +607,7 @@ void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsi
     std::memcpy(&rec[(size_t)nsplit * kBBytes], &T, sizeof(T));
 }
 
-size_t smem_bytes(int nsplit) { return 1024 + 4 * kABytes + (size_t)nsplit * kBBytes + kTablesBytes + 128; }
+size_t smem_bytes(int nsplit) { return 1024 + 2 * kABytes + (size_t)nsplit * kBBytes + kTablesBytes + 128; }
 
 }  // namespace
 
@@ -519,12 +631,42 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     int rc = stage_operand(s, rec.data(), rec.size(), &dev_rec);
     if (rc) return rc;
     static bool attr_set[64] = {false};
+    static int per_sm[64][4] = {{0}};
     const int dev = s->device;
-    const size_t smem = smem_bytes(3);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = smem_bytes(nsplit);
+    if (dev < 0 || dev >= 64) return QSIM_ENOTSUP;
+    if (!attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes(3));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return cuda_err(s, e, "tc kernel attribute");
         attr_set[dev] = true;
+    }
+    if (!per_sm[dev][nsplit]) {
+        // resident CTAs per SM from the kernel's footprint: registers, shared
+        // memory (+1 KB reserved per CTA) and tensor-memory columns; CTAs
+        // never wait on one another, so an overestimate only queues CTAs
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_block_tc);
+        int regs_sm = 65536, smem_sm = 233472;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) return cuda_err(s, e, "tc kernel attributes");
+        const int by_regs = regs_sm / (fa.numRegs * kTcThreads);
+        const int by_smem = smem_sm / (int)(smem + 1024);
+        int occ = by_regs < by_smem ? by_regs : by_smem;
+        if (occ > (int)(512 / kTmemCols)) occ = (int)(512 / kTmemCols);
+        if (occ > 4) occ = 4;
+        if (occ < 1) occ = 1;
+        int api = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, k_block_tc, kTcThreads, smem);
+        cudaGetLastError();
+        if (getenv("QSIM_DEBUG"))
+            fprintf(stderr, "qsim: k_block_tc regs %d smem %zu: %d CTAs/SM (registers %d, shared memory %d, "
+                    "occupancy API %d)\n", fa.numRegs, smem, occ, by_regs, by_smem, api);
+        per_sm[dev][nsplit] = occ;
     }
     a.psi = (float2 *)s->state;
     a.rec = dev_rec;
@@ -532,7 +674,8 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     a.nsplit = nsplit;
     a.ntiles = 1ull << (s->n - 12);
     a.err = (unsigned int *)((char *)s->ws + kWsErr);
-    const uint64_t grid = a.ntiles < (uint64_t)kMaxTcGrid ? a.ntiles : (uint64_t)kMaxTcGrid;
+    const uint64_t cap = (uint64_t)kSMs * per_sm[dev][nsplit];
+    const uint64_t grid = a.ntiles < cap ? a.ntiles : cap;
     double *slots = (double *)((char *)s->ws + kWsNorm);
     const int slot = (int)(s->tc_passes & 1);
     a.norm_out = slots + slot * 2 * kMaxTcGrid;

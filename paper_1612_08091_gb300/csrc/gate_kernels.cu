@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "df128.cuh"
 #include "internal.h"
 
 using namespace qsim_dev;
@@ -90,6 +91,91 @@ __global__ void __launch_bounds__(256) k_x(Amp *__restrict__ psi, uint64_t ngrou
     const Amp a = psi[i0], b = psi[i1];
     psi[i0] = b;
     psi[i1] = a;
+}
+
+// complex128 with double-float arithmetic (df128.cuh): one-qubit dense,
+// diagonal and phase gates
+struct MatDF {
+    qsim_df::C2 m[4];
+};
+
+__global__ void __launch_bounds__(256) k_dense1_df(double2 *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                                   uint64_t cmask, uint64_t tbit, const MatDF M) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t i0 = insert_zeros(g, ins) | cmask;
+    const uint64_t i1 = i0 | tbit;
+    const qsim_df::C2 a = qsim_df::split(psi[i0]), b = qsim_df::split(psi[i1]);
+    psi[i0] = qsim_df::to_double(qsim_df::cdot2(M.m[0], a, M.m[1], b));
+    psi[i1] = qsim_df::to_double(qsim_df::cdot2(M.m[2], a, M.m[3], b));
+}
+
+__global__ void __launch_bounds__(256) k_diag1_df(double2 *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                                  uint64_t cmask, uint64_t tbit, const MatDF M) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t i0 = insert_zeros(g, ins) | cmask;
+    const uint64_t i1 = i0 | tbit;
+    psi[i0] = qsim_df::to_double(qsim_df::cmul(M.m[0], qsim_df::split(psi[i0])));
+    psi[i1] = qsim_df::to_double(qsim_df::cmul(M.m[3], qsim_df::split(psi[i1])));
+}
+
+__global__ void __launch_bounds__(256) k_phase_df(double2 *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
+                                                  uint64_t mask, const MatDF M) {
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const uint64_t i = insert_zeros(g, ins) | mask;
+    psi[i] = qsim_df::to_double(qsim_df::cmul(M.m[3], qsim_df::split(psi[i])));
+}
+
+qsim_df::F2 host_split(double x) {
+    qsim_df::F2 r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+MatDF make_df(const cd *m, int count) {
+    MatDF M{};
+    for (int i = 0; i < count; ++i) M.m[i] = qsim_df::C2{host_split(m[i].real()), host_split(m[i].imag())};
+    return M;
+}
+
+// Returns true if the gate was launched on a double-float kernel.
+bool gate_df(qsim *s, const GateRec &g) {
+    if (g.t != 1) return false;
+    double2 *psi = (double2 *)s->state;
+    const uint64_t tbit = 1ull << g.targets[0];
+    InsertSpec ins{};
+    auto spec = [&](uint64_t mask) {
+        ins.m = 0;
+        for (int b = 0; b < 64; ++b)
+            if ((mask >> b) & 1ull) ins.pos[ins.m++] = b;
+    };
+    const MatDF M = make_df(g.m.data(), 4);
+    switch (g.kind) {
+    case GK_DENSE: {
+        spec(g.tmask | g.cmask);
+        const uint64_t ng = 1ull << (s->n - ins.m);
+        k_dense1_df<<<(unsigned)((ng + 255) / 256), 256, 0, s->stream>>>(psi, ng, ins, g.cmask, tbit, M);
+        return true;
+    }
+    case GK_DIAG1: {
+        spec(g.tmask | g.cmask);
+        const uint64_t ng = 1ull << (s->n - ins.m);
+        k_diag1_df<<<(unsigned)((ng + 255) / 256), 256, 0, s->stream>>>(psi, ng, ins, g.cmask, tbit, M);
+        return true;
+    }
+    case GK_PHASE: {
+        const uint64_t mask = g.tmask | g.cmask;
+        spec(mask);
+        const uint64_t ng = 1ull << (s->n - ins.m);
+        k_phase_df<<<(unsigned)((ng + 255) / 256), 256, 0, s->stream>>>(psi, ng, ins, mask, M);
+        return true;
+    }
+    default:
+        return false;
+    }
 }
 
 InsertSpec make_spec(uint64_t mask) {
@@ -210,6 +296,10 @@ __global__ void k_set_basis(Amp *__restrict__ psi, uint64_t N, uint64_t basis) {
 }  // namespace
 
 int launch_gate_plain(qsim *s, const GateRec &g) {
+    if (s->prec == QSIM_C128 && s->c128_df && gate_df(s, g)) {
+        s->stats.launches++;
+        return cuda_err(s, cudaGetLastError(), "double-float gate launch");
+    }
     return s->prec == QSIM_C128 ? gate_plain<double2>(s, g) : gate_plain<float2>(s, g);
 }
 

@@ -39,6 +39,16 @@ struct PlanItem {
     std::vector<cd> m;      // 2^k x 2^k block matrix
     double amp_updates = 0; // credited to the original gates
     int ngates = 0;
+    std::vector<int> members;  // queue indices of the gates it executes, in order
+};
+
+// The learned cost model used by the planner (host inference).
+constexpr int kFeatures = 16;
+struct CostModel {
+    int hidden = 0;
+    std::vector<float> p;  // W1[H][16], b1[H], W2[H][H], b2[H], w3[H], b3
+    bool loaded() const { return hidden > 0; }
+    float predict(const float *x) const;  // predicted log(ms)
 };
 
 struct qsim {
@@ -61,6 +71,7 @@ struct qsim {
     bool tc_enabled = true;
     int tc_terms = 3;
     bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
+    bool c128_df = false;       // complex128 one-qubit gates in double-float arithmetic
     uint64_t tc_passes = 0;
     int tc_prev_grid = 0;
     unsigned char *stage_host = nullptr;  // pinned staging for block operands
@@ -69,7 +80,13 @@ struct qsim {
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    struct Pending { int cls; size_t ev; double bytes; };
+    struct Pending { int cls; size_t ev; double bytes; long feat; };
+    bool record_items = false;
+    std::vector<float> pending_feats;  // features of pending launches (record_items)
+    std::vector<float> item_feats;     // harvested: kFeatures floats per launch
+    std::vector<float> item_ms;        // harvested: event-timed duration per launch
+    CostModel cost;
+    double last_plan_predicted_ms = 0;
     std::vector<Pending> pending;
     struct ClassTime { uint64_t launches = 0; double ms = 0, bytes = 0; };
     ClassTime class_time[8];
@@ -90,7 +107,7 @@ constexpr size_t kWsChunkBytes = 64u << 10;
 constexpr size_t kWsErr = kWsChunk + kWsChunkBytes;     // device error flags
 constexpr size_t kWsErrBytes = 256;
 constexpr size_t kWsNorm = kWsErr + kWsErrBytes;        // block-pass norm partials
-constexpr size_t kWsNormBytes = 16u << 10;
+constexpr size_t kWsNormBytes = 32u << 10;  // 2 slots x 2 sums x up to 608 CTAs
 constexpr size_t kWsRing = kWsNorm + kWsNormBytes;      // block operand ring
 constexpr size_t kWsRingBytes = 16u << 20;
 constexpr size_t kWsTotal = kWsRing + kWsRingBytes;
@@ -127,3 +144,10 @@ int run_measure_all(qsim *s, double u, uint64_t *outcome);
 // Planner (planner.cpp) -------------------------------------------------------
 void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out);
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out);
+// Features of one plan item (kFeatures floats).
+void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, float *f);
+// Learned planner: greedy blocks for several kmax, each block fused or left
+// as plain gates, whichever the cost model predicts faster; the plan with
+// the lowest predicted total wins.  *predicted_ms receives its prediction.
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, const CostModel &cm,
+              std::vector<PlanItem> &out, double *predicted_ms);

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cmath>
+
 #include "internal.h"
 
 void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out) {
@@ -30,6 +32,7 @@ void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out)
         it.gate = (int)i;
         it.amp_updates = (double)(1ull << (n - (int)q[i].controls.size()));
         it.ngates = 1;
+        it.members.push_back((int)i);
         out.push_back(std::move(it));
     }
 }
@@ -117,6 +120,7 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
             it.gate = seed;
             it.amp_updates = (double)(1ull << (n - (int)q[seed].controls.size()));
             it.ngates = 1;
+            it.members.push_back(seed);
             take(seed);
             out.push_back(std::move(it));
             continue;
@@ -165,6 +169,7 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
         }
         PlanItem it;
         it.ngates = (int)members.size();
+        it.members = members;
         for (int gi : members) it.amp_updates += (double)(1ull << (n - (int)q[gi].controls.size()));
         if (members.size() == 1) {
             it.fused = false;
@@ -181,4 +186,116 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
         }
         out.push_back(std::move(it));
     }
+}
+
+// ---------------------------------------------------------------------------
+// learned planner
+// ---------------------------------------------------------------------------
+// Features (all scaled to O(1)):
+//  0 n/32            1 bytes per amplitude/16   2 fused block        3 runs on tensor cores
+//  4 width/5         5 gates in item/32         6 plain dense gate   7 plain phase gate
+//  8 plain diagonal  9 plain X permutation     10 controls/8        11 log2(fraction touched)/8
+// 12 lowest qubit/32 13 highest qubit/32       14 qubits below 5 /5  15 constant 1
+void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, float *f) {
+    for (int i = 0; i < kFeatures; ++i) f[i] = 0.f;
+    f[0] = n / 32.f;
+    f[1] = (prec == QSIM_C128 ? 16.f : 8.f) / 16.f;
+    f[15] = 1.f;
+    uint64_t mask = 0;
+    if (it.fused) {
+        f[2] = 1.f;
+        f[3] = (prec == QSIM_C64 && it.k >= 4 && n >= 12 && tc_enabled) ? 1.f : 0.f;
+        f[4] = it.k / 5.f;
+        f[5] = it.ngates / 32.f;
+        for (int j = 0; j < it.k; ++j) mask |= 1ull << it.qubits[j];
+    } else {
+        const GateRec &g = q[it.gate];
+        f[4] = g.t / 5.f;
+        f[5] = 1.f / 32.f;
+        f[6 + (g.kind == GK_PHASE ? 1 : g.kind == GK_DIAG1 ? 2 : g.kind == GK_X ? 3 : 0)] = 1.f;
+        const int c = (int)g.controls.size();
+        f[10] = c / 8.f;
+        const int fixed = c + (g.kind == GK_PHASE ? 1 : 0);
+        f[11] = -(float)fixed / 8.f;
+        mask = g.tmask | g.cmask;
+    }
+    int lo = 64, hi = -1, low5 = 0;
+    for (int b = 0; b < 64; ++b)
+        if ((mask >> b) & 1ull) {
+            lo = b < lo ? b : lo;
+            hi = b;
+            if (b < 5) ++low5;
+        }
+    f[12] = (lo == 64 ? 0 : lo) / 32.f;
+    f[13] = (hi < 0 ? 0 : hi) / 32.f;
+    f[14] = low5 / 5.f;
+}
+
+float CostModel::predict(const float *x) const {
+    const int H = hidden;
+    const float *W1 = p.data(), *b1 = W1 + (size_t)H * kFeatures, *W2 = b1 + H, *b2 = W2 + (size_t)H * H,
+                *w3 = b2 + H, *b3 = w3 + H;
+    std::vector<float> h1(H), h2(H);
+    for (int j = 0; j < H; ++j) {
+        float a = b1[j];
+        for (int i = 0; i < kFeatures; ++i) a += W1[(size_t)j * kFeatures + i] * x[i];
+        h1[j] = a > 0.f ? a : 0.f;
+    }
+    for (int j = 0; j < H; ++j) {
+        float a = b2[j];
+        for (int i = 0; i < H; ++i) a += W2[(size_t)j * H + i] * h1[i];
+        h2[j] = a > 0.f ? a : 0.f;
+    }
+    float y = b3[0];
+    for (int i = 0; i < H; ++i) y += w3[i] * h2[i];
+    return y;
+}
+
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, const CostModel &cm,
+              std::vector<PlanItem> &out, double *predicted_ms) {
+    auto cost = [&](const PlanItem &it) {
+        float f[kFeatures];
+        item_features(it, q, n, prec, tc_enabled, f);
+        return std::exp((double)cm.predict(f));
+    };
+    auto single = [&](int gi) {
+        PlanItem it;
+        it.fused = false;
+        it.gate = gi;
+        it.ngates = 1;
+        it.members.push_back(gi);
+        it.amp_updates = (double)(1ull << (n - (int)q[gi].controls.size()));
+        return it;
+    };
+    double best = 1e300;
+    for (int kmax = 1; kmax <= 5; ++kmax) {
+        std::vector<PlanItem> blocks, plan;
+        if (kmax == 1)
+            plan_none(q, n, blocks);
+        else
+            plan_greedy(q, n, kmax, blocks);
+        double total = 0.0;
+        for (PlanItem &b : blocks) {
+            const double cf = cost(b);
+            if (!b.fused) {
+                total += cf;
+                plan.push_back(std::move(b));
+                continue;
+            }
+            double cs = 0.0;
+            for (int gi : b.members) cs += cost(single(gi));
+            if (cs < cf) {
+                total += cs;
+                for (int gi : b.members) plan.push_back(single(gi));
+            } else {
+                total += cf;
+                plan.push_back(std::move(b));
+            }
+        }
+        if (total < best) {
+            best = total;
+            out.swap(plan);
+        }
+    }
+    if (predicted_ms) *predicted_ms = best;
 }

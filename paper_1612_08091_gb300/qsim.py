@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("fusion", ctypes.c_int), ("kmax", ctypes.c_int),
                 ("device", ctypes.c_int), ("tc_terms", ctypes.c_int), ("no_tensor_cores", ctypes.c_int),
-                ("no_norm_tracking", ctypes.c_int)]
+                ("no_norm_tracking", ctypes.c_int), ("c128_double_float", ctypes.c_int)]
 
 
 class Pauli(ctypes.Structure):
@@ -119,7 +119,7 @@ class Simulator:
     """An n-qubit register on the GPU behind the libqsim C ABI."""
 
     def __init__(self, n, precision="c128", fusion="none", kmax=5, device=None, stream=None, torch_memory=True,
-                 tc_terms=3, tensor_cores=True, norm_tracking=True):
+                 tc_terms=3, tensor_cores=True, norm_tracking=True, c128_df=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -137,6 +137,7 @@ class Simulator:
         opts.tc_terms = int(tc_terms)
         opts.no_tensor_cores = 0 if tensor_cores else 1
         opts.no_norm_tracking = 0 if norm_tracking else 1
+        opts.c128_double_float = 1 if c128_df else 0
         self._keep = []
         if torch_memory:
             ws = ctypes.c_size_t()
@@ -277,7 +278,9 @@ class Simulator:
         self._check(self.lib.sim_reset_stats(self.h), "sim_reset_stats")
 
     def set_profiling(self, on=True):
-        self._check(self.lib.sim_set_profiling(self.h, 1 if on else 0), "sim_set_profiling")
+        """on: False/0 off, True/1 per-class times, 2 also per-launch records."""
+        mode = int(on) if not isinstance(on, bool) else (1 if on else 0)
+        self._check(self.lib.sim_set_profiling(self.h, mode), "sim_set_profiling")
 
     def kernel_times(self):
         rows = (KernelTime * 16)()
@@ -370,3 +373,132 @@ def hea_angles(circuits):
             parts.append(np.asarray(c["ry"][l], dtype=np.float64))
             parts.append(np.asarray(c["rz"][l], dtype=np.float64))
     return np.concatenate(parts) if parts else np.zeros(0)
+
+
+def _bind_learned(lib):
+    if getattr(lib, "_learned_bound", False):
+        return lib
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    FP, IP = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "sim_get_item_times": [P, FP, FP, I, IP],
+        "sim_set_cost_model": [P, FP, I, I],
+        "sim_plan_stats": [P, ctypes.POINTER(D)],
+        "sim_mlp_create": [I, ctypes.c_ulonglong, P, ctypes.POINTER(P)],
+        "sim_mlp_destroy": [P],
+        "sim_mlp_get_params": [P, FP, I],
+        "sim_mlp_set_params": [P, FP, I],
+        "sim_mlp_forward": [P, FP, I, FP],
+        "sim_mlp_gradient": [P, FP, FP, I, FP, FP],
+        "sim_mlp_train": [P, FP, FP, I, I, I, ctypes.c_float, FP],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.sim_mlp_param_count.argtypes = [I]
+    lib.sim_mlp_param_count.restype = I
+    lib._learned_bound = True
+    return lib
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+NFEATURES = 16
+
+
+def _sim_item_times(self):
+    lib = _bind_learned(self.lib)
+    n = ctypes.c_int()
+    self._check(lib.sim_get_item_times(self.h, None, None, 0, ctypes.byref(n)), "sim_get_item_times")
+    feats = np.zeros((max(1, n.value), NFEATURES), dtype=np.float32)
+    ms = np.zeros(max(1, n.value), dtype=np.float32)
+    self._check(lib.sim_get_item_times(self.h, _fp(feats), _fp(ms), n.value, ctypes.byref(n)), "sim_get_item_times")
+    return feats[:n.value], ms[:n.value]
+
+
+def _sim_set_cost_model(self, params, hidden):
+    lib = _bind_learned(self.lib)
+    if params is None:
+        self._check(lib.sim_set_cost_model(self.h, None, 0, 0), "sim_set_cost_model")
+        return
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    self._check(lib.sim_set_cost_model(self.h, _fp(p), p.size, int(hidden)), "sim_set_cost_model")
+
+
+def _sim_plan_predicted_ms(self):
+    lib = _bind_learned(self.lib)
+    v = ctypes.c_double()
+    self._check(lib.sim_plan_stats(self.h, ctypes.byref(v)), "sim_plan_stats")
+    return v.value
+
+
+Simulator.item_times = _sim_item_times
+Simulator.set_cost_model = _sim_set_cost_model
+Simulator.plan_predicted_ms = _sim_plan_predicted_ms
+
+
+class MLP:
+    """The cost model's network on the GPU (sim_mlp_* in the C ABI):
+    16 -> hidden -> hidden -> 1, ReLU, trained with Adam on squared error."""
+
+    def __init__(self, hidden=32, seed=1):
+        self.lib = _bind_learned(load())
+        self.hidden = int(hidden)
+        self.nparams = self.lib.sim_mlp_param_count(self.hidden)
+        h = ctypes.c_void_p()
+        rc = self.lib.sim_mlp_create(self.hidden, int(seed), None, ctypes.byref(h))
+        if rc:
+            raise QsimError(rc, "sim_mlp_create", "")
+        self.h = h
+
+    def _check(self, rc, call):
+        if rc:
+            raise QsimError(rc, call, "")
+
+    @property
+    def params(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        self._check(self.lib.sim_mlp_get_params(self.h, _fp(p), p.size), "sim_mlp_get_params")
+        return p
+
+    @params.setter
+    def params(self, value):
+        p = np.ascontiguousarray(value, dtype=np.float32)
+        self._check(self.lib.sim_mlp_set_params(self.h, _fp(p), p.size), "sim_mlp_set_params")
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(X.shape[0], dtype=np.float32)
+        self._check(self.lib.sim_mlp_forward(self.h, _fp(X), X.shape[0], _fp(y)), "sim_mlp_forward")
+        return y
+
+    def gradient(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(self.lib.sim_mlp_gradient(self.h, _fp(X), _fp(T), X.shape[0], _fp(g), ctypes.byref(loss)),
+                    "sim_mlp_gradient")
+        return g, loss.value
+
+    def train(self, X, T, epochs=200, batch=256, lr=3e-3):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(self.lib.sim_mlp_train(self.h, _fp(X), _fp(T), X.shape[0], int(epochs), int(batch),
+                                           float(lr), ctypes.byref(loss)), "sim_mlp_train")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sim_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

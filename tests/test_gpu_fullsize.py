@@ -1,0 +1,157 @@
+"""Full-size checks at the register sizes of the benchmark configurations,
+in the launch configuration bench.py times (fused complex64, greedy k <= 5;
+plain complex128).  The oracle cannot hold these states in seconds, so the
+checks use properties that hold at any size (U U^dag = 1, QFT and Grover
+closed forms on sampled amplitudes, probabilities of 1/2, cumulative-sum
+sampling against a host cumsum) plus one direct oracle comparison of the
+full depth-40 circuit structure at 26 qubits."""
+import math
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+from helpers import TOL64_INFID, infidelity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1612_08091_gb300 as q
+
+    q.load()
+    return q
+
+
+def _free():
+    import torch
+
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def qft_amplitudes(x, n, idx):
+    N = 1 << n
+    r = (np.uint64(x) * idx.astype(np.uint64)) % np.uint64(N)
+    return np.exp(2j * np.pi * r.astype(np.float64) / N) / math.sqrt(N)
+
+
+# per-amplitude bounds relative to the amplitude magnitude 2^-15: complex64
+# blocks carry about 1e-6 relative error per amplitude after a few passes
+# (infidelity ~1e-11); complex128 about 1e-14
+@pytest.mark.parametrize("prec,fusion,rel", [("c64", "greedy", 1e-4), ("c128", "none", 1e-9)])
+def test_qft30_closed_form(qs, prec, fusion, rel):
+    n = 30
+    x = cg.random_basis_state(n, seed=8091)
+    idx = np.unique(np.concatenate([np.arange(64), (1 << n) - 1 - np.arange(64),
+                                    np.random.default_rng(1).integers(0, 1 << n, 4096)]))
+    with qs.Simulator(n, precision=prec, fusion=fusion) as sim:
+        sim.run(cg.basis_prep_ops(x, n) + cg.qft_ops(n))
+        p1, nrm = sim.probs_all()
+        got = np.array([sim.get_amplitudes(int(i), 1)[0] for i in idx])
+    want = qft_amplitudes(x, n, idx)
+    err = np.max(np.abs(got - want)) / 2.0 ** (-n / 2)
+    print("QFT-30 %s: max relative amplitude error %.3e" % (prec, err))
+    assert err <= rel, err
+    np.testing.assert_allclose(p1, 0.5, atol=1e-5 if prec == "c64" else 1e-12)
+    assert abs(nrm - 1.0) <= (1e-5 if prec == "c64" else 1e-12)
+    _free()
+
+
+def test_random32_depth40_roundtrip_fused(qs):
+    n = 32
+    ops = cg.random_u3_brickwork(n, 40, seed=8091)
+    with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
+        sim.run(ops)
+        sim.flush()
+        mid = sim.get_amplitudes(0, 4)
+        sim.run(cg.inverse_ops(ops))
+        a0 = sim.get_amplitudes(0, 1)[0]
+        p1, nrm = sim.probs_all()
+    assert abs(mid[0]) < 1e-3  # the forward circuit spread the state
+    # fidelity with |0...0> after U U^dag
+    assert 1.0 - abs(a0) ** 2 / nrm <= 2 * TOL64_INFID, 1.0 - abs(a0) ** 2 / nrm
+    assert np.max(p1) <= 2 * TOL64_INFID
+    _free()
+
+
+def test_random32_roundtrip_plain_c128(qs):
+    n = 32
+    ops = cg.random_u3_brickwork(n, 3, seed=8091)
+    with qs.Simulator(n, precision="c128", fusion="none") as sim:
+        sim.run(ops + cg.inverse_ops(ops))
+        a0 = sim.get_amplitudes(0, 1)[0]
+    assert abs(abs(a0) - 1.0) <= 1e-12
+    _free()
+
+
+@pytest.mark.parametrize("prec,fusion", [("c64", "greedy"), ("c128", "none")])
+def test_random26_depth40_against_oracle(qs, oracle_mod, prec, fusion):
+    n = 26
+    ops = cg.random_u3_brickwork(n, 40, seed=8091)
+    ref = oracle_mod.OracleSim(n)
+    oracle_mod.run_ops(ref, ops)
+    with qs.Simulator(n, precision=prec, fusion=fusion) as sim:
+        sim.run(ops)
+        got = sim.get_amplitudes()
+        p1, _ = sim.probs_all()
+        e = sim.expect(cg.zz_chain_terms(n))
+    inf = infidelity(ref.psi, got)
+    if prec == "c128":
+        assert np.max(np.abs(got - ref.psi)) <= 1e-11
+    else:
+        assert inf <= TOL64_INFID, inf
+    np.testing.assert_allclose(p1, ref.probs_all(), atol=1e-5)
+    assert abs(e - ref.expect(cg.zz_chain_terms(n))) <= 1e-5 * (n - 1)
+    _free()
+
+
+@pytest.mark.parametrize("prec,fusion", [("c64", "greedy"), ("c128", "none")])
+def test_grover28_truncated_closed_form(qs, prec, fusion):
+    n = 28
+    marked = cg.grover_marked(n, seed=2017)
+    r = 12  # of the 12867 iterations; the closed form holds after any number
+    with qs.Simulator(n, precision=prec, fusion=fusion) as sim:
+        sim.run(cg.grover_ops(n, marked, iterations=r))
+        am = sim.get_amplitudes(marked, 1)[0]
+        others = sim.get_amplitudes(0, 64)
+        p1, nrm = sim.probs_all()
+    theta = math.asin(2.0 ** (-n / 2))
+    sign = (-1) ** r
+    a_m = sign * math.sin((2 * r + 1) * theta)
+    a_o = sign * math.cos((2 * r + 1) * theta) / math.sqrt((1 << n) - 1)
+    tol = 1e-6 if prec == "c64" else 1e-12
+    rel = 1e-4 if prec == "c64" else 1e-9  # relative to the unmarked amplitude
+    assert abs(am - a_m) <= tol
+    mask = np.arange(64) != marked
+    err = np.max(np.abs(others[mask] - a_o)) / abs(a_o)
+    print("Grover-28 %s: marked error %.3e, unmarked relative error %.3e" % (prec, abs(am - a_m), err))
+    assert err <= rel
+    # P(q = 1) from the closed form
+    want = np.array([((marked >> q) & 1) * a_m ** 2 + a_o ** 2 * ((1 << (n - 1)) - ((marked >> q) & 1))
+                     for q in range(n)])
+    np.testing.assert_allclose(p1, want, atol=10 * tol)
+    _free()
+
+
+def test_measure_all_30_against_host_cumsum(qs):
+    n = 30
+    ops = cg.random_u3_brickwork(n, 2, seed=5)
+    u = float(cg.uniform_draws(8092, 1)[0])
+    with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
+        sim.run(ops)
+        psi = sim.get_amplitudes()
+        j = sim.measure_all(u)
+        after = sim.get_amplitudes(j, 1)[0]
+        p1, nrm = sim.probs_all()
+    w = (psi.real ** 2 + psi.imag ** 2)
+    c = np.cumsum(w)
+    jr = int(np.searchsorted(c, u * c[-1], side="right"))
+    assert j == jr or abs(c[min(j, jr)] - u * c[-1]) < 1e-6 * c[-1]
+    assert abs(abs(after) - 1.0) < 1e-6 and abs(nrm - 1.0) < 1e-6
+    np.testing.assert_allclose(p1, [(j >> q) & 1 for q in range(n)], atol=1e-6)
+    _free()

@@ -1,0 +1,113 @@
+"""The learned planner: GPU-trained cost-model network against the FP64
+oracle network (forward and gradient), training, the simulator's own
+timing records, and the planner it drives (correct states; measured gain
+over greedy fusion)."""
+import time
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+from helpers import TOL64_INFID, infidelity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1612_08091_gb300 as q
+
+    q.load()
+    return q
+
+
+def test_forward_and_gradient_match_fp64_oracle(qs):
+    from oracle import mlp as omlp
+    from paper_1612_08091_gb300.qsim import MLP
+
+    rng = np.random.default_rng(3)
+    for H, B in ((8, 5), (32, 300)):
+        net = MLP(hidden=H, seed=11)
+        p = net.params.astype(np.float64)
+        X = rng.normal(size=(B, 16)).astype(np.float32)
+        T = rng.normal(size=B).astype(np.float32)
+        y = net.forward(X)
+        np.testing.assert_allclose(y, omlp.forward(p, X, H), rtol=1e-4, atol=1e-4)
+        g, loss = net.gradient(X, T)
+        l_ref, g_ref = omlp.loss_and_grad(p, X, T, H)
+        assert abs(loss - l_ref) <= 1e-4 * max(1.0, abs(l_ref))
+        rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+        assert rel <= 1e-3, rel
+        net.close()
+
+
+def test_training_reduces_loss(qs):
+    from paper_1612_08091_gb300.qsim import MLP
+
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, size=(2000, 16)).astype(np.float32)
+    T = (np.sin(2 * X[:, 0]) + 0.5 * X[:, 1] ** 2 - X[:, 2] * X[:, 3]).astype(np.float32)
+    net = MLP(hidden=32, seed=2)
+    _, l0 = net.gradient(X, T)
+    l1 = net.train(X, T, epochs=150, batch=128, lr=3e-3)
+    assert l1 < 0.1 * l0, (l0, l1)
+    net.close()
+
+
+def test_item_time_records(qs):
+    n = 20
+    with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
+        sim.set_profiling(2)
+        sim.run(cg.random_u3_brickwork(n, 3, seed=1))
+        sim.flush()
+        feats, ms = sim.item_times()
+        st = sim.stats()
+    assert len(ms) == st["passes"] and len(ms) > 0
+    assert np.all(ms > 0)
+    np.testing.assert_allclose(feats[:, 0], n / 32.0)
+    np.testing.assert_allclose(feats[:, 15], 1.0)
+
+
+def _wall(qs, n, ops, fusion, model=None, reps=3):
+    ts = []
+    with qs.Simulator(n, precision="c64", fusion=fusion) as sim:
+        if model is not None:
+            sim.set_cost_model(*model)
+        for _ in range(reps + 1):
+            sim.reset(0)
+            import torch
+
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.run(ops)
+            sim.flush()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        psi = sim.get_amplitudes()
+        pred = sim.plan_predicted_ms() if model is not None else None
+    return float(np.median(ts[1:])), psi, pred
+
+
+def test_learned_planner_end_to_end(qs, oracle_mod):
+    from paper_1612_08091_gb300 import costmodel
+
+    X, ms = costmodel.collect(sizes=(20, 21, 22), precisions=("c64",), seed=7)
+    params, loss = costmodel.train(X, ms, hidden=32, epochs=150)
+    assert loss < 0.5, loss
+    model = (params, 32)
+    n = 22
+    for name, ops in (("qft", cg.basis_prep_ops(5, n) + cg.qft_ops(n)),
+                      ("random", cg.random_u3_brickwork(n, 8, seed=2018))):
+        t_greedy, psi_g, _ = _wall(qs, n, ops, "greedy")
+        t_mlp, psi_m, pred = _wall(qs, n, ops, "mlp", model)
+        ref = oracle_mod.OracleSim(n)
+        oracle_mod.run_ops(ref, ops)
+        assert infidelity(ref.psi, psi_m) <= TOL64_INFID
+        assert infidelity(ref.psi, psi_g) <= TOL64_INFID
+        print("%s n=%d: greedy %.2f ms, learned %.2f ms (predicted %.2f ms), gain %.2fx"
+              % (name, n, 1e3 * t_greedy, 1e3 * t_mlp, pred, t_greedy / t_mlp))
+        # the learned plan must not be clearly worse than greedy fusion
+        assert t_mlp <= 1.25 * t_greedy + 2e-3
