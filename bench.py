@@ -25,6 +25,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -51,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-gates", type=int, default=6, help="gates of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--workload", default="random", choices=["random", "vqe", "planner"],
+                    help="random: the headline line; vqe / planner: secondary measurements")
     return ap.parse_args()
 
 
@@ -379,10 +383,119 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# secondary workloads (their own JSON lines; not the headline)
+# ---------------------------------------------------------------------------
+def run_vqe(args):
+    """4096 hardware-efficient-ansatz circuits (n uniform 10..20, L 2..8),
+    TFIM energies, one persistent launch replayed from a CUDA graph."""
+    import torch
+
+    import paper_1612_08091_gb300 as q
+
+    torch.cuda.set_device(0)
+    circuits = cg.hea_batch(4096, seed=2016)
+    nq = [c["n"] for c in circuits]
+    nl = [c["L"] for c in circuits]
+    angles = q.hea_angles(circuits)
+    upd = float(sum((1 << c["n"]) * (c["L"] * (3 * c["n"] - 1)) for c in circuits))
+    with q.Batch(nq, nl) as b:
+        t0 = time.perf_counter()
+        cfg = b.autotune(angles, reps=3)
+        tune_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            b.run(angles)
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            e = b.run(angles)
+            ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    out = {"metric": "variational batch throughput", "value": upd / t, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+           "dtype": "c64", "data": "synthetic",
+           "config": {"workload": "4096 ansatz circuits, n uniform in 10..20, L in 2..8, RY/RZ + CNOT ladder, "
+                                  "TFIM energy (seed 2016)", "circuits_per_s": 4096 / t,
+                      "amp_updates_per_step": upd, "autotuned": {"threads": cfg[0], "smem_qubits": cfg[1]},
+                      "autotune_s": tune_s, "timing": "host clock around sim_batch_run (graph replay: angles "
+                                                      "H2D, persistent kernel, energies D2H)"},
+           "check": {"energy_mean": float(np.mean(e))}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_planner(args):
+    """Held-out 33-qubit complex64 random circuits of depth 30: the learned
+    planner (trained here on this GPU's timings of 26-28 qubit circuits)
+    against greedy fusion (k <= 5); unfused complex128 on a sample."""
+    import torch
+
+    import paper_1612_08091_gb300 as q
+    from paper_1612_08091_gb300 import costmodel
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    X, ms = costmodel.collect(sizes=(26, 27, 28), precisions=("c64",), seed=2018)
+    collect_s = time.perf_counter() - t0
+    params, loss = costmodel.train(X, ms, hidden=32, epochs=300)
+    n = 33
+    ops = cg.random_u3_brickwork(n, 30, seed=2018)
+    upd = amp_updates(ops, n)
+
+    def timed(fusion, model=None):
+        with q.Simulator(n, precision="c64", fusion=fusion) as sim:
+            if model is not None:
+                sim.set_cost_model(*model)
+            res = []
+            for _ in range(args.warmup + args.steps):
+                sim.reset(0)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                sim.run(ops)
+                sim.flush()
+                torch.cuda.synchronize()
+                res.append(time.perf_counter() - t1)
+            st = sim.stats()
+        torch.cuda.empty_cache()
+        return statistics.median(res[args.warmup:]), st["passes"] / (args.warmup + args.steps)
+
+    t_greedy, p_greedy = timed("greedy")
+    t_mlp, p_mlp = timed("mlp", (params, 32))
+    # plain complex128 on the first layer, extrapolated per amplitude update
+    layer = ops[: n + len(range(0, n - 1, 2))]
+    with q.Simulator(n, precision="c128", fusion="none") as ps:
+        ps.run(layer[:2])
+        ps.flush()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ps.run(layer)
+        ps.flush()
+        torch.cuda.synchronize()
+        t_layer = time.perf_counter() - t1
+    rate_plain = amp_updates(layer, n) / t_layer
+    out = {"metric": "learned fusion planner, held-out 33-qubit circuit", "value": upd / t_mlp, "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_mlp,
+           "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+           "config": {"workload": "33-qubit random U3 + CNOT brickwork, depth 30 (seed 2018), complex64",
+                      "training": {"samples": int(len(ms)), "sizes": [26, 27, 28], "collect_s": collect_s,
+                                   "train_mse_log_ms": loss}},
+           "greedy_k5": {"ms": 1e3 * t_greedy, "passes": p_greedy, "value": upd / t_greedy},
+           "learned": {"ms": 1e3 * t_mlp, "passes": p_mlp, "gain_over_greedy": t_greedy / t_mlp},
+           "plain_c128": {"value": rate_plain, "unit": UNIT,
+                          "sample": "first layer (%d gates), fp64 arithmetic" % len(layer),
+                          "extrapolated_ms": 1e3 * upd / rate_plain}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "vqe":
+        return run_vqe(args)
+    if args.workload == "planner":
+        return run_planner(args)
     return run_ours(args)
 
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -63,7 +64,8 @@ double gate_bytes(const qsim *s, const GateRec &g) {
     return 2.0 * b * std::ldexp(1.0, s->n - fixed);
 }
 
-const char *kClassName[KC_COUNT] = {"gate_dense", "gate_phase", "gate_diag", "gate_x", "block_tc", "block_dense"};
+const char *kClassName[KC_COUNT] = {"gate_dense", "gate_phase", "gate_diag", "gate_x",
+                                    "block_tc",   "block_dense", "block_diag"};
 
 int harvest(qsim *s) {
     if (s->pending.empty()) return QSIM_OK;
@@ -125,6 +127,10 @@ int execute_plan(qsim *s, const std::vector<PlanItem> &plan) {
             rc = launch_gate_plain(s, g);
             bytes = gate_bytes(s, g);
             cls = gate_class(g);
+        } else if (it.diag_block) {
+            cls = KC_BLOCK_DIAG;
+            rc = launch_block_diag(s, it.dmask, it.dtab.data());
+            bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
         } else {
             rc = QSIM_ENOTSUP;
             cls = KC_BLOCK_TC;
@@ -244,6 +250,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->tc_enabled = o.no_tensor_cores == 0;
     s->norm_tracking = o.no_norm_tracking == 0;
     s->c128_df = o.c128_double_float != 0;
+    if (const char *v = getenv("QSIM_TC_KERNEL")) s->tc_variant = (v[0] == 'w') ? 1 : 0;
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
@@ -335,6 +342,13 @@ int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const in
     g.m.resize((size_t)D * D);
     for (int i = 0; i < D * D; ++i) g.m[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
     g.kind = classify(g);
+    g.diag = true;
+    for (int r = 0; r < D && g.diag; ++r)
+        for (int c = 0; c < D; ++c)
+            if (r != c && g.m[(size_t)r * D + c] != 0.0) {
+                g.diag = false;
+                break;
+            }
     s->queue.push_back(std::move(g));
     s->stats.gates++;
     return QSIM_OK;

@@ -1,0 +1,132 @@
+// diag_kernels.cu -- a block of diagonal gates applied in one pass.
+//
+// Gates whose matrices are diagonal (Z, S, T, R(phi), RZ, CZ, controlled
+// phases, multi-controlled Z) only multiply each amplitude by a phase that
+// depends on the bits of its index on the gate's qubits, and they commute
+// with one another.  A run of them over a qubit set S (|S| <= 12) is one
+// table d of 2^|S| factors (built on the host in FP64: the product of the
+// gates' diagonal entries for every assignment of S), and the pass is
+//     psi_i <- d[bits of i on S] * psi_i.
+// The phase ladders of the QFT (ProjectQ paper, Sec. 3: the constant adder
+// is QFT, phase shifts, inverse QFT) and the controlled z-rotation chain of
+// the simulator benchmark (Sec. 4.3.2, Fig. 7) are made of such gates.
+//
+// The table and five 256-entry bit-gather tables (index bits 0..39 -> bits
+// of the table index) are copied to shared memory per CTA; each thread
+// handles 16 bytes of amplitudes per step (two complex64 or one complex128).
+// complex128 uses FP64 products, or double-float products when the handle
+// runs complex128 gates in double-float arithmetic.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "df128.cuh"
+#include "internal.h"
+
+using namespace qsim_dev;
+
+namespace {
+
+constexpr int kDiagThreads = 256;
+
+template <typename Amp>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_block(Amp *__restrict__ psi, uint64_t N, int k,
+                                                            const unsigned char *__restrict__ rec, int use_df) {
+    extern __shared__ unsigned char sm_raw[];
+    Amp *d = (Amp *)sm_raw;
+    uint16_t *gather = (uint16_t *)(sm_raw + (sizeof(Amp) << k));  // [5][256]
+    const int D = 1 << k;
+    const Amp *gd = (const Amp *)rec;
+    const uint16_t *gg = (const uint16_t *)(rec + (sizeof(Amp) << k));
+    for (int i = threadIdx.x; i < D; i += blockDim.x) d[i] = gd[i];
+    for (int i = threadIdx.x; i < 5 * 256; i += blockDim.x) gather[i] = gg[i];
+    __syncthreads();
+    auto tidx = [&](uint64_t i) {
+        return (unsigned)gather[i & 255] | gather[256 + ((i >> 8) & 255)] | gather[512 + ((i >> 16) & 255)] |
+               gather[768 + ((i >> 24) & 255)] | gather[1024 + ((i >> 32) & 255)];
+    };
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (sizeof(Amp) == 8) {
+        // two complex64 per 16-byte access
+        float4 *p4 = (float4 *)psi;
+        for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < N / 2; j += stride) {
+            float4 v = p4[j];
+            const float2 a = cmul(((const float2 *)d)[tidx(2 * j)], make_float2(v.x, v.y));
+            const float2 b = cmul(((const float2 *)d)[tidx(2 * j + 1)], make_float2(v.z, v.w));
+            p4[j] = make_float4(a.x, a.y, b.x, b.y);
+        }
+    } else {
+        double2 *p2 = (double2 *)psi;
+        const double2 *dd = (const double2 *)d;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+            const double2 z = dd[tidx(i)];
+            if (use_df) {
+                const qsim_df::C2 u = qsim_df::split(z);
+                p2[i] = qsim_df::to_double(qsim_df::cmul(u, qsim_df::split(p2[i])));
+            } else {
+                p2[i] = cmul(z, p2[i]);
+            }
+        }
+    }
+}
+
+template <typename Amp> Amp to_amp(cd z);
+template <> double2 to_amp<double2>(cd z) { return make_double2(z.real(), z.imag()); }
+template <> float2 to_amp<float2>(cd z) { return make_float2((float)z.real(), (float)z.imag()); }
+
+template <typename Amp>
+int diag_block(qsim *s, uint64_t dmask, const cd *dt) {
+    const int k = __builtin_popcountll(dmask);
+    if (k < 1 || k > kMaxDiagQubits) return set_err(s, QSIM_EINVAL, "diagonal block width");
+    // record: table (2^k Amp) then 5 x 256 uint16 gather tables
+    const size_t tbytes = sizeof(Amp) << k, gbytes = 5 * 256 * sizeof(uint16_t);
+    std::vector<unsigned char> rec(tbytes + gbytes);
+    std::vector<Amp> tab(1u << k);
+    for (int r = 0; r < (1 << k); ++r) tab[r] = to_amp<Amp>(dt[r]);
+    std::memcpy(rec.data(), tab.data(), tbytes);
+    int pos[64], np = 0;
+    for (int b = 0; b < 64; ++b)
+        if ((dmask >> b) & 1ull) pos[b] = np++;
+        else pos[b] = -1;
+    std::vector<uint16_t> g(5 * 256, 0);
+    for (int c = 0; c < 5; ++c)
+        for (int v = 0; v < 256; ++v) {
+            uint16_t r = 0;
+            for (int bit = 0; bit < 8; ++bit)
+                if ((v >> bit) & 1) {
+                    const int b = 8 * c + bit;
+                    if (b < 64 && pos[b] >= 0) r |= (uint16_t)(1u << pos[b]);
+                }
+            g[c * 256 + v] = r;
+        }
+    std::memcpy(rec.data() + tbytes, g.data(), gbytes);
+    unsigned char *dev = nullptr;
+    int rc = stage_operand(s, rec.data(), rec.size(), &dev);
+    if (rc) return rc;
+    const size_t smem = tbytes + gbytes;
+    static bool attr[2][64] = {{false}};
+    const int which = sizeof(Amp) == 8 ? 0 : 1;
+    if (s->device >= 0 && s->device < 64 && !attr[which][s->device]) {
+        cudaError_t e = cudaFuncSetAttribute(k_diag_block<Amp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((sizeof(Amp) << kMaxDiagQubits) + gbytes));
+        if (e != cudaSuccess) return cuda_err(s, e, "diagonal kernel attribute");
+        attr[which][s->device] = true;
+    }
+    const uint64_t N = 1ull << s->n;
+    const uint64_t work = sizeof(Amp) == 8 ? N / 2 : N;
+    uint64_t grid = (work + kDiagThreads - 1) / kDiagThreads;
+    if (grid > (uint64_t)kSMs * 8) grid = (uint64_t)kSMs * 8;
+    k_diag_block<Amp><<<(unsigned)grid, kDiagThreads, smem, s->stream>>>((Amp *)s->state, N, k, dev,
+                                                                           s->c128_df ? 1 : 0);
+    s->stats.launches++;
+    return cuda_err(s, cudaGetLastError(), "diagonal block launch");
+}
+
+}  // namespace
+
+int launch_block_diag(qsim *s, uint64_t dmask, const cd *d) {
+    if (s->n < 2) return set_err(s, QSIM_ENOTSUP, "diagonal block needs n >= 2");
+    return s->prec == QSIM_C128 ? diag_block<double2>(s, dmask, d) : diag_block<float2>(s, dmask, d);
+}

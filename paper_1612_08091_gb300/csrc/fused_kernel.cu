@@ -26,8 +26,8 @@
 // V always contains qubits 0..6 (or more), so every tile is made of runs of
 // at least 128 contiguous amplitudes.
 //
-// Per CTA (persistent, 128 threads, up to four CTAs per SM, ~51 KB of shared
-// memory and 64 TMEM columns each):
+// Per CTA (persistent, 128 threads, two CTAs per SM, ~85 KB of shared memory
+// and 128 TMEM columns each):
 //   - one TMA bulk copy brings the gate operand R1, R2(, R3) (pre-swizzled
 //     on the host) and the tile index tables into shared memory;
 //   - each thread loads 32 amplitudes of a tile with 16-byte loads, splits
@@ -36,10 +36,9 @@
 //     chosen per block so these writes are free of bank conflicts);
 //   - thread 0 issues 12 (or 20) tcgen05.mma (M128 N64 K16) into the TMEM
 //     accumulator and commits them to an mbarrier;
-//   - the next tile's loads go out while the tensor cores work; then the
-//     four warps read the accumulator with tcgen05.ld (warp w owns TMEM
-//     lanes 32w..32w+31 = tile columns) and store it.  The other CTAs on the
-//     SM keep HBM busy meanwhile.
+//   - while the tensor cores work on tile t and the loads of tile t+1 are in
+//     flight, the four warps read tile t-1's accumulator with tcgen05.ld
+//     (warp w owns TMEM lanes 32w..32w+31 = tile columns) and store it.
 // Every wait is bounded; on time-out the kernel raises an error flag in the
 // workspace, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -48,6 +47,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -61,30 +62,47 @@ constexpr int kTcThreads = 128;
 constexpr int kTile = 4096;              // amplitudes per tile (2^12)
 constexpr int kABytes = 128 * 128;       // one bf16 split of X: 128 rows x 128 B
 constexpr int kBBytes = 64 * 128;        // one bf16 split of R: 64 rows x 128 B
-constexpr int kTablesBytes = 2816;
-constexpr uint32_t kTmemCols = 64;       // one 64-column fp32 accumulator
+constexpr int kTablesBytes = 4560;
+constexpr uint32_t kTmemCols = 128;      // two 64-column fp32 accumulators
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMaxTcGrid = 4 * kSMs;
 
 // Layout of the per-block operand record (host-built, copied to smem as is).
-// Thread tid loads tile elements e = e0(tid) | ei(i) | h for i < 16, h < 2
-// (bit sets of e0, ei and h disjoint): the address, block row r and tile
-// column c of e are the ORs of the parts.  The split of the 11 element bits
-// into 5 lane bits, 2 warp bits and 4 loop bits is chosen per block so that
-// a warp's writes of the bf16 operand hit 32 distinct banks and its 16-byte
-// loads fill whole 32-byte sectors.
+// Thread t handles tile elements e = e0(t) | ei(i) | h (bit sets disjoint):
+// the address, block row r and tile column c of e are the ORs of the parts.
+// The 11 element bits above h are ordered as 5 lane bits L and 6 more bits
+// E0..E5; e0(t) takes L from t mod 32 and E0.. from t / 32, ei(i) takes
+// E2..E5 from i.  k_block_tc (128 threads) uses E0,E1 for its warps and 16
+// loop steps i; k_block_tc_ws (256 converter threads) uses E0..E2 for its
+// warps and the 8 steps ei(2i).  L is chosen per block so that a warp's
+// writes of the bf16 operand hit 32 distinct banks and its 16-byte loads
+// fill whole 32-byte sectors.
 struct RecTables {
-    uint64_t a0[128];    // address bits of e0(tid)
+    uint64_t a0[256];    // address bits of e0(t) for thread t (k_block_tc: t < 128)
     uint64_t cdep[128];  // address bits of tile column c (epilogue)
     uint64_t ai[16];     // address bits of ei(i)
     uint64_t rdep[32];   // address bits of block row r (epilogue)
-    uint8_t r0[128], c0[128];  // row / column bits of e0(tid)
+    uint16_t e0[256];    // element bits e0(t) (staged-tile offset of k_block_tc_ws)
+    uint16_t ei[16];     // element bits ei(i)
+    uint8_t r0[256], c0[256];  // row / column bits of e0(t)
     uint8_t ri[16], ci[16];    // row / column bits of ei(i)
     uint8_t rh, ch;            // row / column bit of h (address bit 0)
     uint8_t pair_r;            // 1 if rows r, r+1 are adjacent in memory (qubit 0 in S)
-    uint8_t pad[93];
+    uint8_t pad[13];
 };
 static_assert(sizeof(RecTables) == kTablesBytes, "table layout");
+
+// Contiguous runs of a tile for the TMA producer of k_block_tc_ws: the tile's
+// lowest p element bits are address bits 0..p-1, so it is 2^(12-p) runs of
+// 2^p amplitudes; run j starts at element j << p.
+struct RunTable {
+    uint64_t run_off[32];  // address bits of run j (relative to the tile base)
+    uint32_t nruns;
+    uint32_t run_amps;
+    uint32_t pad[2];
+};
+constexpr int kRunBytes = sizeof(RunTable);
+static_assert(kRunBytes % 16 == 0, "run table size");
 
 struct TcArgs {
     float2 *psi;
@@ -175,6 +193,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive fp32 columns of this warp's 32 TMEM lanes; the wait is in
+// the same asm statement, so the registers are complete when it returns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_half, float hi_half) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo_half, hi_half);
     uint32_t u;
@@ -198,6 +234,8 @@ __device__ __forceinline__ void put_amp(unsigned char *a_hi, unsigned char *a_lo
     *(uint32_t *)(a_lo + off) = lw;
 }
 
+__device__ __forceinline__ float2 *psi_ptr(const TcArgs &a) { return a.psi; }
+
 // Two amplitudes of the same column at rows r (even) and r+1: one 8-byte
 // write per split.
 __device__ __forceinline__ void put_amp2(unsigned char *a_hi, unsigned char *a_lo, int c, int r, float4 v) {
@@ -218,13 +256,14 @@ __device__ __forceinline__ void put_amp2(unsigned char *a_hi, unsigned char *a_l
     *(uint2 *)(a_lo + off) = lw;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 4) k_block_tc(const TcArgs args) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *A = smem;                           // [2 split][kABytes]
-    unsigned char *B = smem + 2 * kABytes;             // [nsplit][kBBytes] then tables
+    unsigned char *A = smem;                           // [2 buf][2 split][kABytes]
+    unsigned char *B = smem + 4 * kABytes;             // [nsplit][kBBytes] then tables
     const RecTables *tab = (const RecTables *)(B + args.nsplit * kBBytes);
-    uint64_t *bars = (uint64_t *)(B + args.nsplit * kBBytes + kTablesBytes);  // [0]=operand, [1],[2]=mma
+    // barriers after the copied record (tables and run table)
+    uint64_t *bars = (uint64_t *)(B + args.nsplit * kBBytes + kTablesBytes + kRunBytes);  // [0]=operand, [1],[2]=mma
     uint32_t *tmem_slot = (uint32_t *)(bars + 3);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *s_scale = (float *)(tmem_slot + 2);
@@ -301,32 +340,33 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_block_tc(const TcArgs args) {
             for (int i = 0; i < 16; ++i) regs[i] = *(const float4 *)(p + tab->ai[i]);
         };
         auto epilogue = [&](uint64_t tt, int j) {
-            if (!mbar_wait(&bars[1], (uint32_t)(j & 1))) {
+            const int buf = j & 1;
+            if (!mbar_wait(&bars[1 + buf], (uint32_t)((j >> 1) & 1))) {
                 atomicOr(args.err, 2u);
                 *abort_flag = 1;
                 return;
             }
             tc_fence_after();
             const uint64_t base = insert_zeros(tt, args.vspec) + my_cdep;
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 64);
             float ssq = 0.f;
 #pragma unroll
-            for (int chunk = 0; chunk < 4; ++chunk) {
-                float v[16];
-                tmem_ld16(taddr + chunk * 16, v);
+            for (int chunk = 0; chunk < 2; ++chunk) {
+                float v[32];
+                tmem_ld32(taddr + chunk * 32, v);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) ssq = fmaf(v[q], v[q], ssq);
+                for (int q = 0; q < 32; ++q) ssq = fmaf(v[q], v[q], ssq);
                 if (pair_r) {
 #pragma unroll
-                    for (int q = 0; q < 8; q += 2) {
-                        const int r = chunk * 8 + q;
+                    for (int q = 0; q < 16; q += 2) {
+                        const int r = chunk * 16 + q;
                         *(float4 *)(psi + base + tab->rdep[r]) = make_float4(
                             v[2 * q] * scale, v[2 * q + 1] * scale, v[2 * q + 2] * scale, v[2 * q + 3] * scale);
                     }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int r = chunk * 8 + q;
+                    for (int q = 0; q < 16; ++q) {
+                        const int r = chunk * 16 + q;
                         psi[base + tab->rdep[r]] = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
                     }
                 }
@@ -335,14 +375,15 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_block_tc(const TcArgs args) {
             tc_fence_before();
         };
 
-        // One A buffer and one accumulator: tile t is converted, multiplied
-        // and stored before tile t+1 is converted; the loads of tile t+1 are
-        // in flight while the tensor cores work on tile t and while tile t is
-        // stored, and the other CTAs on the SM overlap the rest.
+        // Two A buffers and two accumulators: while the tensor cores work on
+        // tile t, the loads of tile t+1 are in flight and tile t-1 is read
+        // out of tensor memory and stored.
         if (t < args.ntiles) load_tile(t);
         int it = 0;
-        unsigned char *a_hi = A, *a_lo = A + kABytes;
         for (; t < args.ntiles; t += gridDim.x, ++it) {
+            const int buf = it & 1;
+            unsigned char *a_hi = A + (2 * buf) * kABytes;
+            unsigned char *a_lo = A + (2 * buf + 1) * kABytes;
             float xsq = 0.f;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
@@ -363,6 +404,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_block_tc(const TcArgs args) {
             if (*abort_flag) break;
             if (tid == 0) {
                 tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * 64);
                 const uint32_t ahi = smem_u32(a_hi), alo = smem_u32(a_lo);
                 const uint32_t b0 = smem_u32(B), b1 = b0 + kBBytes, b2 = b0 + 2 * kBBytes;
                 uint32_t acc = 0;
@@ -372,17 +414,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_block_tc(const TcArgs args) {
                     const uint32_t b = term < 2 ? b0 : (term < 4 ? b1 : b2);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        mma_bf16(tmem, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), acc);
+                        mma_bf16(d, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), acc);
                         acc = 1;
                     }
                 }
-                mma_commit(&bars[1]);
+                mma_commit(&bars[1 + buf]);
             }
             const uint64_t tn = t + gridDim.x;
             if (tn < args.ntiles) load_tile(tn);
-            epilogue(t, it);
-            if (*abort_flag) break;
+            if (it >= 1) epilogue(t - gridDim.x, it - 1);
         }
+        if (it >= 1 && !*abort_flag) epilogue(t - gridDim.x, it - 1);
     }
     // per-CTA norm sums, fixed reduction order
     nrm_in = warp_sum(nrm_in);
@@ -398,6 +440,284 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_block_tc(const TcArgs args) {
         args.norm_out[kMaxTcGrid + blockIdx.x] = s_red[1] + s_red[3] + s_red[5] + s_red[7];
     }
     if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Warp-specialised variant: one CTA per SM, 10 warps.
+//   warp 0     TMA producer: for every tile, the contiguous runs (>= 1 KB
+//              each) go into a 3-stage FP32 staging ring by cp.async.bulk,
+//              completing on the stage's mbarrier;
+//   warp 1     owns TMEM and issues the MMAs of tile j into accumulator j%2
+//              once its A operand is complete and the epilogue has drained
+//              that accumulator;
+//   warps 2-9  convert a staged tile into the bf16 hi/lo A operand (buffer
+//              j%2), then read the previous tile's accumulator (warp w owns
+//              TMEM lanes 32(w%4).. and half (w-2)/4 of the 64 columns) and
+//              store it to global memory.
+// Hand-offs (all mbarriers, all waits bounded): stage full (TMA bytes) /
+// stage empty (8 converter warps), A full (8 warps) / A empty (MMA commit),
+// accumulator full (MMA commit) / accumulator empty (8 epilogue warps).
+// ---------------------------------------------------------------------------
+constexpr int kWsThreads = 320;  // producer, MMA, 8 converter / epilogue warps
+constexpr int kWsConv = 8;
+constexpr int kStages = 3;
+constexpr int kStageBytes = kTile * 8;
+
+__global__ void __launch_bounds__(kWsThreads, 1) k_block_tc_ws(const TcArgs args) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *stage_buf = smem;                               // [kStages][kStageBytes]
+    unsigned char *A = smem + kStages * kStageBytes;               // [2 buf][2 split][kABytes]
+    unsigned char *B = A + 4 * kABytes;                            // [nsplit][kBBytes], tables, runs
+    const RecTables *tab = (const RecTables *)(B + args.nsplit * kBBytes);
+    const RunTable *runs = (const RunTable *)(B + args.nsplit * kBBytes + kTablesBytes);
+    uint64_t *bars = (uint64_t *)(B + args.nsplit * kBBytes + kTablesBytes + kRunBytes);
+    uint64_t *op_bar = bars;               // operand record
+    uint64_t *st_full = bars + 1;          // [kStages]
+    uint64_t *st_empty = bars + 4;         // [kStages]
+    uint64_t *a_full = bars + 7;           // [2]
+    uint64_t *a_empty = bars + 9;          // [2]
+    uint64_t *d_full = bars + 11;          // [2]
+    uint64_t *d_empty = bars + 13;         // [2]
+    uint32_t *tmem_slot = (uint32_t *)(bars + 15);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *s_scale = (float *)(tmem_slot + 2);
+    volatile int *s_issued = (volatile int *)(tmem_slot + 3);
+    volatile int *s_consumed = (volatile int *)(tmem_slot + 4);
+    double *s_red = (double *)(bars + 18);  // [8 warps][2]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(op_bar, 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&st_full[i], 1);
+            mbar_init(&st_empty[i], kWsConv);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a_full[i], kWsConv);
+            mbar_init(&a_empty[i], 1);
+            mbar_init(&d_full[i], 1);
+            mbar_init(&d_empty[i], kWsConv);
+        }
+        *abort_flag = 0;
+        *s_issued = 0;
+        *s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        float sc = 1.0f;
+        if (args.norm_prev) {
+            double a = 0.0, b = 0.0;
+            for (int i = 0; i < args.prev_grid; ++i) {
+                a += args.norm_prev[i];
+                b += args.norm_prev[kMaxTcGrid + i];
+            }
+            if (a > 0.0 && b > 0.0 && a < 1e300 && b < 1e300) sc = (float)sqrt(a / b);
+        }
+        *s_scale = sc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(op_bar)),
+                     "r"(args.rec_bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(B)),
+                     "l"(args.rec), "r"(args.rec_bytes), "r"(smem_u32(op_bar))
+                     : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (!mbar_wait(op_bar, 0)) {
+        atomicOr(args.err, 4u);
+        *abort_flag = 1;
+    }
+    __syncthreads();
+
+    const uint64_t ntiles = args.ntiles;
+    const int my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    double nrm_in = 0.0, nrm_out = 0.0;
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        const uint32_t nr = runs->nruns, ra = runs->run_amps;
+        for (int j = 0; j < my_tiles && !*abort_flag; ++j) {
+            const int st = j % kStages;
+            if (j >= kStages && !mbar_wait(&st_empty[st], (uint32_t)(((j / kStages) - 1) & 1))) {
+                if (lane == 0) atomicOr(args.err, 8u);
+                *abort_flag = 1;
+                break;
+            }
+            const uint64_t t = blockIdx.x + (uint64_t)j * gridDim.x;
+            const uint64_t base = insert_zeros(t, args.vspec);
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&st_full[st])),
+                             "r"((uint32_t)kStageBytes)
+                             : "memory");
+            __syncwarp();
+            for (uint32_t r = lane; r < nr; r += 32) {
+                const float2 *src = args.psi + base + runs->run_off[r];
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(stage_buf + st * kStageBytes + (size_t)r * ra * 8)),
+                    "l"(src), "r"(ra * 8), "r"(smem_u32(&st_full[st]))
+                    : "memory");
+            }
+            if (lane == 0) *s_issued = j + 1;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        const int nterms = args.nsplit == 3 ? 5 : 3;
+        for (int j = 0; j < my_tiles && !*abort_flag; ++j) {
+            const int buf = j & 1;
+            bool ok = mbar_wait(&a_full[buf], (uint32_t)((j >> 1) & 1));
+            if (ok && j >= 2) ok = mbar_wait(&d_empty[buf], (uint32_t)(((j >> 1) - 1) & 1));
+            if (!ok) {
+                if (lane == 0) atomicOr(args.err, 16u);
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t d = tmem + (uint32_t)(buf * 64);
+                const uint32_t ahi = smem_u32(A + (2 * buf) * kABytes), alo = smem_u32(A + (2 * buf + 1) * kABytes);
+                const uint32_t b0 = smem_u32(B), b1 = b0 + kBBytes, b2 = b0 + 2 * kBBytes;
+                uint32_t acc = 0;
+                for (int term = 0; term < nterms; ++term) {
+                    const uint32_t a = (term == 1 || term == 3) ? alo : ahi;
+                    const uint32_t b = term < 2 ? b0 : (term < 4 ? b1 : b2);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        mma_bf16(d, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), acc);
+                        acc = 1;
+                    }
+                }
+                mma_commit(&a_empty[buf]);
+                mma_commit(&d_full[buf]);
+            }
+            __syncwarp();
+        }
+    } else {
+        // ---------------- converters / epilogue (warps 2..9) ----------------
+        const int ct = tid - 64;                  // 0..255: element mapping
+        const int quarter = warp & 3;             // TMEM lanes 32*quarter..
+        const int half = (warp - 2) >> 2;         // accumulator columns 32*half..
+        const int col = quarter * 32 + lane;      // tile column read back by this thread
+        const uint64_t my_cdep = tab->cdep[col];
+        const int r00 = tab->r0[ct], c00 = tab->c0[ct];
+        const int r01 = r00 | tab->rh, c01 = c00 | tab->ch;
+        const bool pair_r = tab->pair_r != 0;
+        const float scale = *s_scale;
+        // element e = e0(ct) | ei(i) | h of the staged tile sits at byte 8e
+        // (the runs are staged in element order)
+        auto epilogue = [&](int j) {
+            const int buf = j & 1;
+            if (!mbar_wait(&d_full[buf], (uint32_t)((j >> 1) & 1))) {
+                if (lane == 0) atomicOr(args.err, 32u);
+                *abort_flag = 1;
+                return false;
+            }
+            tc_fence_after();
+            const uint64_t t = blockIdx.x + (uint64_t)j * gridDim.x;
+            const uint64_t base = insert_zeros(t, args.vspec) + my_cdep;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 64 + half * 32);
+            float v[32];
+            tmem_ld32(taddr, v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&d_empty[buf])) : "memory");
+            float ssq = 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) ssq = fmaf(v[q], v[q], ssq);
+            nrm_out += (double)ssq;
+            const int r0 = half * 16;
+            if (pair_r) {
+#pragma unroll
+                for (int q = 0; q < 16; q += 2)
+                    *(float4 *)(psi_ptr(args) + base + tab->rdep[r0 + q]) =
+                        make_float4(v[2 * q] * scale, v[2 * q + 1] * scale, v[2 * q + 2] * scale, v[2 * q + 3] * scale);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    psi_ptr(args)[base + tab->rdep[r0 + q]] = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
+            }
+            return true;
+        };
+        for (int j = 0; j < my_tiles && !*abort_flag; ++j) {
+            const int st = j % kStages, buf = j & 1;
+            bool ok = mbar_wait(&st_full[st], (uint32_t)((j / kStages) & 1));
+            if (ok && j >= 2) ok = mbar_wait(&a_empty[buf], (uint32_t)(((j >> 1) - 1) & 1));
+            if (!ok) {
+                if (lane == 0) atomicOr(args.err, 64u);
+                *abort_flag = 1;
+                break;
+            }
+            const float4 *sb = (const float4 *)(stage_buf + st * kStageBytes);
+            unsigned char *a_hi = A + (2 * buf) * kABytes;
+            unsigned char *a_lo = A + (2 * buf + 1) * kABytes;
+            const unsigned e0 = tab->e0[ct];
+            float xsq = 0.f;
+#pragma unroll
+            for (int i2 = 0; i2 < 16; i2 += 2) {  // steps ei(2i): element bits E3..E5
+                const float4 x = sb[(e0 | tab->ei[i2]) >> 1];
+                xsq = fmaf(x.x, x.x, fmaf(x.y, x.y, xsq));
+                xsq = fmaf(x.z, x.z, fmaf(x.w, x.w, xsq));
+                const int ri = tab->ri[i2], ci = tab->ci[i2];
+                if (pair_r) {
+                    put_amp2(a_hi, a_lo, c00 | ci, r00 | ri, x);
+                } else {
+                    put_amp(a_hi, a_lo, c00 | ci, r00 | ri, x.x, x.y);
+                    put_amp(a_hi, a_lo, c01 | ci, r01 | ri, x.z, x.w);
+                }
+            }
+            nrm_in += (double)xsq;
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&st_empty[st])) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_full[buf])) : "memory");
+            }
+            if (tid == 64) *s_consumed = j + 1;
+            if (j >= 1 && !epilogue(j - 1)) break;
+        }
+        if (my_tiles >= 1 && !*abort_flag) epilogue(my_tiles - 1);
+    }
+    // on a time-out, let the producer's copies in flight land before exit
+    if (*abort_flag && warp == 0 && lane == 0) {
+        for (int j = *s_consumed; j < *s_issued; ++j) mbar_wait(&st_full[j % kStages], (uint32_t)((j / kStages) & 1));
+    }
+    // per-CTA norm sums (converter warps), fixed order
+    if (warp >= 2) {
+        nrm_in = warp_sum(nrm_in);
+        nrm_out = warp_sum(nrm_out);
+        if (lane == 0) {
+            s_red[2 * (warp - 2)] = nrm_in;
+            s_red[2 * (warp - 2) + 1] = nrm_out;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && args.norm_out) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kWsConv; ++w) {
+            a += s_red[2 * w];
+            b += s_red[2 * w + 1];
+        }
+        args.norm_out[blockIdx.x] = a;
+        args.norm_out[kMaxTcGrid + blockIdx.x] = b;
+    }
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");
@@ -451,6 +771,35 @@ void pad_to_five(int n, const int *q, int k, const cd *m, int *q5, std::vector<c
         }
 }
 
+void build_tables(int n, const int *S, RecTables &T, InsertSpec &vspec);
+
+// Index tables depend only on the block's qubits and the register size, so
+// they are built once per (S, n) and reused (the lane-mapping search is the
+// costly part of building them).
+struct TableCacheEntry {
+    RecTables T;
+    InsertSpec vspec;
+};
+std::mutex g_table_mutex;
+std::unordered_map<uint64_t, TableCacheEntry> g_table_cache;
+
+void cached_tables(int n, const int *S, RecTables &T, InsertSpec &vspec) {
+    uint64_t key = (uint64_t)n << 58;
+    for (int j = 0; j < 5; ++j) key |= 1ull << S[j];
+    {
+        std::lock_guard<std::mutex> lock(g_table_mutex);
+        auto it = g_table_cache.find(key);
+        if (it != g_table_cache.end()) {
+            T = it->second.T;
+            vspec = it->second.vspec;
+            return;
+        }
+    }
+    build_tables(n, S, T, vspec);
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    if (g_table_cache.size() < 4096) g_table_cache[key] = TableCacheEntry{T, vspec};
+}
+
 void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsigned char> &rec, InsertSpec &vspec) {
     // R[2r+a][2r'+b]: real 2x2 block of U[r][r']
     double R[64][64];
@@ -462,7 +811,7 @@ void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsi
             R[2 * r + 1][2 * c] = ui;
             R[2 * r + 1][2 * c + 1] = ur;
         }
-    rec.assign((size_t)nsplit * kBBytes + kTablesBytes, 0);
+    rec.assign((size_t)nsplit * kBBytes + kTablesBytes + kRunBytes, 0);
     for (int row = 0; row < 64; ++row)
         for (int k = 0; k < 64; ++k) {
             double rem = R[row][k];
@@ -473,6 +822,26 @@ void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsi
                 std::memcpy(&rec[(size_t)sp * kBBytes + off], &h, 2);
             }
         }
+    RecTables T;
+    cached_tables(n, S, T, vspec);
+    std::memcpy(&rec[(size_t)nsplit * kBBytes], &T, sizeof(T));
+    // runs: p = number of element bits that are address bits 0..p-1
+    int p = 0;
+    while (p < 12 && vspec.pos[p] == p) ++p;
+    RunTable RT;
+    std::memset(&RT, 0, sizeof(RT));
+    RT.nruns = 1u << (12 - p);
+    RT.run_amps = 1u << p;
+    for (uint32_t j = 0; j < RT.nruns; ++j) {
+        uint64_t a = 0;
+        for (int b = p; b < 12; ++b)
+            if (((j << p) >> b) & 1u) a |= 1ull << vspec.pos[b];
+        RT.run_off[j] = a;
+    }
+    std::memcpy(&rec[(size_t)nsplit * kBBytes + kTablesBytes], &RT, sizeof(RT));
+}
+
+void build_tables(int n, const int *S, RecTables &T, InsertSpec &vspec) {
     // V = S u F, F = lowest 7 qubits outside S
     uint64_t Smask = 0;
     for (int j = 0; j < 5; ++j) Smask |= 1ull << S[j];
@@ -490,7 +859,6 @@ void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsi
     vspec = InsertSpec{};
     vspec.m = 12;
     for (int j = 0; j < 12; ++j) vspec.pos[j] = V[j];
-    RecTables T;
     std::memset(&T, 0, sizeof(T));
     auto s_index = [&](int bit) {
         for (int j = 0; j < 5; ++j)
@@ -567,25 +935,23 @@ void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsi
             for (int j = 0; j < 5; ++j) best_lane[j] = lb[j];
         }
     }
-    int warp_bits[2], loop_bits[4], nw = 0, nl = 0;
+    int ebits[6], ne = 0;
     for (int b = 1; b < 12; ++b) {
         bool lane = false;
         for (int j = 0; j < 5; ++j) lane |= best_lane[j] == b;
-        if (lane) continue;
-        if (nw < 2)
-            warp_bits[nw++] = b;
-        else
-            loop_bits[nl++] = b;
+        if (!lane) ebits[ne++] = b;
     }
-    for (unsigned tid = 0; tid < 128; ++tid) {
-        const unsigned e0 = deposit(tid & 31, best_lane, 5) | deposit(tid >> 5, warp_bits, 2);
-        T.a0[tid] = addr_of(e0);
-        T.r0[tid] = (uint8_t)row_of(e0);
-        T.c0[tid] = (uint8_t)col_of(e0);
+    for (unsigned t = 0; t < 256; ++t) {
+        const unsigned e0 = deposit(t & 31, best_lane, 5) | deposit(t >> 5, ebits, 3);
+        T.a0[t] = addr_of(e0);
+        T.e0[t] = (uint16_t)e0;
+        T.r0[t] = (uint8_t)row_of(e0);
+        T.c0[t] = (uint8_t)col_of(e0);
     }
     for (unsigned i = 0; i < 16; ++i) {
-        const unsigned ei = deposit(i, loop_bits, 4);
+        const unsigned ei = deposit(i, ebits + 2, 4);
         T.ai[i] = addr_of(ei);
+        T.ei[i] = (uint16_t)ei;
         T.ri[i] = (uint8_t)row_of(ei);
         T.ci[i] = (uint8_t)col_of(ei);
     }
@@ -604,10 +970,16 @@ void build_record(int n, const int *S, const cd *U, int nsplit, std::vector<unsi
             if ((r >> j) & 1) a |= 1ull << S[j];
         T.rdep[r] = a;
     }
-    std::memcpy(&rec[(size_t)nsplit * kBBytes], &T, sizeof(T));
 }
 
-size_t smem_bytes(int nsplit) { return 1024 + 2 * kABytes + (size_t)nsplit * kBBytes + kTablesBytes + 128; }
+size_t smem_bytes_ws(int nsplit) {
+    return 1024 + (size_t)kStages * kStageBytes + 4 * kABytes + (size_t)nsplit * kBBytes + kTablesBytes + kRunBytes +
+           384;
+}
+
+size_t smem_bytes(int nsplit) {
+    return 1024 + 4 * kABytes + (size_t)nsplit * kBBytes + kTablesBytes + kRunBytes + 128;
+}
 
 }  // namespace
 
@@ -636,11 +1008,12 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     const size_t smem = smem_bytes(nsplit);
     if (dev < 0 || dev >= 64) return QSIM_ENOTSUP;
     if (!attr_set[dev]) {
+        // no carveout preference: the driver keeps the rest of the unified
+        // L1/shared array as L1, which stages the returns of the 16-byte
+        // loads in flight (forcing the maximum shared carveout, 28 KB of L1,
+        // cut the kernel's bandwidth by a fifth)
         cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_bytes(3));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return cuda_err(s, e, "tc kernel attribute");
         attr_set[dev] = true;
     }
@@ -658,7 +1031,9 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
         const int by_smem = smem_sm / (int)(smem + 1024);
         int occ = by_regs < by_smem ? by_regs : by_smem;
         if (occ > (int)(512 / kTmemCols)) occ = (int)(512 / kTmemCols);
-        if (occ > 4) occ = 4;
+        int cap = 2;  // the loop is tuned for two CTAs per SM
+        if (const char *v = getenv("QSIM_TC_CTAS")) cap = atoi(v) > 0 ? atoi(v) : cap;
+        if (occ > cap) occ = cap;
         if (occ < 1) occ = 1;
         int api = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, k_block_tc, kTcThreads, smem);
@@ -668,20 +1043,33 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
                     "occupancy API %d)\n", fa.numRegs, smem, occ, by_regs, by_smem, api);
         per_sm[dev][nsplit] = occ;
     }
+    const bool ws = s->tc_variant == 1;
+    if (ws) {
+        static bool ws_attr[64] = {false};
+        if (!ws_attr[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(k_block_tc_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem_bytes_ws(3));
+            if (e != cudaSuccess) return cuda_err(s, e, "tc ws kernel attribute");
+            ws_attr[dev] = true;
+        }
+    }
     a.psi = (float2 *)s->state;
     a.rec = dev_rec;
     a.rec_bytes = (uint32_t)rec.size();
     a.nsplit = nsplit;
     a.ntiles = 1ull << (s->n - 12);
     a.err = (unsigned int *)((char *)s->ws + kWsErr);
-    const uint64_t cap = (uint64_t)kSMs * per_sm[dev][nsplit];
+    const uint64_t cap = ws ? (uint64_t)kSMs : (uint64_t)kSMs * per_sm[dev][nsplit];
     const uint64_t grid = a.ntiles < cap ? a.ntiles : cap;
     double *slots = (double *)((char *)s->ws + kWsNorm);
     const int slot = (int)(s->tc_passes & 1);
     a.norm_out = slots + slot * 2 * kMaxTcGrid;
     a.norm_prev = (s->norm_tracking && s->tc_passes > 0) ? slots + (slot ^ 1) * 2 * kMaxTcGrid : nullptr;
     a.prev_grid = s->tc_prev_grid;
-    k_block_tc<<<(unsigned)grid, kTcThreads, smem, s->stream>>>(a);
+    if (ws)
+        k_block_tc_ws<<<(unsigned)grid, kWsThreads, smem_bytes_ws(nsplit), s->stream>>>(a);
+    else
+        k_block_tc<<<(unsigned)grid, kTcThreads, smem, s->stream>>>(a);
     s->stats.launches++;
     s->tc_passes++;
     s->tc_prev_grid = (int)grid;

@@ -28,11 +28,15 @@ struct GateRec {
     uint64_t tmask = 0, cmask = 0;
     std::vector<cd> m;  // 4^t entries, row-major, index bit j = targets[j]
     int kind = GK_DENSE;
+    bool diag = false;  // the matrix is diagonal (the gate only multiplies amplitudes by phases)
 };
 
 // One unit of device work produced by the planner.
 struct PlanItem {
     bool fused = false;     // false: execute gates[gate] with the plain kernels
+    bool diag_block = false;  // fused block of diagonal gates: one multiply per amplitude
+    uint64_t dmask = 0;       // qubits of a diagonal block (up to kMaxDiagQubits)
+    std::vector<cd> dtab;     // its 2^popc(dmask) factors, index bit j = j-th qubit of dmask
     int gate = -1;
     int k = 0;              // fused block width
     int qubits[5] = {0, 0, 0, 0, 0};  // sorted ascending; bit j of the block index
@@ -72,6 +76,7 @@ struct qsim {
     int tc_terms = 3;
     bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
     bool c128_df = false;       // complex128 one-qubit gates in double-float arithmetic
+    int tc_variant = 0;         // 0: k_block_tc (2 CTAs/SM), 1: k_block_tc_ws (warp-specialised, TMA-fed)
     uint64_t tc_passes = 0;
     int tc_prev_grid = 0;
     unsigned char *stage_host = nullptr;  // pinned staging for block operands
@@ -92,7 +97,8 @@ struct qsim {
     ClassTime class_time[8];
 };
 
-enum KernelClass { KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_COUNT };
+enum KernelClass { KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_BLOCK_DIAG, KC_COUNT };
+constexpr int kMaxDiagQubits = 12;
 
 // Bytes of one amplitude.
 inline size_t amp_bytes(const qsim *s) { return s->prec == QSIM_C128 ? 16 : 8; }
@@ -121,6 +127,8 @@ int cuda_err(qsim *s, cudaError_t e, const char *where);
 // Launchers (gate_kernels.cu) -----------------------------------------------
 int launch_gate_plain(qsim *s, const GateRec &g);
 int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m);
+// Diagonal block: psi_i *= d[bits of i on dmask] (diag_kernels.cu).
+int launch_block_diag(qsim *s, uint64_t dmask, const cd *d);
 int launch_set_basis(qsim *s, uint64_t basis);
 
 // Copy a block operand record into the device ring (via pinned staging) on
@@ -143,7 +151,9 @@ int run_measure_all(qsim *s, double u, uint64_t *outcome);
 
 // Planner (planner.cpp) -------------------------------------------------------
 void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out);
-void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out);
+// diag_k: widest diagonal block (0 disables diagonal blocks)
+void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out,
+                 int diag_k = kMaxDiagQubits);
 // Features of one plan item (kFeatures floats).
 void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, float *f);
 // Learned planner: greedy blocks for several kmax, each block fused or left

@@ -81,7 +81,36 @@ inline uint64_t qmask(const GateRec &g) { return g.tmask | g.cmask; }
 
 }  // namespace
 
-void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out) {
+// Fraction of the amplitudes a plain launch of g reads and writes.
+double touched_fraction(const GateRec &g) {
+    int fixed = (int)g.controls.size() + (g.kind == GK_PHASE ? 1 : 0);
+    return std::ldexp(1.0, -fixed);
+}
+
+// Table of a diagonal block over qubit set dmask: d[r] = product over the
+// member gates of their diagonal entry for the assignment r of dmask (bit j
+// of r = j-th lowest qubit of dmask); gates whose controls are not all 1
+// in r contribute 1.
+std::vector<cd> diag_table(const std::vector<GateRec> &q, const std::vector<int> &members, uint64_t dmask) {
+    int pos[64], k = 0;
+    for (int b = 0; b < 64; ++b) pos[b] = ((dmask >> b) & 1ull) ? k++ : -1;
+    std::vector<cd> d((size_t)1 << k, cd(1.0, 0.0));
+    for (int gi : members) {
+        const GateRec &g = q[gi];
+        const int T = 1 << g.t;
+        for (size_t r = 0; r < d.size(); ++r) {
+            bool on = true;
+            for (int c : g.controls) on = on && ((r >> pos[c]) & 1u);
+            if (!on) continue;
+            int ti = 0;
+            for (int j = 0; j < g.t; ++j) ti |= (int)((r >> pos[g.targets[j]]) & 1u) << j;
+            d[r] *= g.m[(size_t)ti * T + ti];
+        }
+    }
+    return d;
+}
+
+void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out, int diag_k) {
     out.clear();
     const size_t G = q.size();
     if (G == 0) return;
@@ -110,10 +139,61 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
             if ((m >> b) & 1ull) ++front[b];
     };
     auto popc = [](uint64_t x) { return __builtin_popcountll(x); };
+    auto untake = [&](int gi) {
+        done[gi] = 0;
+        ++remaining;
+        const uint64_t m = qmask(q[gi]);
+        for (int b = 0; b < n; ++b)
+            if ((m >> b) & 1ull) --front[b];
+    };
 
     while (remaining) {
         while (next_seed < G && done[next_seed]) ++next_seed;
         const int seed = (int)next_seed;  // earliest undone gate is always ready
+        if (diag_k > 0 && q[seed].diag && popc(qmask(q[seed])) <= diag_k) {
+            // a diagonal block: ready diagonal gates commute with each other,
+            // so absorb them (fewest new qubits first) up to diag_k qubits
+            std::vector<int> dm;
+            uint64_t Sd = qmask(q[seed]);
+            double frac = touched_fraction(q[seed]);
+            take(seed);
+            dm.push_back(seed);
+            for (;;) {
+                int best = -1, best_add = 1 << 30;
+                for (int b = 0; b < n; ++b) {
+                    if (front[b] >= wire[b].size()) continue;
+                    const int gi = wire[b][front[b]];
+                    if (!q[gi].diag) continue;
+                    const uint64_t m = qmask(q[gi]);
+                    const int add = popc(m & ~Sd);
+                    if (popc(Sd | m) > diag_k || !is_ready(gi)) continue;
+                    if (add < best_add || (add == best_add && gi < best)) {
+                        best = gi;
+                        best_add = add;
+                    }
+                }
+                if (best < 0) break;
+                take(best);
+                dm.push_back(best);
+                Sd |= qmask(q[best]);
+                frac += touched_fraction(q[best]);
+            }
+            // worth one full pass only if the separate launches would touch more
+            if (dm.size() >= 2 && frac >= 1.0) {
+                PlanItem it;
+                it.fused = true;
+                it.diag_block = true;
+                it.dmask = Sd;
+                it.k = popc(Sd);
+                it.ngates = (int)dm.size();
+                it.members = dm;
+                for (int gi : dm) it.amp_updates += (double)(1ull << (n - (int)q[gi].controls.size()));
+                it.dtab = diag_table(q, dm, Sd);
+                out.push_back(std::move(it));
+                continue;
+            }
+            for (auto r = dm.rbegin(); r != dm.rend(); ++r) untake(*r);
+        }
         if (popc(qmask(q[seed])) > kmax) {
             PlanItem it;
             it.fused = false;
@@ -202,7 +282,13 @@ void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int
     f[1] = (prec == QSIM_C128 ? 16.f : 8.f) / 16.f;
     f[15] = 1.f;
     uint64_t mask = 0;
-    if (it.fused) {
+    if (it.fused && it.diag_block) {
+        f[2] = 1.f;
+        f[4] = it.k / 5.f;
+        f[5] = it.ngates / 32.f;
+        f[8] = 1.f;
+        mask = it.dmask;
+    } else if (it.fused) {
         f[2] = 1.f;
         f[3] = (prec == QSIM_C64 && it.k >= 4 && n >= 12 && tc_enabled) ? 1.f : 0.f;
         f[4] = it.k / 5.f;

@@ -323,3 +323,19 @@ def test_expect_closed_forms(oracle_mod):
     assert abs(ghz.expect([(1.0, full, 0)]) - 1.0) < 1e-14
     # Y on qubits 0 and 1, X elsewhere: i*i = -1 on |1...1> <-> |0...0>
     assert abs(ghz.expect([(1.0, full, 0b11)]) + 1.0) < 1e-14
+
+
+def test_semiclassical_phase_estimation_oracle(oracle_mod):
+    """Appendix A.3's measure-and-reset loop (semi-classical inverse QFT) on
+    the oracle: the phase k / 2^m of R(2 pi k / 2^m) on |1> comes out bit
+    for bit, least significant first."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location(
+        "semiclassical", os.path.join(os.path.dirname(__file__), "test_gpu_semiclassical.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    for m, k in [(3, 5), (5, 19), (7, 100)]:
+        s = _sim(oracle_mod, 3)
+        bits = mod.phase_estimation(s, m, k, cg.uniform_draws(k, m))
+        assert bits == [(k >> j) & 1 for j in range(m)]
