@@ -250,7 +250,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->tc_enabled = o.no_tensor_cores == 0;
     s->norm_tracking = o.no_norm_tracking == 0;
     s->c128_df = o.c128_double_float != 0;
-    if (const char *v = getenv("QSIM_TC_KERNEL")) s->tc_variant = (v[0] == 'w') ? 1 : 0;
+    if (const char *v = getenv("QSIM_TC_KERNEL")) s->tc_variant = (v[0] == 'w') ? 1 : (v[0] == 's') ? 2 : 0;
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {

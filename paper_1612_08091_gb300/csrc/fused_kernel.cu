@@ -62,7 +62,7 @@ constexpr int kTcThreads = 128;
 constexpr int kTile = 4096;              // amplitudes per tile (2^12)
 constexpr int kABytes = 128 * 128;       // one bf16 split of X: 128 rows x 128 B
 constexpr int kBBytes = 64 * 128;        // one bf16 split of R: 64 rows x 128 B
-constexpr int kTablesBytes = 4560;
+constexpr int kTablesBytes = 4688;
 constexpr uint32_t kTmemCols = 128;      // two 64-column fp32 accumulators
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMaxTcGrid = 4 * kSMs;
@@ -89,6 +89,13 @@ struct RecTables {
     uint8_t rh, ch;            // row / column bit of h (address bit 0)
     uint8_t pair_r;            // 1 if rows r, r+1 are adjacent in memory (qubit 0 in S)
     uint8_t pad[13];
+    // byte offset of (column c, row r) in the swizzled A operand is
+    //   c*128 + ((r>>2 ^ c) & 7)*16 + (r&3)*4;
+    // with c = c_t | c_i and r = r_t | r_i (disjoint bits) it splits into
+    //   lin_t + lin_i + (swz_t ^ swz_i),  lin = c*128 + (r&3)*4,
+    //   swz = ((r>>2 ^ c) & 7) << 4
+    uint32_t lin_i[16];        // of ei(i)
+    uint32_t swz_i[16];
 };
 static_assert(sizeof(RecTables) == kTablesBytes, "table layout");
 
@@ -256,11 +263,49 @@ __device__ __forceinline__ void put_amp2(unsigned char *a_hi, unsigned char *a_l
     *(uint2 *)(a_lo + off) = lw;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
+// Split (re, im) into bf16 hi = round-to-nearest and lo = round-to-nearest
+// bf16 of the exact remainder x - hi (hi + lo carries x to 2^-16 relative).
+// A truncated hi costs the same instructions but biases the dropped lo x lo
+// product and doubles the norm drift, so hi is rounded.
+__device__ __forceinline__ void split_pair(float re, float im, uint32_t &hw, uint32_t &lw) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    memcpy(&hw, &h, 4);
+    const float rr = re - __uint_as_float(hw << 16);
+    const float ri = im - __uint_as_float(hw & 0xFFFF0000u);
+    lw = pack_bf16x2(rr, ri);
+}
+
+// one amplitude at precomputed operand offset `off`
+__device__ __forceinline__ void put_amp_off(unsigned char *a_hi, unsigned char *a_lo, uint32_t off, float re,
+                                            float im) {
+    uint32_t hw, lw;
+    split_pair(re, im, hw, lw);
+    *(uint32_t *)(a_hi + off) = hw;
+    *(uint32_t *)(a_lo + off) = lw;
+}
+
+// rows r (even) and r+1 of one column at precomputed offset `off`
+__device__ __forceinline__ void put_amp2_off(unsigned char *a_hi, unsigned char *a_lo, uint32_t off, float4 v) {
+    uint2 hw, lw;
+    split_pair(v.x, v.y, hw.x, lw.x);
+    split_pair(v.z, v.w, hw.y, lw.y);
+    *(uint2 *)(a_hi + off) = hw;
+    *(uint2 *)(a_lo + off) = lw;
+}
+
+__device__ __forceinline__ uint32_t lin_of(int c, int r) { return (uint32_t)(c * 128 + (r & 3) * 4); }
+__device__ __forceinline__ uint32_t swz_of(int c, int r) { return (uint32_t)((((r >> 2) ^ c) & 7) << 4); }
+
+// ABUF = 2: two A operands (the convert of tile t+1 overlaps the MMA of t),
+// two CTAs per SM.  ABUF = 1: one A operand (the convert of tile t+1 waits
+// for the MMA of t), ~54 KB of shared memory, three CTAs per SM and more L1
+// left for the loads in flight.
+template <int ABUF>
+__global__ void __launch_bounds__(kTcThreads, (ABUF == 2 ? 2 : 3)) k_block_tc(const TcArgs args) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *A = smem;                           // [2 buf][2 split][kABytes]
-    unsigned char *B = smem + 4 * kABytes;             // [nsplit][kBBytes] then tables
+    unsigned char *A = smem;                           // [ABUF][2 split][kABytes]
+    unsigned char *B = smem + 2 * ABUF * kABytes;      // [nsplit][kBBytes] then tables
     const RecTables *tab = (const RecTables *)(B + args.nsplit * kBBytes);
     // barriers after the copied record (tables and run table)
     uint64_t *bars = (uint64_t *)(B + args.nsplit * kBBytes + kTablesBytes + kRunBytes);  // [0]=operand, [1],[2]=mma
@@ -327,6 +372,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
         const uint64_t toff0 = tab->a0[tid];
         const int r00 = tab->r0[tid], c00 = tab->c0[tid];
         const int r01 = r00 | tab->rh, c01 = c00 | tab->ch;
+        const uint32_t lin0 = lin_of(c00, r00), swz0 = swz_of(c00, r00);
+        const uint32_t lin1 = lin_of(c01, r01), swz1 = swz_of(c01, r01);
         const bool pair_r = tab->pair_r != 0;
         const uint64_t my_cdep = tab->cdep[tid];
         const int nterms = args.nsplit == 3 ? 5 : 3;
@@ -382,19 +429,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_block_tc(const TcArgs args) {
         int it = 0;
         for (; t < args.ntiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
-            unsigned char *a_hi = A + (2 * buf) * kABytes;
-            unsigned char *a_lo = A + (2 * buf + 1) * kABytes;
+            const int abuf = ABUF == 2 ? buf : 0;
+            unsigned char *a_hi = A + (2 * abuf) * kABytes;
+            unsigned char *a_lo = A + (2 * abuf + 1) * kABytes;
+            if (ABUF == 1 && it >= 1) {
+                // the single A operand is free once the MMA of tile it-1 is done
+                const int pb = (it - 1) & 1;
+                if (!mbar_wait(&bars[1 + pb], (uint32_t)(((it - 1) >> 1) & 1))) {
+                    atomicOr(args.err, 2u);
+                    *abort_flag = 1;
+                }
+            }
             float xsq = 0.f;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 xsq = fmaf(regs[i].x, regs[i].x, fmaf(regs[i].y, regs[i].y, xsq));
                 xsq = fmaf(regs[i].z, regs[i].z, fmaf(regs[i].w, regs[i].w, xsq));
-                const int ri = tab->ri[i], ci = tab->ci[i];
+                const uint32_t li = tab->lin_i[i], si = tab->swz_i[i];
                 if (pair_r) {
-                    put_amp2(a_hi, a_lo, c00 | ci, r00 | ri, regs[i]);
+                    put_amp2_off(a_hi, a_lo, lin0 + li + (swz0 ^ si), regs[i]);
                 } else {
-                    put_amp(a_hi, a_lo, c00 | ci, r00 | ri, regs[i].x, regs[i].y);
-                    put_amp(a_hi, a_lo, c01 | ci, r01 | ri, regs[i].z, regs[i].w);
+                    put_amp_off(a_hi, a_lo, lin0 + li + (swz0 ^ si), regs[i].x, regs[i].y);
+                    put_amp_off(a_hi, a_lo, lin1 + li + (swz1 ^ si), regs[i].z, regs[i].w);
                 }
             }
             nrm_in += (double)xsq;
@@ -617,6 +673,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_block_tc_ws(const TcArgs args
         const uint64_t my_cdep = tab->cdep[col];
         const int r00 = tab->r0[ct], c00 = tab->c0[ct];
         const int r01 = r00 | tab->rh, c01 = c00 | tab->ch;
+        const uint32_t lin0 = lin_of(c00, r00), swz0 = swz_of(c00, r00);
+        const uint32_t lin1 = lin_of(c01, r01), swz1 = swz_of(c01, r01);
         const bool pair_r = tab->pair_r != 0;
         const float scale = *s_scale;
         // element e = e0(ct) | ei(i) | h of the staged tile sits at byte 8e
@@ -673,12 +731,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_block_tc_ws(const TcArgs args
                 const float4 x = sb[(e0 | tab->ei[i2]) >> 1];
                 xsq = fmaf(x.x, x.x, fmaf(x.y, x.y, xsq));
                 xsq = fmaf(x.z, x.z, fmaf(x.w, x.w, xsq));
-                const int ri = tab->ri[i2], ci = tab->ci[i2];
+                const uint32_t li = tab->lin_i[i2], si = tab->swz_i[i2];
                 if (pair_r) {
-                    put_amp2(a_hi, a_lo, c00 | ci, r00 | ri, x);
+                    put_amp2_off(a_hi, a_lo, lin0 + li + (swz0 ^ si), x);
                 } else {
-                    put_amp(a_hi, a_lo, c00 | ci, r00 | ri, x.x, x.y);
-                    put_amp(a_hi, a_lo, c01 | ci, r01 | ri, x.z, x.w);
+                    put_amp_off(a_hi, a_lo, lin0 + li + (swz0 ^ si), x.x, x.y);
+                    put_amp_off(a_hi, a_lo, lin1 + li + (swz1 ^ si), x.z, x.w);
                 }
             }
             nrm_in += (double)xsq;
@@ -954,6 +1012,8 @@ void build_tables(int n, const int *S, RecTables &T, InsertSpec &vspec) {
         T.ei[i] = (uint16_t)ei;
         T.ri[i] = (uint8_t)row_of(ei);
         T.ci[i] = (uint8_t)col_of(ei);
+        T.lin_i[i] = (uint32_t)(T.ci[i] * 128 + (T.ri[i] & 3) * 4);
+        T.swz_i[i] = (uint32_t)((((T.ri[i] >> 2) ^ T.ci[i]) & 7) << 4);
     }
     T.rh = (uint8_t)row_of(1u);
     T.ch = (uint8_t)col_of(1u);
@@ -977,8 +1037,8 @@ size_t smem_bytes_ws(int nsplit) {
            384;
 }
 
-size_t smem_bytes(int nsplit) {
-    return 1024 + 4 * kABytes + (size_t)nsplit * kBBytes + kTablesBytes + kRunBytes + 128;
+size_t smem_bytes(int nsplit, int abuf = 2) {
+    return 1024 + 2 * (size_t)abuf * kABytes + (size_t)nsplit * kBBytes + kTablesBytes + kRunBytes + 128;
 }
 
 }  // namespace
@@ -1002,27 +1062,30 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     unsigned char *dev_rec = nullptr;
     int rc = stage_operand(s, rec.data(), rec.size(), &dev_rec);
     if (rc) return rc;
-    static bool attr_set[64] = {false};
-    static int per_sm[64][4] = {{0}};
+    const int abuf = s->tc_variant == 2 ? 1 : 2;
+    auto kernel = abuf == 2 ? k_block_tc<2> : k_block_tc<1>;
+    static bool attr_set[2][64] = {{false}};
+    static int per_sm[2][64][4] = {{{0}}};
     const int dev = s->device;
-    const size_t smem = smem_bytes(nsplit);
+    const size_t smem = smem_bytes(nsplit, abuf);
     if (dev < 0 || dev >= 64) return QSIM_ENOTSUP;
-    if (!attr_set[dev]) {
+    const int ai = abuf - 1;
+    if (!attr_set[ai][dev]) {
         // no carveout preference: the driver keeps the rest of the unified
         // L1/shared array as L1, which stages the returns of the 16-byte
         // loads in flight (forcing the maximum shared carveout, 28 KB of L1,
         // cut the kernel's bandwidth by a fifth)
-        cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes(3));
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes(3, abuf));
         if (e != cudaSuccess) return cuda_err(s, e, "tc kernel attribute");
-        attr_set[dev] = true;
+        attr_set[ai][dev] = true;
     }
-    if (!per_sm[dev][nsplit]) {
+    if (!per_sm[ai][dev][nsplit]) {
         // resident CTAs per SM from the kernel's footprint: registers, shared
         // memory (+1 KB reserved per CTA) and tensor-memory columns; CTAs
         // never wait on one another, so an overestimate only queues CTAs
         cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, k_block_tc);
+        cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
         int regs_sm = 65536, smem_sm = 233472;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -1031,17 +1094,14 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
         const int by_smem = smem_sm / (int)(smem + 1024);
         int occ = by_regs < by_smem ? by_regs : by_smem;
         if (occ > (int)(512 / kTmemCols)) occ = (int)(512 / kTmemCols);
-        int cap = 2;  // the loop is tuned for two CTAs per SM
+        int cap = abuf == 2 ? 2 : 3;  // the loop is tuned for these
         if (const char *v = getenv("QSIM_TC_CTAS")) cap = atoi(v) > 0 ? atoi(v) : cap;
         if (occ > cap) occ = cap;
         if (occ < 1) occ = 1;
-        int api = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, k_block_tc, kTcThreads, smem);
-        cudaGetLastError();
         if (getenv("QSIM_DEBUG"))
-            fprintf(stderr, "qsim: k_block_tc regs %d smem %zu: %d CTAs/SM (registers %d, shared memory %d, "
-                    "occupancy API %d)\n", fa.numRegs, smem, occ, by_regs, by_smem, api);
-        per_sm[dev][nsplit] = occ;
+            fprintf(stderr, "qsim: k_block_tc<%d> regs %d smem %zu: %d CTAs/SM (registers %d, shared memory %d)\n",
+                    abuf, fa.numRegs, smem, occ, by_regs, by_smem);
+        per_sm[ai][dev][nsplit] = occ;
     }
     const bool ws = s->tc_variant == 1;
     if (ws) {
@@ -1059,7 +1119,7 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     a.nsplit = nsplit;
     a.ntiles = 1ull << (s->n - 12);
     a.err = (unsigned int *)((char *)s->ws + kWsErr);
-    const uint64_t cap = ws ? (uint64_t)kSMs : (uint64_t)kSMs * per_sm[dev][nsplit];
+    const uint64_t cap = ws ? (uint64_t)kSMs : (uint64_t)kSMs * per_sm[ai][dev][nsplit];
     const uint64_t grid = a.ntiles < cap ? a.ntiles : cap;
     double *slots = (double *)((char *)s->ws + kWsNorm);
     const int slot = (int)(s->tc_passes & 1);
@@ -1069,7 +1129,7 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     if (ws)
         k_block_tc_ws<<<(unsigned)grid, kWsThreads, smem_bytes_ws(nsplit), s->stream>>>(a);
     else
-        k_block_tc<<<(unsigned)grid, kTcThreads, smem, s->stream>>>(a);
+        kernel<<<(unsigned)grid, kTcThreads, smem, s->stream>>>(a);
     s->stats.launches++;
     s->tc_passes++;
     s->tc_prev_grid = (int)grid;

@@ -76,7 +76,7 @@ struct qsim {
     int tc_terms = 3;
     bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
     bool c128_df = false;       // complex128 one-qubit gates in double-float arithmetic
-    int tc_variant = 0;         // 0: k_block_tc (2 CTAs/SM), 1: k_block_tc_ws (warp-specialised, TMA-fed)
+    int tc_variant = 0;         // 0: k_block_tc<2>, 1: k_block_tc_ws (warp-specialised, TMA-fed), 2: k_block_tc<1>
     uint64_t tc_passes = 0;
     int tc_prev_grid = 0;
     unsigned char *stage_host = nullptr;  // pinned staging for block operands
