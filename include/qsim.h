@@ -133,6 +133,15 @@ int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const in
 /* Execute every queued gate (Sec. 4.1.3: eng.flush()). */
 int sim_flush(qsim *s);
 
+/* Emulation of a classical reversible function on a register (Sec. 4.3.3,
+ * BasicMathGate: e.g. AddConstant(c), x -> x + c mod 2^m; the modular
+ * multiplication of Appendix A.3).  The register is qubits[0..m-1] (bit j of
+ * its value is qubits[j]), 1 <= m <= 12; perm[x] = f(x) for x < 2^m must be
+ * a bijection (QSIM_EINVAL otherwise).  Where all controls are |1>, the
+ * amplitude of register value x moves to register value f(x).  Flushes the
+ * queue, then runs at once (one pass over the touched groups). */
+int sim_apply_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, const int *controls, int c);
+
 /* P(qubit = 1) = sum of |psi_i|^2 over indices with bit q set, accumulated
  * in FP64 (Sec. 4, measurement in the computational basis). */
 int sim_prob(qsim *s, int qubit, double *p1);

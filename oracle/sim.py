@@ -82,6 +82,29 @@ class OracleSim:
     def apply_op(self, op):
         self.apply(G.matrix(op.kind, op.params), op.targets, op.controls)
 
+    def apply_permutation(self, perm, qubits, controls=()):
+        """Emulated classical bijection on a register (bit j of the register
+        value is qubits[j]), from its definition: where all controls are 1,
+        the amplitude of register value x moves to register value perm[x]."""
+        perm = np.asarray(perm, dtype=np.int64)
+        N = 1 << self.n
+        idx = np.arange(N, dtype=np.int64)
+        val = np.zeros(N, dtype=np.int64)
+        regmask = 0
+        for j, q in enumerate(qubits):
+            val |= ((idx >> q) & 1) << j
+            regmask |= 1 << q
+        on = np.ones(N, dtype=bool)
+        for c in controls:
+            on &= ((idx >> c) & 1) == 1
+        fv = perm[val]
+        dest = idx & ~regmask
+        for j, q in enumerate(qubits):
+            dest |= ((fv >> j) & 1) << q
+        out = self.psi.copy()
+        out[dest[on]] = self.psi[on]
+        self.psi = out
+
     # -- reads -------------------------------------------------------------
     def norm2(self):
         return float(self.lib.or_norm2(self._p(), self.n))

@@ -250,7 +250,8 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->tc_enabled = o.no_tensor_cores == 0;
     s->norm_tracking = o.no_norm_tracking == 0;
     s->c128_df = o.c128_double_float != 0;
-    if (const char *v = getenv("QSIM_TC_KERNEL")) s->tc_variant = (v[0] == 'w') ? 1 : (v[0] == 's') ? 2 : 0;
+    if (const char *v = getenv("QSIM_TC_KERNEL")) s->tc_variant = (v[0] == 'w') ? 1 : (v[0] == 'd') ? 0 : 2;
+    if (const char *v = getenv("QSIM_TC_STREAMING")) s->tc_streaming = atoi(v);
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
@@ -357,6 +358,29 @@ int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const in
 int sim_flush(qsim *s) {
     if (!s) return QSIM_EINVAL;
     return flush(s);
+}
+
+int sim_apply_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, const int *controls, int c) {
+    if (!s) return QSIM_EINVAL;
+    if (!perm || !qubits || m < 1 || m > 12 || c < 0 || (c > 0 && !controls))
+        return set_err(s, QSIM_EINVAL, "bad permutation arguments");
+    if (m + c > s->n) return set_err(s, QSIM_ERANGE, "more qubits than the register has");
+    uint64_t qmask, cmask;
+    int rc = validate_qubits(s, qubits, m, controls, c, &qmask, &cmask);
+    if (rc) return rc;
+    const uint64_t D = 1ull << m;
+    std::vector<char> seen(D, 0);
+    for (uint64_t v = 0; v < D; ++v) {
+        if (perm[v] >= D || seen[perm[v]]) return set_err(s, QSIM_EINVAL, "permutation is not a bijection");
+        seen[perm[v]] = 1;
+    }
+    if ((rc = flush(s))) return rc;
+    rc = launch_permutation(s, perm, qubits, m, qmask, cmask);
+    if (rc) return rc;
+    s->stats.passes++;
+    s->stats.amp_updates += std::ldexp(1.0, s->n - c);
+    s->stats.alg_bytes += 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n - c);
+    return QSIM_OK;
 }
 
 int sim_prob(qsim *s, int qubit, double *p1) {

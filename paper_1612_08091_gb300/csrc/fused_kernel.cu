@@ -126,6 +126,7 @@ struct TcArgs {
     double *norm_out;
     const double *norm_prev;
     int prev_grid;
+    int streaming;             // 1: evict-first hints on the state's loads and stores
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -383,8 +384,13 @@ __global__ void __launch_bounds__(kTcThreads, (ABUF == 2 ? 2 : 3)) k_block_tc(co
         auto load_tile = [&](uint64_t tt) {
             const uint64_t base = insert_zeros(tt, args.vspec);
             const float2 *p = psi_in + base + toff0;
+            if (args.streaming) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) regs[i] = *(const float4 *)(p + tab->ai[i]);
+                for (int i = 0; i < 16; ++i) regs[i] = __ldcs((const float4 *)(p + tab->ai[i]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) regs[i] = *(const float4 *)(p + tab->ai[i]);
+            }
         };
         auto epilogue = [&](uint64_t tt, int j) {
             const int buf = j & 1;
@@ -407,14 +413,22 @@ __global__ void __launch_bounds__(kTcThreads, (ABUF == 2 ? 2 : 3)) k_block_tc(co
 #pragma unroll
                     for (int q = 0; q < 16; q += 2) {
                         const int r = chunk * 16 + q;
-                        *(float4 *)(psi + base + tab->rdep[r]) = make_float4(
-                            v[2 * q] * scale, v[2 * q + 1] * scale, v[2 * q + 2] * scale, v[2 * q + 3] * scale);
+                        const float4 o = make_float4(v[2 * q] * scale, v[2 * q + 1] * scale, v[2 * q + 2] * scale,
+                                                     v[2 * q + 3] * scale);
+                        if (args.streaming)
+                            __stcs((float4 *)(psi + base + tab->rdep[r]), o);
+                        else
+                            *(float4 *)(psi + base + tab->rdep[r]) = o;
                     }
                 } else {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int r = chunk * 16 + q;
-                        psi[base + tab->rdep[r]] = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
+                        const float2 o = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
+                        if (args.streaming)
+                            __stcs(psi + base + tab->rdep[r], o);
+                        else
+                            psi[base + tab->rdep[r]] = o;
                     }
                 }
             }
@@ -1126,6 +1140,7 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     a.norm_out = slots + slot * 2 * kMaxTcGrid;
     a.norm_prev = (s->norm_tracking && s->tc_passes > 0) ? slots + (slot ^ 1) * 2 * kMaxTcGrid : nullptr;
     a.prev_grid = s->tc_prev_grid;
+    a.streaming = s->tc_streaming;
     if (ws)
         k_block_tc_ws<<<(unsigned)grid, kWsThreads, smem_bytes_ws(nsplit), s->stream>>>(a);
     else

@@ -76,7 +76,8 @@ struct qsim {
     int tc_terms = 3;
     bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
     bool c128_df = false;       // complex128 one-qubit gates in double-float arithmetic
-    int tc_variant = 0;         // 0: k_block_tc<2>, 1: k_block_tc_ws (warp-specialised, TMA-fed), 2: k_block_tc<1>
+    int tc_variant = 2;         // 0: k_block_tc<2>, 1: k_block_tc_ws (warp-specialised, TMA-fed), 2: k_block_tc<1>
+    int tc_streaming = 0;       // streaming (evict-first) cache hints on the block kernel's loads and stores
     uint64_t tc_passes = 0;
     int tc_prev_grid = 0;
     unsigned char *stage_host = nullptr;  // pinned staging for block operands
@@ -127,6 +128,9 @@ int cuda_err(qsim *s, cudaError_t e, const char *where);
 // Launchers (gate_kernels.cu) -----------------------------------------------
 int launch_gate_plain(qsim *s, const GateRec &g);
 int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m);
+// Emulated classical bijection on a register (perm_kernels.cu).
+int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask);
+
 // Diagonal block: psi_i *= d[bits of i on dmask] (diag_kernels.cu).
 int launch_block_diag(qsim *s, uint64_t dmask, const cd *d);
 int launch_set_basis(qsim *s, uint64_t basis);

@@ -88,6 +88,7 @@ def load():
         "sim_get_stats": [P, ctypes.POINTER(Stats)],
         "sim_reset_stats": [P],
         "sim_set_profiling": [P, I],
+        "sim_apply_permutation": [P, ctypes.POINTER(U64), IP, I, IP, I],
         "sim_batch_workspace_bytes": [I, IP, IP, ctypes.POINTER(ctypes.c_size_t)],
         "sim_batch_create": [I, IP, IP, D, P, P, ctypes.c_size_t, ctypes.POINTER(P)],
         "sim_batch_run": [P, DP, DP],
@@ -201,6 +202,16 @@ class Simulator:
 
     def flush(self):
         self._check(self.lib.sim_flush(self.h), "sim_flush")
+
+    def apply_permutation(self, perm, qubits, controls=()):
+        """Emulate a classical bijection on the register `qubits` (bit j of
+        the register value is qubits[j]): x -> perm[x] where all controls
+        are |1> (sim_apply_permutation)."""
+        p = np.ascontiguousarray(perm, dtype=np.uint64)
+        q, m = _ints(qubits)
+        c, nc = _ints(controls)
+        self._check(self.lib.sim_apply_permutation(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), q, m,
+                                                   c if nc else None, nc), "sim_apply_permutation")
 
     def prob(self, qubit):
         out = ctypes.c_double()

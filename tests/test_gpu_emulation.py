@@ -1,0 +1,90 @@
+"""Emulated classical functions on registers (the paper's BasicMathGate,
+Sec. 4.3.3) against the oracle, and Shor's order finding for 7 mod 15 with
+the semi-classical measure-and-reset loop of Appendix A.3."""
+import math
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1612_08091_gb300 as q
+
+    q.load()
+    return q
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("qubits,controls", [((0, 1, 2, 3), ()), ((13, 2, 7), (0,)), (tuple(range(4, 16)), ()),
+                                             ((5, 9), (1, 3, 11))])
+def test_permutation_matches_oracle(qs, oracle_mod, prec, qubits, controls):
+    n = 16
+    rng = np.random.default_rng(len(qubits) + 7 * len(controls))
+    perm = rng.permutation(1 << len(qubits))
+    psi = cg.random_state(n, seed=4)
+    ref = oracle_mod.OracleSim(n, psi=psi)
+    ref.apply_permutation(perm, qubits, controls)
+    with qs.Simulator(n, precision=prec) as sim:
+        sim.set_amplitudes(psi)
+        sim.apply_permutation(perm, qubits, controls)
+        got = sim.get_amplitudes()
+    tol = 0 if prec == "c128" else 1e-7  # amplitudes only move (c64 storage rounding only)
+    np.testing.assert_allclose(got, ref.psi, atol=tol)
+
+
+def test_permutation_rejects_non_bijection(qs):
+    with qs.Simulator(6) as sim:
+        with pytest.raises(qs.QsimError) as e:
+            sim.apply_permutation([0, 0, 1, 2], [0, 1])
+        assert e.value.status == "EINVAL"
+
+
+def shor_order_finding(sim, a, N, m, draws):
+    """Register x on qubits 1..4 starts at |1>; qubit 0 is the recycled
+    control.  Round k: H, controlled multiply-by a^(2^(m-1-k)) mod N (an
+    emulated permutation: identity for x >= N), rotations conditioned on
+    the earlier outcomes, H, measure, reset."""
+    xq = [1, 2, 3, 4]
+    sim.apply_op(cg.op("X", (1,)))
+    bits = []
+    for k in range(m):
+        ak = pow(a, 1 << (m - 1 - k), N)
+        perm = [(ak * x) % N if x < N else x for x in range(16)]
+        sim.apply_op(cg.op("H", (0,)))
+        sim.apply_permutation(perm, xq, (0,))
+        for i in range(k):
+            if bits[i]:
+                sim.apply_op(cg.op("R", (0,), (), (-math.pi / (1 << (k - i)),)))
+        sim.apply_op(cg.op("H", (0,)))
+        b = sim.measure(0, draws[k])
+        b = b[0] if isinstance(b, tuple) else b
+        bits.append(b)
+        if b:
+            sim.apply_op(cg.op("X", (0,)))
+    # bits come least significant first: phase = sum bits[k] 2^k / 2^m
+    return sum(b << k for k, b in enumerate(bits))
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_shor_order_finding_7_mod_15(qs, oracle_mod, prec):
+    a, N, m = 7, 15, 6
+    seen = set()
+    for trial in range(6):
+        draws = cg.uniform_draws(500 + trial, m)
+        ref = oracle_mod.OracleSim(5)
+        want = shor_order_finding(ref, a, N, m, draws)
+        with qs.Simulator(5, precision=prec) as sim:
+            got = shor_order_finding(sim, a, N, m, draws)
+        assert got == want
+        # the order of 7 mod 15 is 4: the measured phase is s/4 exactly
+        assert (got * 4) % (1 << m) == 0
+        seen.add(got)
+    assert len(seen) >= 2  # different draws reach different multiples of 2^m/4

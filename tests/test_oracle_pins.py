@@ -339,3 +339,31 @@ def test_semiclassical_phase_estimation_oracle(oracle_mod):
         s = _sim(oracle_mod, 3)
         bits = mod.phase_estimation(s, m, k, cg.uniform_draws(k, m))
         assert bits == [(k >> j) & 1 for j in range(m)]
+
+
+def test_permutation_emulation_pins(oracle_mod):
+    """The oracle's register permutation (Sec. 4.3.3 emulation): identity,
+    an inverse pair, and agreement with the permutation matrix applied as an
+    ordinary (controlled) gate."""
+    n = 6
+    rng = np.random.default_rng(3)
+    psi = cg.random_state(n, seed=33)
+    s = _sim(oracle_mod, n, psi=psi)
+    s.apply_permutation(np.arange(8), [4, 1, 2])
+    np.testing.assert_array_equal(s.psi, psi)
+    add5 = (np.arange(16) + 5) % 16
+    sub5 = (np.arange(16) - 5) % 16
+    s.apply_permutation(add5, [0, 2, 3, 5])
+    assert np.max(np.abs(s.psi - psi)) > 0.1
+    s.apply_permutation(sub5, [0, 2, 3, 5])
+    np.testing.assert_allclose(s.psi, psi, atol=0)
+    for qubits, controls in [((1, 3), ()), ((5, 0, 2), (4,)), ((2, 3, 4, 0), (1,))]:
+        m = len(qubits)
+        perm = rng.permutation(1 << m)
+        P = np.zeros((1 << m, 1 << m))
+        P[perm, np.arange(1 << m)] = 1.0  # column x has its 1 in row perm[x]
+        a = _sim(oracle_mod, n, psi=psi)
+        a.apply_permutation(perm, qubits, controls)
+        b = _sim(oracle_mod, n, psi=psi)
+        b.apply(P, qubits, controls)
+        np.testing.assert_allclose(a.psi, b.psi, atol=1e-15)
