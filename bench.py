@@ -158,6 +158,26 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def kernel_traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), scaled from the captured register size to n
+    (the block kernel's traffic is proportional to 2^n).  None if there is
+    no capture or the kernel's source changed since it was taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    if digest != rec["sha256"]:
+        return None
+    return rec["bytes_per_launch"] * 2.0 ** (n - rec["n"])
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -305,8 +325,9 @@ def run_ours(args):
         per_launch_s = dom["total_ms"] / dom["launches"] / 1e3
         achieved = per_launch_bytes / per_launch_s / 1e9
         step_ms_total = sum(v["total_ms"] for v in kt.values())
+        traffic = kernel_traffic("k_block_tc", n) if dom_name == "block_tc" else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_kind, "traffic": None, "kernel": dom_name,
+                "peak_source": peak_kind, "traffic": traffic, "kernel": dom_name,
                 "alg_bytes_per_launch": per_launch_bytes, "launches_per_step": dom["launches"] / args.steps,
                 "share_of_gate_time": dom["total_ms"] / step_ms_total if step_ms_total else None}
 

@@ -127,6 +127,12 @@ struct TcArgs {
     const double *norm_prev;
     int prev_grid;
     int streaming;             // 1: evict-first hints on the state's loads and stores
+    // per-step tables (same values as in RecTables), read with compile-time
+    // indices from the constant bank instead of shared memory
+    uint64_t ai[16];
+    uint32_t lin_i[16];
+    uint32_t swz_i[16];
+    uint64_t rdep[32];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -386,10 +392,10 @@ __global__ void __launch_bounds__(kTcThreads, (ABUF == 2 ? 2 : 3)) k_block_tc(co
             const float2 *p = psi_in + base + toff0;
             if (args.streaming) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) regs[i] = __ldcs((const float4 *)(p + tab->ai[i]));
+                for (int i = 0; i < 16; ++i) regs[i] = __ldcs((const float4 *)(p + args.ai[i]));
             } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) regs[i] = *(const float4 *)(p + tab->ai[i]);
+                for (int i = 0; i < 16; ++i) regs[i] = *(const float4 *)(p + args.ai[i]);
             }
         };
         auto epilogue = [&](uint64_t tt, int j) {
@@ -416,9 +422,9 @@ __global__ void __launch_bounds__(kTcThreads, (ABUF == 2 ? 2 : 3)) k_block_tc(co
                         const float4 o = make_float4(v[2 * q] * scale, v[2 * q + 1] * scale, v[2 * q + 2] * scale,
                                                      v[2 * q + 3] * scale);
                         if (args.streaming)
-                            __stcs((float4 *)(psi + base + tab->rdep[r]), o);
+                            __stcs((float4 *)(psi + base + args.rdep[r]), o);
                         else
-                            *(float4 *)(psi + base + tab->rdep[r]) = o;
+                            *(float4 *)(psi + base + args.rdep[r]) = o;
                     }
                 } else {
 #pragma unroll
@@ -426,9 +432,9 @@ __global__ void __launch_bounds__(kTcThreads, (ABUF == 2 ? 2 : 3)) k_block_tc(co
                         const int r = chunk * 16 + q;
                         const float2 o = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
                         if (args.streaming)
-                            __stcs(psi + base + tab->rdep[r], o);
+                            __stcs(psi + base + args.rdep[r], o);
                         else
-                            psi[base + tab->rdep[r]] = o;
+                            psi[base + args.rdep[r]] = o;
                     }
                 }
             }
@@ -459,7 +465,7 @@ __global__ void __launch_bounds__(kTcThreads, (ABUF == 2 ? 2 : 3)) k_block_tc(co
             for (int i = 0; i < 16; ++i) {
                 xsq = fmaf(regs[i].x, regs[i].x, fmaf(regs[i].y, regs[i].y, xsq));
                 xsq = fmaf(regs[i].z, regs[i].z, fmaf(regs[i].w, regs[i].w, xsq));
-                const uint32_t li = tab->lin_i[i], si = tab->swz_i[i];
+                const uint32_t li = args.lin_i[i], si = args.swz_i[i];
                 if (pair_r) {
                     put_amp2_off(a_hi, a_lo, lin0 + li + (swz0 ^ si), regs[i]);
                 } else {
@@ -717,12 +723,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_block_tc_ws(const TcArgs args
             if (pair_r) {
 #pragma unroll
                 for (int q = 0; q < 16; q += 2)
-                    *(float4 *)(psi_ptr(args) + base + tab->rdep[r0 + q]) =
+                    *(float4 *)(psi_ptr(args) + base + args.rdep[r0 + q]) =
                         make_float4(v[2 * q] * scale, v[2 * q + 1] * scale, v[2 * q + 2] * scale, v[2 * q + 3] * scale);
             } else {
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    psi_ptr(args)[base + tab->rdep[r0 + q]] = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
+                    psi_ptr(args)[base + args.rdep[r0 + q]] = make_float2(v[2 * q] * scale, v[2 * q + 1] * scale);
             }
             return true;
         };
@@ -745,7 +751,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_block_tc_ws(const TcArgs args
                 const float4 x = sb[(e0 | tab->ei[i2]) >> 1];
                 xsq = fmaf(x.x, x.x, fmaf(x.y, x.y, xsq));
                 xsq = fmaf(x.z, x.z, fmaf(x.w, x.w, xsq));
-                const uint32_t li = tab->lin_i[i2], si = tab->swz_i[i2];
+                const uint32_t li = args.lin_i[i2], si = args.swz_i[i2];
                 if (pair_r) {
                     put_amp2_off(a_hi, a_lo, lin0 + li + (swz0 ^ si), x);
                 } else {
@@ -1141,6 +1147,15 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     a.norm_prev = (s->norm_tracking && s->tc_passes > 0) ? slots + (slot ^ 1) * 2 * kMaxTcGrid : nullptr;
     a.prev_grid = s->tc_prev_grid;
     a.streaming = s->tc_streaming;
+    {
+        const RecTables *T = (const RecTables *)(rec.data() + (size_t)nsplit * kBBytes);
+        for (int i = 0; i < 16; ++i) {
+            a.ai[i] = T->ai[i];
+            a.lin_i[i] = T->lin_i[i];
+            a.swz_i[i] = T->swz_i[i];
+        }
+        for (int r = 0; r < 32; ++r) a.rdep[r] = T->rdep[r];
+    }
     if (ws)
         k_block_tc_ws<<<(unsigned)grid, kWsThreads, smem_bytes_ws(nsplit), s->stream>>>(a);
     else

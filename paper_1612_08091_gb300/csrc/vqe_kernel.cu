@@ -16,12 +16,12 @@
 // (largest circuits first) until the batch is done; there is no waiting on
 // other CTAs.  A circuit of n <= m qubits (m = 12..14, tuned) lives in the
 // CTA's shared memory; a larger one lives in a per-CTA pair of global
-// buffers and is processed in cache-blocked tiles of 2^m amplitudes: one
-// tile pass applies the gates on qubits 0..m-1, a second (tiles made of runs
-// of 2^(m-h) amplitudes times the h = n-m top qubits) applies the gates on
-// the top qubits, and a third applies the CNOT permutation into the other
-// buffer.  Amplitudes are complex64 in FP32 arithmetic; energies accumulate
-// per thread in FP32 over a few terms and in FP64 beyond.
+// buffers and is processed in cache-blocked tiles of 2^m amplitudes: a low
+// pass gathers each chunk through the previous layer's CNOT permutation and
+// applies the gates on qubits 0..m-1, a high pass (tiles made of runs of
+// 2^(m-h) amplitudes times the h = n-m top qubits) applies the gates on the
+// top qubits.  Amplitudes are complex64 in FP32 arithmetic; energies
+// accumulate per thread in FP32 over a few terms and in FP64 beyond.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -182,60 +182,95 @@ __global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
             for (int q = 0; q < n; ++q) xx += (double)x_chunk(sm, n, q);
         } else {
             // --- global-memory circuit, cache-blocked tiles of 2^m --------------
+            // Each layer is two passes over the state in the per-CTA buffers:
+            //   low pass:  chunks of 2^m consecutive amplitudes; the chunk is
+            //              gathered through the previous layer's CNOT-ladder
+            //              permutation psi'[y] = psi[y ^ (y << 1)] from the
+            //              source buffer, gets the gates on qubits 0..m-1 in
+            //              shared memory and is written to the other buffer;
+            //   high pass: tiles of runs of 2^(m-h) amplitudes times the h top
+            //              qubits, in place, gates on qubits m..n-1.
+            // The last layer's permutation is applied by the energy passes'
+            // gathers.  Global loads are issued in batches of 8 per thread so
+            // their latencies overlap.
             const int m = A.m, h = n - m, lowrun = m - h;  // lowrun >= 5 by construction
-            float2 *b0 = A.gbuf + (size_t)blockIdx.x * 2 * A.gstride;
-            float2 *b1 = b0 + A.gstride;
-            for (unsigned i = threadIdx.x; i < N; i += T) b0[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+            float2 *src = A.gbuf + (size_t)blockIdx.x * 2 * A.gstride;
+            float2 *dst = src + A.gstride;
+            const unsigned M = 1u << m, nchunks = 1u << h, mask = N - 1;
+            constexpr int kB = T >= 1024 ? 4 : 8;
+            for (unsigned i = threadIdx.x; i < N; i += T) src[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
             __syncthreads();
-            const unsigned nchunks = 1u << h;
+            bool permuted = false;  // src holds the state before a pending ladder permutation
+            auto gather_chunk = [&](const float2 *from, unsigned ch) {
+                for (unsigned i0 = threadIdx.x; i0 < M; i0 += T * kB) {
+                    float2 v[kB];
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        const unsigned i = i0 + u * T;
+                        const unsigned y = (ch << m) | i;
+                        if (i < M) v[u] = from[permuted ? ladder_src(y, mask) : y];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        const unsigned i = i0 + u * T;
+                        if (i < M) sm[i] = v[u];
+                    }
+                }
+                __syncthreads();
+            };
+            auto tile_index = [&](unsigned t, unsigned e) {
+                const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
+                return lo | (t << lowrun) | (top << m);
+            };
+            auto gather_tile = [&](const float2 *from, unsigned t, bool through_perm) {
+                for (unsigned e0 = threadIdx.x; e0 < M; e0 += T * kB) {
+                    float2 v[kB];
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        const unsigned e = e0 + u * T;
+                        const unsigned y = tile_index(t, e);
+                        if (e < M) v[u] = from[through_perm ? ladder_src(y, mask) : y];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        const unsigned e = e0 + u * T;
+                        if (e < M) sm[e] = v[u];
+                    }
+                }
+                __syncthreads();
+            };
             for (int l = 0; l < L; ++l) {
                 const double *al = ang + 2 * l * n;
-                // qubits 0..m-1: contiguous chunks
+                // low pass: src (through the pending permutation) -> dst
                 for (unsigned ch = 0; ch < nchunks; ++ch) {
-                    float2 *g = b0 + ((size_t)ch << m);
-                    for (unsigned i = threadIdx.x; i < (1u << m); i += T) sm[i] = g[i];
-                    __syncthreads();
+                    gather_chunk(src, ch);
                     for (int q = 0; q < m; ++q) gate_smem(sm, m, q, make_gate(al[q], al[n + q]));
-                    for (unsigned i = threadIdx.x; i < (1u << m); i += T) g[i] = sm[i];
+                    float2 *g = dst + ((size_t)ch << m);
+                    for (unsigned i = threadIdx.x; i < M; i += T) g[i] = sm[i];
                     __syncthreads();
                 }
-                // qubits m..n-1: tiles = runs of 2^lowrun amplitudes x the h top qubits
+                // high pass on dst, in place
                 for (unsigned t = 0; t < nchunks; ++t) {
-                    for (unsigned e = threadIdx.x; e < (1u << m); e += T) {
-                        const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
-                        sm[e] = b0[lo | (t << lowrun) | (top << m)];
-                    }
-                    __syncthreads();
+                    gather_tile(dst, t, false);
                     for (int q = m; q < n; ++q) gate_smem(sm, m, lowrun + (q - m), make_gate(al[q], al[n + q]));
-                    for (unsigned e = threadIdx.x; e < (1u << m); e += T) {
-                        const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
-                        b0[lo | (t << lowrun) | (top << m)] = sm[e];
-                    }
+                    for (unsigned e = threadIdx.x; e < M; e += T) dst[tile_index(t, e)] = sm[e];
                     __syncthreads();
                 }
-                // CNOT ladder into the other buffer
-                for (unsigned y = threadIdx.x; y < N; y += T) b1[y] = b0[ladder_src(y, N - 1)];
-                __syncthreads();
-                float2 *tmp = b0;
-                b0 = b1;
-                b1 = tmp;
+                float2 *tmp = src;
+                src = dst;
+                dst = tmp;
+                permuted = true;  // this layer's CNOT ladder is still to be applied
             }
-            // energy: ZZ and X on qubits < m per chunk, X on the top qubits per tile
+            // energy of the permuted state, read through the permutation
             float zf = 0.f, xf = 0.f;
             for (unsigned ch = 0; ch < nchunks; ++ch) {
-                const float2 *g = b0 + ((size_t)ch << m);
-                for (unsigned i = threadIdx.x; i < (1u << m); i += T) sm[i] = g[i];
-                __syncthreads();
+                gather_chunk(src, ch);
                 zf += zz_chunk(sm, m, (unsigned long long)ch << m, n);
                 for (int q = 0; q < m; ++q) xf += x_chunk(sm, m, q);
                 __syncthreads();
             }
             for (unsigned t = 0; t < nchunks; ++t) {
-                for (unsigned e = threadIdx.x; e < (1u << m); e += T) {
-                    const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
-                    sm[e] = b0[lo | (t << lowrun) | (top << m)];
-                }
-                __syncthreads();
+                gather_tile(src, t, permuted);
                 for (int q = m; q < n; ++q) xf += x_chunk(sm, m, lowrun + (q - m));
                 __syncthreads();
             }
