@@ -99,6 +99,97 @@ __device__ __forceinline__ void gate_smem(float2 *x, int k, int bit, const Gate1
 
 __device__ __forceinline__ unsigned ladder_src(unsigned y, unsigned mask) { return (y ^ (y << 1)) & mask; }
 
+// Gates on `nb` bits of a 2^k-amplitude array in shared memory, applied four
+// bits at a time in registers: each thread loads the 16 amplitudes of a group
+// that differ only in four of the bits, applies those bits' gates there and
+// stores them back, so a layer of k one-qubit gates costs ceil(k/4) passes
+// over shared memory instead of k.  bit[j] is the array bit of gate g[j];
+// a group of fewer than four bits is padded with identity gates on other
+// bits.
+__device__ __forceinline__ void cswap(int &a, int &b) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+__device__ void gates_blocked(float2 *x, int k, const int *bit, const Gate1 *g, int nb, const Gate1 *ident) {
+    if (k < 4) {
+        // fewer than four bits in the array: one pass per gate
+        for (int j = 0; j < nb; ++j) gate_smem(x, k, bit[j], g[j]);
+        return;
+    }
+    for (int g0 = 0; g0 < nb; g0 += 4) {
+        // the group's four bits (padded with identity gates on unused bits)
+        int p0, p1, p2, p3;
+        const Gate1 *q0, *q1, *q2, *q3;
+        {
+            int pos[4];
+            const Gate1 *gg[4];
+            unsigned used = 0;
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (g0 + j < nb) {
+                    pos[j] = bit[g0 + j];
+                    gg[j] = &g[g0 + j];
+                    used |= 1u << pos[j];
+                    cnt = j + 1;
+                }
+            int b = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j >= cnt) {
+                    while ((used >> b) & 1u) ++b;
+                    pos[j] = b;
+                    gg[j] = ident;
+                    used |= 1u << b;
+                }
+            p0 = pos[0]; p1 = pos[1]; p2 = pos[2]; p3 = pos[3];
+            q0 = gg[0]; q1 = gg[1]; q2 = gg[2]; q3 = gg[3];
+        }
+        int s0 = p0, s1 = p1, s2 = p2, s3 = p3;  // sorted copy for the zero insertion
+        cswap(s0, s1);
+        cswap(s2, s3);
+        cswap(s0, s2);
+        cswap(s1, s3);
+        cswap(s1, s2);
+        const unsigned m0 = 1u << p0, m1 = 1u << p1, m2 = 1u << p2, m3 = 1u << p3;
+        const unsigned ngroups = 1u << (k - 4);
+        for (unsigned gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+            unsigned base = gi;
+            base = ((base >> s0) << (s0 + 1)) | (base & ((1u << s0) - 1u));
+            base = ((base >> s1) << (s1 + 1)) | (base & ((1u << s1) - 1u));
+            base = ((base >> s2) << (s2 + 1)) | (base & ((1u << s2) - 1u));
+            base = ((base >> s3) << (s3 + 1)) | (base & ((1u << s3) - 1u));
+            float2 v[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                v[r] = x[base | ((r & 1) ? m0 : 0u) | ((r & 2) ? m1 : 0u) | ((r & 4) ? m2 : 0u) | ((r & 8) ? m3 : 0u)];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const Gate1 *G = j == 0 ? q0 : j == 1 ? q1 : j == 2 ? q2 : q3;
+                const float2 u00 = G->u00, u01 = G->u01, u10 = G->u10, u11 = G->u11;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    if ((r >> j) & 1) continue;
+                    const int r1 = r | (1 << j);
+                    const float2 a = v[r], bb = v[r1];
+                    float2 na = cmul(u00, a);
+                    na = cfma(u01, bb, na);
+                    float2 nb2 = cmul(u10, a);
+                    nb2 = cfma(u11, bb, nb2);
+                    v[r] = na;
+                    v[r1] = nb2;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                x[base | ((r & 1) ? m0 : 0u) | ((r & 2) ? m1 : 0u) | ((r & 4) ? m2 : 0u) | ((r & 8) ? m3 : 0u)] = v[r];
+        }
+        __syncthreads();
+    }
+}
+
 __device__ double block_sum_d(double v, double *sh) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -146,6 +237,15 @@ __global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
     extern __shared__ float2 sm[];
     __shared__ int s_idx;
     __shared__ double s_red[32];
+    __shared__ Gate1 s_gate[32];   // this layer's RZ RY per qubit; [31] = identity
+    __shared__ int s_bit[32];      // array bit of each gate in the current pass
+    if (threadIdx.x == 0) {
+        s_gate[31].u00 = make_float2(1.f, 0.f);
+        s_gate[31].u01 = make_float2(0.f, 0.f);
+        s_gate[31].u10 = make_float2(0.f, 0.f);
+        s_gate[31].u11 = make_float2(1.f, 0.f);
+    }
+    const Gate1 *ident = &s_gate[31];
     for (;;) {
         if (threadIdx.x == 0) s_idx = (int)atomicAdd(A.counter, 1u);
         __syncthreads();
@@ -162,7 +262,12 @@ __global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
             for (unsigned i = threadIdx.x; i < N; i += T) sm[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
             __syncthreads();
             for (int l = 0; l < L; ++l) {
-                for (int q = 0; q < n; ++q) gate_smem(sm, n, q, make_gate(ang[2 * l * n + q], ang[2 * l * n + n + q]));
+                if (threadIdx.x < (unsigned)n) {
+                    s_gate[threadIdx.x] = make_gate(ang[2 * l * n + threadIdx.x], ang[2 * l * n + n + threadIdx.x]);
+                    s_bit[threadIdx.x] = threadIdx.x;
+                }
+                __syncthreads();
+                gates_blocked(sm, n, s_bit, s_gate, n, ident);
                 // CNOT ladder as one permutation through registers
                 float2 v[kRegAmps];
 #pragma unroll
@@ -241,10 +346,14 @@ __global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
             };
             for (int l = 0; l < L; ++l) {
                 const double *al = ang + 2 * l * n;
+                if (threadIdx.x < (unsigned)n) s_gate[threadIdx.x] = make_gate(al[threadIdx.x], al[n + threadIdx.x]);
+                if (threadIdx.x < (unsigned)m) s_bit[threadIdx.x] = threadIdx.x;
+                if (threadIdx.x < (unsigned)h) s_bit[m + threadIdx.x] = lowrun + threadIdx.x;
+                __syncthreads();
                 // low pass: src (through the pending permutation) -> dst
                 for (unsigned ch = 0; ch < nchunks; ++ch) {
                     gather_chunk(src, ch);
-                    for (int q = 0; q < m; ++q) gate_smem(sm, m, q, make_gate(al[q], al[n + q]));
+                    gates_blocked(sm, m, s_bit, s_gate, m, ident);
                     float2 *g = dst + ((size_t)ch << m);
                     for (unsigned i = threadIdx.x; i < M; i += T) g[i] = sm[i];
                     __syncthreads();
@@ -252,7 +361,7 @@ __global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
                 // high pass on dst, in place
                 for (unsigned t = 0; t < nchunks; ++t) {
                     gather_tile(dst, t, false);
-                    for (int q = m; q < n; ++q) gate_smem(sm, m, lowrun + (q - m), make_gate(al[q], al[n + q]));
+                    gates_blocked(sm, m, s_bit + m, s_gate + m, h, ident);
                     for (unsigned e = threadIdx.x; e < M; e += T) dst[tile_index(t, e)] = sm[e];
                     __syncthreads();
                 }
