@@ -158,22 +158,29 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+# profiling class of the library -> kernel name in profiles/traffic.json
+TRAFFIC_KERNEL = {"block_tc": "k_block_tc", "block_tc6": "k_block_tc6"}
+
+
 def kernel_traffic(kernel, n):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.json), scaled from the captured register size to n
-    (the block kernel's traffic is proportional to 2^n).  None if there is
-    no capture or the kernel's source changed since it was taken."""
+    (the block kernels' traffic is proportional to 2^n).  None if there is
+    no capture or the kernel's sources changed since it was taken (SHA-256
+    over the listed source files, in order)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)[kernel]
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
-    except (OSError, KeyError, ValueError):
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, KeyError, ValueError, TypeError):
         return None
-    if digest != rec["sha256"]:
+    if h.hexdigest() != rec["sha256"]:
         return None
     return rec["bytes_per_launch"] * 2.0 ** (n - rec["n"])
 
@@ -325,7 +332,7 @@ def run_ours(args):
         per_launch_s = dom["total_ms"] / dom["launches"] / 1e3
         achieved = per_launch_bytes / per_launch_s / 1e9
         step_ms_total = sum(v["total_ms"] for v in kt.values())
-        traffic = kernel_traffic("k_block_tc", n) if dom_name == "block_tc" else None
+        traffic = kernel_traffic(TRAFFIC_KERNEL[dom_name], n) if dom_name in TRAFFIC_KERNEL else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_kind, "traffic": traffic, "kernel": dom_name,
                 "alg_bytes_per_launch": per_launch_bytes, "launches_per_step": dom["launches"] / args.steps,

@@ -82,7 +82,9 @@ typedef struct qsim_opts {
     size_t workspace_bytes; /* its size; must be >= sim_workspace_bytes() */
     void *stream;           /* cudaStream_t to run on; NULL = legacy default stream */
     int fusion;             /* enum qsim_fusion; default QSIM_FUSE_NONE */
-    int kmax;               /* largest fused block, 1..5; 0 = default 5 */
+    int kmax;               /* largest fused block, 1..6; 0 = default 5.  6-qubit blocks run
+                               only on the complex64 tensor-core path with n >= 13; elsewhere
+                               kmax 6 plans blocks of at most 5 qubits */
     int device;             /* CUDA device ordinal; the current device is used if < 0 */
     int tc_terms;           /* complex64 tensor-core blocks: 3 = BF16x3 (default, 0 means 3),
                                5 = five split products (gate split in three parts) */
@@ -185,7 +187,8 @@ int sim_state_ptr(qsim *s, void **dev_ptr);
  * queued work, which this call waits for). */
 int sim_set_stream(qsim *s, void *stream);
 
-/* Choose the fusion mode (enum qsim_fusion) and block width kmax (1..5).
+/* Choose the fusion mode (enum qsim_fusion) and block width kmax (1..6, see
+ * qsim_opts.kmax).
  * QSIM_FUSE_MLP uses the cost model loaded with sim_set_cost_model (greedy
  * fusion if none is loaded).  Flushes the queue first. */
 int sim_set_fusion(qsim *s, int mode, int kmax);

@@ -65,7 +65,7 @@ double gate_bytes(const qsim *s, const GateRec &g) {
 }
 
 const char *kClassName[KC_COUNT] = {"gate_dense", "gate_phase", "gate_diag", "gate_x",
-                                    "block_tc",   "block_dense", "block_diag"};
+                                    "block_tc",   "block_dense", "block_diag", "block_tc6"};
 
 int harvest(qsim *s) {
     if (s->pending.empty()) return QSIM_OK;
@@ -112,6 +112,14 @@ int gate_class(const GateRec &g) {
     }
 }
 
+// Widest block the executors take: 6-qubit blocks exist only as the
+// complex64 tensor-core kernel (tiles of 2^13 amplitudes); elsewhere kmax 6
+// plans 5-qubit blocks.
+int block_kmax(const qsim *s) {
+    if (s->kmax == 6 && (s->prec != QSIM_C64 || !s->tc_enabled || s->n < 13)) return 5;
+    return s->kmax;
+}
+
 int execute_plan(qsim *s, const std::vector<PlanItem> &plan) {
     for (const PlanItem &it : plan) {
         int rc;
@@ -134,7 +142,11 @@ int execute_plan(qsim *s, const std::vector<PlanItem> &plan) {
         } else {
             rc = QSIM_ENOTSUP;
             cls = KC_BLOCK_TC;
-            if (s->prec == QSIM_C64 && it.k >= 4) rc = launch_block_tc(s, it.qubits, it.k, it.m.data());
+            if (it.k == 6) {
+                cls = KC_BLOCK_TC6;
+                rc = launch_block_tc6(s, it.qubits, it.m.data());
+            } else if (s->prec == QSIM_C64 && it.k >= 4)
+                rc = launch_block_tc(s, it.qubits, it.k, it.m.data());
             if (rc == QSIM_ENOTSUP) {
                 cls = KC_BLOCK_DENSE;
                 rc = launch_block_dense(s, it.qubits, it.k, it.m.data());
@@ -168,7 +180,7 @@ int flush(qsim *s) {
     else if (s->fusion == QSIM_FUSE_MLP && s->cost.loaded())
         plan_mlp(s->queue, s->n, s->prec, s->tc_enabled, s->cost, plan, &s->last_plan_predicted_ms);
     else
-        plan_greedy(s->queue, s->n, s->kmax, plan);
+        plan_greedy(s->queue, s->n, block_kmax(s), plan);
     const int rc = execute_plan(s, plan);
     s->queue.clear();
     return rc;
@@ -235,7 +247,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     if (opts) o = *opts;
     if (o.fusion < QSIM_FUSE_NONE || o.fusion > QSIM_FUSE_MLP) return QSIM_EINVAL;
     if (o.kmax == 0) o.kmax = 5;
-    if (o.kmax < 1 || o.kmax > 5) return QSIM_EINVAL;
+    if (o.kmax < 1 || o.kmax > 6) return QSIM_EINVAL;
     qsim *s = new (std::nothrow) qsim();
     if (!s) return QSIM_ENOMEM;
     s->n = n;
@@ -537,7 +549,7 @@ int sim_set_stream(qsim *s, void *stream) {
 int sim_set_fusion(qsim *s, int mode, int kmax) {
     if (!s) return QSIM_EINVAL;
     if (mode < QSIM_FUSE_NONE || mode > QSIM_FUSE_MLP) return set_err(s, QSIM_EINVAL, "unknown fusion mode");
-    if (kmax < 1 || kmax > 5) return set_err(s, QSIM_EINVAL, "kmax outside 1..5");
+    if (kmax < 1 || kmax > 6) return set_err(s, QSIM_EINVAL, "kmax outside 1..6");
     int rc = flush(s);
     if (rc) return rc;
     s->fusion = mode;

@@ -53,8 +53,10 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 using namespace qsim_dev;
+using namespace qsim_tc;
 
 namespace {
 
@@ -64,8 +66,7 @@ constexpr int kABytes = 128 * 128;       // one bf16 split of X: 128 rows x 128 
 constexpr int kBBytes = 64 * 128;        // one bf16 split of R: 64 rows x 128 B
 constexpr int kTablesBytes = 4688;
 constexpr uint32_t kTmemCols = 128;      // two 64-column fp32 accumulators
-constexpr uint32_t kWaitLimit = 1u << 24;
-constexpr int kMaxTcGrid = 4 * kSMs;
+static_assert(kMaxTcGrid == 4 * kSMs, "norm slot stride");
 
 // Layout of the per-block operand record (host-built, copied to smem as is).
 // Thread t handles tile elements e = e0(t) | ei(i) | h (bit sets disjoint):
@@ -135,51 +136,8 @@ struct TcArgs {
     uint64_t rdep[32];
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait; returns false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 64-bit shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of
-// 128 B, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset between 8-row groups
-    d |= (uint64_t)1 << 46;             // descriptor version
-    d |= (uint64_t)2 << 61;             // 128-byte swizzle
-    return d;
-}
-
 // Instruction descriptor: D fp32, A and B bf16, both K-major, M = 128, N = 64.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc = idesc_bf16(128, 64);
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
@@ -190,97 +148,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 consecutive fp32 columns of this warp's 32 TMEM lanes; the wait is in
-// the same asm statement, so the registers are complete when it returns
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo_half, float hi_half) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo_half, hi_half);
-    uint32_t u;
-    memcpy(&u, &h, 4);
-    return u;
-}
-
-// Write one amplitude (re, im) at block row r of tile column c into the hi
-// and lo A buffers (128-byte swizzle: 16-byte chunk index ^= row & 7).
-__device__ __forceinline__ void put_amp(unsigned char *a_hi, unsigned char *a_lo, int c, int r, float re, float im) {
-    const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
-    const float rr = re - __bfloat162float(hr), ri = im - __bfloat162float(hi_);
-    __nv_bfloat162 h2;
-    h2.x = hr;
-    h2.y = hi_;
-    uint32_t hw;
-    memcpy(&hw, &h2, 4);
-    const uint32_t lw = pack_bf16x2(rr, ri);
-    const int off = c * 128 + ((((r >> 2) ^ c) & 7) << 4) + ((r & 3) << 2);
-    *(uint32_t *)(a_hi + off) = hw;
-    *(uint32_t *)(a_lo + off) = lw;
-}
-
 __device__ __forceinline__ float2 *psi_ptr(const TcArgs &a) { return a.psi; }
-
-// Two amplitudes of the same column at rows r (even) and r+1: one 8-byte
-// write per split.
-__device__ __forceinline__ void put_amp2(unsigned char *a_hi, unsigned char *a_lo, int c, int r, float4 v) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
-    const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
-    __nv_bfloat162 p0, p1;
-    p0.x = h0;
-    p0.y = h1;
-    p1.x = h2;
-    p1.y = h3;
-    uint2 hw, lw;
-    memcpy(&hw.x, &p0, 4);
-    memcpy(&hw.y, &p1, 4);
-    lw.x = pack_bf16x2(v.x - __bfloat162float(h0), v.y - __bfloat162float(h1));
-    lw.y = pack_bf16x2(v.z - __bfloat162float(h2), v.w - __bfloat162float(h3));
-    const int off = c * 128 + ((((r >> 2) ^ c) & 7) << 4) + ((r & 3) << 2);
-    *(uint2 *)(a_hi + off) = hw;
-    *(uint2 *)(a_lo + off) = lw;
-}
-
-// Split (re, im) into bf16 hi = round-to-nearest and lo = round-to-nearest
-// bf16 of the exact remainder x - hi (hi + lo carries x to 2^-16 relative).
-// A truncated hi costs the same instructions but biases the dropped lo x lo
-// product and doubles the norm drift, so hi is rounded.
-__device__ __forceinline__ void split_pair(float re, float im, uint32_t &hw, uint32_t &lw) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
-    memcpy(&hw, &h, 4);
-    const float rr = re - __uint_as_float(hw << 16);
-    const float ri = im - __uint_as_float(hw & 0xFFFF0000u);
-    lw = pack_bf16x2(rr, ri);
-}
 
 // one amplitude at precomputed operand offset `off`
 __device__ __forceinline__ void put_amp_off(unsigned char *a_hi, unsigned char *a_lo, uint32_t off, float re,
@@ -805,19 +673,6 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_block_tc_ws(const TcArgs args
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-uint16_t f32_to_bf16_bits(float f) {
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    const uint32_t round = 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)((u + round) >> 16);
-}
-double bf16_bits_to_double(uint16_t h) {
-    const uint32_t u = (uint32_t)h << 16;
-    float f;
-    std::memcpy(&f, &u, 4);
-    return (double)f;
-}
-
 // Embed a k-qubit block (k < 5) into 5 qubits by adding the lowest qubits
 // not in S, on which it acts as the identity.
 void pad_to_five(int n, const int *q, int k, const cd *m, int *q5, std::vector<cd> &m5) {

@@ -39,7 +39,7 @@ struct PlanItem {
     std::vector<cd> dtab;     // its 2^popc(dmask) factors, index bit j = j-th qubit of dmask
     int gate = -1;
     int k = 0;              // fused block width
-    int qubits[5] = {0, 0, 0, 0, 0};  // sorted ascending; bit j of the block index
+    int qubits[6] = {0, 0, 0, 0, 0, 0};  // sorted ascending; bit j of the block index
     std::vector<cd> m;      // 2^k x 2^k block matrix
     double amp_updates = 0; // credited to the original gates
     int ngates = 0;
@@ -98,7 +98,9 @@ struct qsim {
     ClassTime class_time[8];
 };
 
-enum KernelClass { KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_BLOCK_DIAG, KC_COUNT };
+enum KernelClass {
+    KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_BLOCK_DIAG, KC_BLOCK_TC6, KC_COUNT
+};
 constexpr int kMaxDiagQubits = 12;
 
 // Bytes of one amplitude.
@@ -114,7 +116,8 @@ constexpr size_t kWsChunkBytes = 64u << 10;
 constexpr size_t kWsErr = kWsChunk + kWsChunkBytes;     // device error flags
 constexpr size_t kWsErrBytes = 256;
 constexpr size_t kWsNorm = kWsErr + kWsErrBytes;        // block-pass norm partials
-constexpr size_t kWsNormBytes = 32u << 10;  // 2 slots x 2 sums x up to 608 CTAs
+constexpr size_t kWsNormBytes = 32u << 10;  // 2 slots x 2 sums x up to kMaxTcGrid CTAs
+constexpr int kMaxTcGrid = 608;             // CTAs of a block pass: 4 per SM at most
 constexpr size_t kWsRing = kWsNorm + kWsNormBytes;      // block operand ring
 constexpr size_t kWsRingBytes = 16u << 20;
 constexpr size_t kWsTotal = kWsRing + kWsRingBytes;
@@ -144,6 +147,8 @@ int check_device_errors(qsim *s);
 // Fused tensor-core block (fused_kernel.cu).  Returns QSIM_ENOTSUP when the
 // block cannot run on the tensor-core kernel (caller falls back).
 int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m);
+// 6-qubit block (complex64, tensor cores, n >= 13); QSIM_ENOTSUP otherwise
+int launch_block_tc6(qsim *s, const int *qubits, const cd *m);
 
 // Reductions and measurement (reduce_kernels.cu) ----------------------------
 int run_probs_all(qsim *s, double *p1, double *norm2);
