@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--depth", type=int, default=40)
     ap.add_argument("--precision", default="c64")
     ap.add_argument("--fusion", default="greedy")
-    ap.add_argument("--kmax", type=int, default=5)
+    ap.add_argument("--kmax", type=int, default=6)
     ap.add_argument("--plain-layers", type=int, default=2, help="layers of the plain c128 comparison sample")
     ap.add_argument("--cpu-gates", type=int, default=6, help="gates of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -159,7 +159,7 @@ class ClockSampler:
 
 
 # profiling class of the library -> kernel name in profiles/traffic.json
-TRAFFIC_KERNEL = {"block_tc": "k_block_tc", "block_tc6": "k_block_tc6"}
+TRAFFIC_KERNEL = {"block_tc": "k_block_tmem5", "block_tc6": "k_block_tmem6"}
 
 
 def kernel_traffic(kernel, n):
@@ -455,7 +455,7 @@ def run_vqe(args):
 def run_planner(args):
     """Held-out 33-qubit complex64 random circuits of depth 30: the learned
     planner (trained here on this GPU's timings of 26-28 qubit circuits)
-    against greedy fusion (k <= 5); unfused complex128 on a sample."""
+    against greedy fusion (k <= 6); unfused complex128 on a sample."""
     import torch
 
     import paper_1612_08091_gb300 as q
@@ -507,7 +507,7 @@ def run_planner(args):
            "config": {"workload": "33-qubit random U3 + CNOT brickwork, depth 30 (seed 2018), complex64",
                       "training": {"samples": int(len(ms)), "sizes": [26, 27, 28], "collect_s": collect_s,
                                    "train_mse_log_ms": loss}},
-           "greedy_k5": {"ms": 1e3 * t_greedy, "passes": p_greedy, "value": upd / t_greedy},
+           "greedy_k6": {"ms": 1e3 * t_greedy, "passes": p_greedy, "value": upd / t_greedy},
            "learned": {"ms": 1e3 * t_mlp, "passes": p_mlp, "gain_over_greedy": t_greedy / t_mlp},
            "plain_c128": {"value": rate_plain, "unit": UNIT,
                           "sample": "first layer (%d gates), fp64 arithmetic" % len(layer),

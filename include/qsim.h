@@ -82,7 +82,7 @@ typedef struct qsim_opts {
     size_t workspace_bytes; /* its size; must be >= sim_workspace_bytes() */
     void *stream;           /* cudaStream_t to run on; NULL = legacy default stream */
     int fusion;             /* enum qsim_fusion; default QSIM_FUSE_NONE */
-    int kmax;               /* largest fused block, 1..6; 0 = default 5.  6-qubit blocks run
+    int kmax;               /* largest fused block, 1..6; 0 = default 6.  6-qubit blocks run
                                only on the complex64 tensor-core path with n >= 13; elsewhere
                                kmax 6 plans blocks of at most 5 qubits */
     int device;             /* CUDA device ordinal; the current device is used if < 0 */

@@ -6,6 +6,7 @@
 // fused_kernel.cu and reduce_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -82,7 +83,8 @@ int harvest(qsim *s) {
         if (p.feat >= 0) {
             s->item_feats.insert(s->item_feats.end(), s->pending_feats.begin() + p.feat,
                                  s->pending_feats.begin() + p.feat + kFeatures);
-            s->item_ms.push_back(ms);
+            // the item's cost: device time, or host time where the host is slower
+            s->item_ms.push_back(ms > p.host_ms ? ms : p.host_ms);
         }
     }
     s->pending.clear();
@@ -120,68 +122,104 @@ int block_kmax(const qsim *s) {
     return s->kmax;
 }
 
-int execute_plan(qsim *s, const std::vector<PlanItem> &plan) {
-    for (const PlanItem &it : plan) {
-        int rc;
-        size_t ev0 = 0, ev1 = 0;
-        if (s->profiling) {
-            if (s->pending.size() >= 4096 && (rc = harvest(s))) return rc;
-            if ((rc = record_event(s, &ev0))) return rc;
-        }
-        int cls;
-        double bytes;
-        if (!it.fused) {
-            const GateRec &g = s->queue[it.gate];
-            rc = launch_gate_plain(s, g);
-            bytes = gate_bytes(s, g);
-            cls = gate_class(g);
-        } else if (it.diag_block) {
-            cls = KC_BLOCK_DIAG;
-            rc = launch_block_diag(s, it.dmask, it.dtab.data());
-            bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
-        } else {
-            rc = QSIM_ENOTSUP;
-            cls = KC_BLOCK_TC;
-            if (it.k == 6) {
-                cls = KC_BLOCK_TC6;
-                rc = launch_block_tc6(s, it.qubits, it.m.data());
-            } else if (s->prec == QSIM_C64 && it.k >= 4)
-                rc = launch_block_tc(s, it.qubits, it.k, it.m.data());
-            if (rc == QSIM_ENOTSUP) {
-                cls = KC_BLOCK_DENSE;
-                rc = launch_block_dense(s, it.qubits, it.k, it.m.data());
-            }
-            bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
-        }
-        if (rc) return rc;
-        s->stats.alg_bytes += bytes;
-        if (s->profiling) {
-            if ((rc = record_event(s, &ev1))) return rc;
-            (void)ev1;
-            long feat = -1;
-            if (s->record_items) {
-                feat = (long)s->pending_feats.size();
-                s->pending_feats.resize(s->pending_feats.size() + kFeatures);
-                item_features(it, s->queue, s->n, s->prec, s->tc_enabled, &s->pending_feats[feat]);
-            }
-            s->pending.push_back({cls, ev0, bytes, feat});
-        }
-        s->stats.passes++;
-        s->stats.amp_updates += it.amp_updates;
+// Launch one planned item.  With profiling: events around it; in mode 2
+// also its features and its host time (building the block matrix, the
+// operand record, staging and launching), for the cost model.
+int execute_item(qsim *s, const PlanItem &it) {
+    const auto h0 = std::chrono::steady_clock::now();
+    int rc;
+    size_t ev0 = 0, ev1 = 0;
+    if (s->profiling) {
+        if (s->pending.size() >= 4096 && (rc = harvest(s))) return rc;
+        if ((rc = record_event(s, &ev0))) return rc;
     }
+    int cls;
+    double bytes;
+    if (!it.fused) {
+        const GateRec &g = s->queue[it.gate];
+        rc = launch_gate_plain(s, g);
+        bytes = gate_bytes(s, g);
+        cls = gate_class(g);
+    } else if (it.diag_block) {
+        cls = KC_BLOCK_DIAG;
+        rc = launch_block_diag(s, it.dmask, it.dtab.data());
+        bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
+    } else {
+        rc = QSIM_ENOTSUP;
+        cls = KC_BLOCK_TC;
+        if (it.k == 6) {
+            cls = KC_BLOCK_TC6;
+            rc = launch_block_tmem(s, it.qubits, 6, it.m.data());
+        } else if (s->prec == QSIM_C64 && it.k >= 4)
+            rc = launch_block_tc(s, it.qubits, it.k, it.m.data());
+        if (rc == QSIM_ENOTSUP) {
+            cls = KC_BLOCK_DENSE;
+            rc = launch_block_dense(s, it.qubits, it.k, it.m.data());
+        }
+        bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
+    }
+    if (rc) return rc;
+    const auto h1 = std::chrono::steady_clock::now();
+    s->stats.alg_bytes += bytes;
+    if (s->profiling) {
+        if ((rc = record_event(s, &ev1))) return rc;
+        (void)ev1;
+        long feat = -1;
+        if (s->record_items) {
+            feat = (long)s->pending_feats.size();
+            s->pending_feats.resize(s->pending_feats.size() + kFeatures);
+            item_features(it, s->queue, s->n, s->prec, s->tc_enabled, &s->pending_feats[feat]);
+        }
+        const double host_ms = it.host_ms + std::chrono::duration<double, std::milli>(h1 - h0).count();
+        s->pending.push_back({cls, ev0, bytes, feat, (float)host_ms});
+    }
+    s->stats.passes++;
+    s->stats.amp_updates += it.amp_updates;
+    return QSIM_OK;
+}
+
+int execute_plan(qsim *s, const std::vector<PlanItem> &plan) {
+    for (const PlanItem &it : plan)
+        if (const int rc = execute_item(s, it)) return rc;
     return QSIM_OK;
 }
 
 int flush(qsim *s) {
     if (s->queue.empty()) return QSIM_OK;
-    std::vector<PlanItem> plan;
-    if (s->fusion == QSIM_FUSE_NONE)
-        plan_none(s->queue, s->n, plan);
-    else if (s->fusion == QSIM_FUSE_MLP && s->cost.loaded())
-        plan_mlp(s->queue, s->n, s->prec, s->tc_enabled, s->cost, plan, &s->last_plan_predicted_ms);
-    else
-        plan_greedy(s->queue, s->n, block_kmax(s), plan);
-    const int rc = execute_plan(s, plan);
+    int rc;
+    const std::vector<GateRec> &q = s->queue;
+    MlpChoice ch;
+    if (s->fusion == QSIM_FUSE_MLP && s->cost.loaded()) {
+        plan_mlp(q, s->n, s->prec, s->tc_enabled, block_kmax(s), s->cost, ch);
+        s->last_plan_predicted_ms = ch.predicted_ms;
+    }
+    if (s->fusion == QSIM_FUSE_NONE || (s->fusion == QSIM_FUSE_MLP && s->cost.loaded() && ch.kmax == 1)) {
+        std::vector<PlanItem> plan;
+        plan_none(q, s->n, plan);
+        rc = execute_plan(s, plan);
+    } else if (s->fusion == QSIM_FUSE_MLP && s->cost.loaded()) {
+        // the chosen plan, regenerated item by item and launched as it forms
+        size_t idx = 0;
+        rc = plan_greedy_each(
+            q, s->n, ch.kmax,
+            [&](PlanItem &it) {
+                const bool fuse = idx < ch.fuse.size() && ch.fuse[idx];
+                ++idx;
+                if (!it.fused) return execute_item(s, it);
+                if (fuse) {
+                    block_matrix(q, it);
+                    return execute_item(s, it);
+                }
+                for (int gi : it.members)
+                    if (const int r = execute_item(s, single_item(q, s->n, gi))) return r;
+                return 0;
+            },
+            kMaxDiagQubits, false);
+    } else {
+        // greedy: each block is launched as soon as it is formed, so the
+        // host's planning of the next blocks overlaps the device's work
+        rc = plan_greedy_each(s->queue, s->n, block_kmax(s), [s](PlanItem &it) { return execute_item(s, it); });
+    }
     s->queue.clear();
     return rc;
 }
@@ -246,7 +284,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     qsim_opts o{};
     if (opts) o = *opts;
     if (o.fusion < QSIM_FUSE_NONE || o.fusion > QSIM_FUSE_MLP) return QSIM_EINVAL;
-    if (o.kmax == 0) o.kmax = 5;
+    if (o.kmax == 0) o.kmax = 6;
     if (o.kmax < 1 || o.kmax > 6) return QSIM_EINVAL;
     qsim *s = new (std::nothrow) qsim();
     if (!s) return QSIM_ENOMEM;
@@ -262,7 +300,8 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->tc_enabled = o.no_tensor_cores == 0;
     s->norm_tracking = o.no_norm_tracking == 0;
     s->c128_df = o.c128_double_float != 0;
-    if (const char *v = getenv("QSIM_TC_KERNEL")) s->tc_variant = (v[0] == 'w') ? 1 : (v[0] == 'd') ? 0 : 2;
+    if (const char *v = getenv("QSIM_TC_KERNEL"))
+        s->tc_variant = (v[0] == 'w') ? 1 : (v[0] == 'd') ? 0 : (v[0] == 's') ? 2 : 3;
     if (const char *v = getenv("QSIM_TC_STREAMING")) s->tc_streaming = atoi(v);
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
@@ -628,7 +667,7 @@ int sim_set_cost_model(qsim *s, const float *params, int count, int hidden) {
         s->cost = CostModel{};
         return QSIM_OK;
     }
-    if (!params || hidden < 1 || hidden > 1024) return set_err(s, QSIM_EINVAL, "bad cost model");
+    if (!params || hidden < 1 || hidden > kMaxHidden) return set_err(s, QSIM_EINVAL, "bad cost model");
     const long need = (long)hidden * kFeatures + hidden + (long)hidden * hidden + hidden + hidden + 1;
     if (count != need) return set_err(s, QSIM_EINVAL, "cost model size does not match hidden width");
     for (int i = 0; i < count; ++i)

@@ -930,6 +930,7 @@ int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
     } else {
         for (int j = 0; j < 5; ++j) q5[j] = qubits[j];
     }
+    if (s->tc_variant == 3) return launch_block_tmem(s, q5, 5, U);
     const int nsplit = s->tc_terms == 5 ? 3 : 2;
     std::vector<unsigned char> rec;
     TcArgs a{};

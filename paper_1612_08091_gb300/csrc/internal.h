@@ -6,6 +6,7 @@
 
 #include <complex>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "../../include/qsim.h"
@@ -44,10 +45,12 @@ struct PlanItem {
     double amp_updates = 0; // credited to the original gates
     int ngates = 0;
     std::vector<int> members;  // queue indices of the gates it executes, in order
+    double host_ms = 0;     // host time spent building its matrix (profiling)
 };
 
 // The learned cost model used by the planner (host inference).
 constexpr int kFeatures = 16;
+constexpr int kMaxHidden = 1024;  // widest cost-model layer
 struct CostModel {
     int hidden = 0;
     std::vector<float> p;  // W1[H][16], b1[H], W2[H][H], b2[H], w3[H], b3
@@ -76,7 +79,8 @@ struct qsim {
     int tc_terms = 3;
     bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
     bool c128_df = false;       // complex128 one-qubit gates in double-float arithmetic
-    int tc_variant = 2;         // 0: k_block_tc<2>, 1: k_block_tc_ws (warp-specialised, TMA-fed), 2: k_block_tc<1>
+    int tc_variant = 3;         // 4-5-qubit blocks: 3 k_block_tmem<5> (state operand in tensor memory);
+                                // 0 k_block_tc<2>, 1 k_block_tc_ws, 2 k_block_tc<1> (state operand in shared memory)
     int tc_streaming = 0;       // streaming (evict-first) cache hints on the block kernel's loads and stores
     uint64_t tc_passes = 0;
     int tc_prev_grid = 0;
@@ -86,7 +90,7 @@ struct qsim {
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    struct Pending { int cls; size_t ev; double bytes; long feat; };
+    struct Pending { int cls; size_t ev; double bytes; long feat; float host_ms; };
     bool record_items = false;
     std::vector<float> pending_feats;  // features of pending launches (record_items)
     std::vector<float> item_feats;     // harvested: kFeatures floats per launch
@@ -147,8 +151,9 @@ int check_device_errors(qsim *s);
 // Fused tensor-core block (fused_kernel.cu).  Returns QSIM_ENOTSUP when the
 // block cannot run on the tensor-core kernel (caller falls back).
 int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m);
-// 6-qubit block (complex64, tensor cores, n >= 13); QSIM_ENOTSUP otherwise
-int launch_block_tc6(qsim *s, const int *qubits, const cd *m);
+// 5- or 6-qubit block with the state operand in tensor memory (complex64,
+// tensor cores, n >= k + 7); QSIM_ENOTSUP otherwise
+int launch_block_tmem(qsim *s, const int *qubits, int k, const cd *m);
 
 // Reductions and measurement (reduce_kernels.cu) ----------------------------
 int run_probs_all(qsim *s, double *p1, double *norm2);
@@ -160,13 +165,32 @@ int run_measure_all(qsim *s, double u, uint64_t *outcome);
 
 // Planner (planner.cpp) -------------------------------------------------------
 void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out);
-// diag_k: widest diagonal block (0 disables diagonal blocks)
+// diag_k: widest diagonal block (0 disables diagonal blocks); matrices:
+// build each fused block's matrix or diagonal table (false: members and
+// qubits only, for comparing plans)
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out,
-                 int diag_k = kMaxDiagQubits);
+                 int diag_k = kMaxDiagQubits, bool matrices = true);
+// The same plan handed to emit item by item as it is formed (so execution
+// overlaps planning); a non-zero return of emit stops planning and is returned.
+int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
+                     int diag_k = kMaxDiagQubits, bool matrices = true);
+// Fill it.m, the product of the member gates embedded in it.qubits (a dense
+// block), or it.dtab (a diagonal block).
+void block_matrix(const std::vector<GateRec> &q, PlanItem &it);
 // Features of one plan item (kFeatures floats).
 void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, float *f);
-// Learned planner: greedy blocks for several kmax, each block fused or left
-// as plain gates, whichever the cost model predicts faster; the plan with
-// the lowest predicted total wins.  *predicted_ms receives its prediction.
-void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, const CostModel &cm,
-              std::vector<PlanItem> &out, double *predicted_ms);
+// Learned planner: the greedy plans for kmax = 2..kmax_limit (without block
+// matrices), each block fused or left as plain gates, whichever the cost
+// model predicts cheaper, against all gates plain (kmax 1); the plan with the
+// lowest predicted total wins.  The choice is its kmax and, for each item of
+// plan_greedy(kmax) in order, whether to run it fused (1) or as its member
+// gates (0); plan_greedy_each regenerates the same items for execution.
+struct MlpChoice {
+    int kmax = 1;
+    std::vector<char> fuse;
+    double predicted_ms = 0;
+};
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, int kmax_limit, const CostModel &cm,
+              MlpChoice &choice);
+// Gate gi as a plan item of its own.
+PlanItem single_item(const std::vector<GateRec> &q, int n, int gi);

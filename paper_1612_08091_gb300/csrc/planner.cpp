@@ -17,7 +17,9 @@
 // FP64.  Gates on more than kmax qubits (e.g. a many-controlled Z) run alone
 // with their specialised plain kernel.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
+#include <functional>
 
 #include <cmath>
 
@@ -39,8 +41,10 @@ void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out)
 
 namespace {
 
-// Apply gate g to every column of the 2^k x 2^k matrix M (column-major view
-// of a k-qubit register whose bit j is qubit S[j]):  M <- G M.
+// Apply gate g to the 2^k x 2^k block matrix M (row-major, row/column bit j
+// = qubit S[j]) from the left: M <- G M.  Row-oriented, so the inner loops
+// run along contiguous rows: an X (with controls) swaps pairs of rows, a
+// diagonal gate scales rows, a dense gate mixes each group of 2^t rows.
 void apply_to_block(std::vector<cd> &M, int k, const int *S, const GateRec &g) {
     const int D = 1 << k;
     auto pos = [&](int qubit) {
@@ -48,31 +52,62 @@ void apply_to_block(std::vector<cd> &M, int k, const int *S, const GateRec &g) {
             if (S[j] == qubit) return j;
         return -1;
     };
-    int tpos[5];
-    for (int j = 0; j < g.t; ++j) tpos[j] = pos(g.targets[j]);
-    int cm = 0;
-    for (int c : g.controls) cm |= 1 << pos(c);
-    int tm = 0;
-    for (int j = 0; j < g.t; ++j) tm |= 1 << tpos[j];
+    int tm = 0, cm = 0;
+    int spread[32];  // row offset of target pattern r (bit j of r -> bit pos(targets[j]))
     const int T = 1 << g.t;
-    std::vector<cd> in(T), outv(T);
-    std::vector<int> idx(T);
-    for (int col = 0; col < D; ++col) {
+    int tbits[5];
+    for (int j = 0; j < g.t; ++j) {
+        tbits[j] = 1 << pos(g.targets[j]);
+        tm |= tbits[j];
+    }
+    for (int r = 0; r < T; ++r) {
+        spread[r] = 0;
+        for (int j = 0; j < g.t; ++j)
+            if ((r >> j) & 1) spread[r] |= tbits[j];
+    }
+    for (int c : g.controls) cm |= 1 << pos(c);
+    double *m = reinterpret_cast<double *>(M.data());  // interleaved (re, im)
+    const size_t row = 2 * (size_t)D;                  // doubles per row
+    if (g.kind == GK_X) {
+        for (int base = 0; base < D; ++base) {
+            if ((base & tm) != 0 || (base & cm) != cm) continue;
+            double *a = m + (size_t)base * row, *b = m + (size_t)(base | tm) * row;
+            for (size_t i = 0; i < row; ++i) std::swap(a[i], b[i]);
+        }
+        return;
+    }
+    if (g.diag) {
         for (int base = 0; base < D; ++base) {
             if ((base & tm) != 0 || (base & cm) != cm) continue;
             for (int r = 0; r < T; ++r) {
-                int i = base;
-                for (int j = 0; j < g.t; ++j)
-                    if ((r >> j) & 1) i |= 1 << tpos[j];
-                idx[r] = i;
-                in[r] = M[(size_t)i * D + col];
+                const double zr = g.m[(size_t)r * T + r].real(), zi = g.m[(size_t)r * T + r].imag();
+                double *a = m + (size_t)(base | spread[r]) * row;
+                for (int col = 0; col < D; ++col) {
+                    const double xr = a[2 * col], xi = a[2 * col + 1];
+                    a[2 * col] = zr * xr - zi * xi;
+                    a[2 * col + 1] = zr * xi + zi * xr;
+                }
             }
-            for (int r = 0; r < T; ++r) {
-                cd acc = 0;
-                for (int c = 0; c < T; ++c) acc += g.m[(size_t)r * T + c] * in[c];
-                outv[r] = acc;
+        }
+        return;
+    }
+    std::vector<double> in((size_t)T * row);
+    for (int base = 0; base < D; ++base) {
+        if ((base & tm) != 0 || (base & cm) != cm) continue;
+        for (int c = 0; c < T; ++c)
+            std::copy_n(m + (size_t)(base | spread[c]) * row, row, in.data() + (size_t)c * row);
+        for (int r = 0; r < T; ++r) {
+            double *out = m + (size_t)(base | spread[r]) * row;
+            std::fill_n(out, row, 0.0);
+            for (int c = 0; c < T; ++c) {
+                const double gr = g.m[(size_t)r * T + c].real(), gi = g.m[(size_t)r * T + c].imag();
+                if (gr == 0.0 && gi == 0.0) continue;
+                const double *x = in.data() + (size_t)c * row;
+                for (int col = 0; col < D; ++col) {
+                    out[2 * col] += gr * x[2 * col] - gi * x[2 * col + 1];
+                    out[2 * col + 1] += gr * x[2 * col + 1] + gi * x[2 * col];
+                }
             }
-            for (int r = 0; r < T; ++r) M[(size_t)idx[r] * D + col] = outv[r];
         }
     }
 }
@@ -110,10 +145,23 @@ std::vector<cd> diag_table(const std::vector<GateRec> &q, const std::vector<int>
     return d;
 }
 
-void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out, int diag_k) {
-    out.clear();
+void block_matrix(const std::vector<GateRec> &q, PlanItem &it) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (it.diag_block) {
+        it.dtab = diag_table(q, it.members, it.dmask);
+    } else {
+        const int D = 1 << it.k;
+        it.m.assign((size_t)D * D, cd(0.0, 0.0));
+        for (int i = 0; i < D; ++i) it.m[(size_t)i * D + i] = 1.0;
+        for (int gi : it.members) apply_to_block(it.m, it.k, it.qubits, q[gi]);
+    }
+    it.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
+                     int diag_k, bool matrices) {
     const size_t G = q.size();
-    if (G == 0) return;
+    if (G == 0) return 0;
     // per-wire gate lists in program order
     std::vector<std::vector<int>> wire(n);
     for (size_t i = 0; i < G; ++i)
@@ -188,8 +236,8 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
                 it.ngates = (int)dm.size();
                 it.members = dm;
                 for (int gi : dm) it.amp_updates += (double)(1ull << (n - (int)q[gi].controls.size()));
-                it.dtab = diag_table(q, dm, Sd);
-                out.push_back(std::move(it));
+                if (matrices) block_matrix(q, it);
+                if (const int rc = emit(it)) return rc;
                 continue;
             }
             for (auto r = dm.rbegin(); r != dm.rend(); ++r) untake(*r);
@@ -202,7 +250,7 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
             it.ngates = 1;
             it.members.push_back(seed);
             take(seed);
-            out.push_back(std::move(it));
+            if (const int rc = emit(it)) return rc;
             continue;
         }
         std::vector<int> members;
@@ -259,13 +307,23 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
             it.k = 0;
             for (int b = 0; b < n; ++b)
                 if ((S >> b) & 1ull) it.qubits[it.k++] = b;
-            const int D = 1 << it.k;
-            it.m.assign((size_t)D * D, cd(0.0, 0.0));
-            for (int i = 0; i < D; ++i) it.m[(size_t)i * D + i] = 1.0;
-            for (int gi : members) apply_to_block(it.m, it.k, it.qubits, q[gi]);
+            if (matrices) block_matrix(q, it);
         }
-        out.push_back(std::move(it));
+        if (const int rc = emit(it)) return rc;
     }
+    return 0;
+}
+
+void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out, int diag_k,
+                 bool matrices) {
+    out.clear();
+    plan_greedy_each(
+        q, n, kmax,
+        [&](PlanItem &it) {
+            out.push_back(std::move(it));
+            return 0;
+        },
+        diag_k, matrices);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,10 +376,10 @@ void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int
 }
 
 float CostModel::predict(const float *x) const {
-    const int H = hidden;
+    const int H = hidden;  // <= kMaxHidden (checked when the model is loaded)
     const float *W1 = p.data(), *b1 = W1 + (size_t)H * kFeatures, *W2 = b1 + H, *b2 = W2 + (size_t)H * H,
                 *w3 = b2 + H, *b3 = w3 + H;
-    std::vector<float> h1(H), h2(H);
+    float h1[kMaxHidden], h2[kMaxHidden];
     for (int j = 0; j < H; ++j) {
         float a = b1[j];
         for (int i = 0; i < kFeatures; ++i) a += W1[(size_t)j * kFeatures + i] * x[i];
@@ -337,51 +395,54 @@ float CostModel::predict(const float *x) const {
     return y;
 }
 
-void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, const CostModel &cm,
-              std::vector<PlanItem> &out, double *predicted_ms) {
+PlanItem single_item(const std::vector<GateRec> &q, int n, int gi) {
+    PlanItem it;
+    it.fused = false;
+    it.gate = gi;
+    it.ngates = 1;
+    it.members.push_back(gi);
+    it.amp_updates = (double)(1ull << (n - (int)q[gi].controls.size()));
+    return it;
+}
+
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, int kmax_limit, const CostModel &cm,
+              MlpChoice &choice) {
     auto cost = [&](const PlanItem &it) {
         float f[kFeatures];
         item_features(it, q, n, prec, tc_enabled, f);
         return std::exp((double)cm.predict(f));
     };
-    auto single = [&](int gi) {
-        PlanItem it;
-        it.fused = false;
-        it.gate = gi;
-        it.ngates = 1;
-        it.members.push_back(gi);
-        it.amp_updates = (double)(1ull << (n - (int)q[gi].controls.size()));
-        return it;
-    };
-    double best = 1e300;
-    for (int kmax = 1; kmax <= 5; ++kmax) {
-        std::vector<PlanItem> blocks, plan;
-        if (kmax == 1)
-            plan_none(q, n, blocks);
-        else
-            plan_greedy(q, n, kmax, blocks);
+    // every gate's cost as a plain launch, predicted once
+    std::vector<double> single(q.size());
+    double total_single = 0.0;
+    for (size_t gi = 0; gi < q.size(); ++gi) {
+        single[gi] = cost(single_item(q, n, (int)gi));
+        total_single += single[gi];
+    }
+    choice.kmax = 1;
+    choice.fuse.clear();
+    choice.predicted_ms = total_single;
+    for (int kmax = 2; kmax <= kmax_limit; ++kmax) {
+        std::vector<PlanItem> blocks;
+        plan_greedy(q, n, kmax, blocks, kMaxDiagQubits, false);
+        std::vector<char> fuse(blocks.size(), 0);
         double total = 0.0;
-        for (PlanItem &b : blocks) {
-            const double cf = cost(b);
+        for (size_t i = 0; i < blocks.size(); ++i) {
+            const PlanItem &b = blocks[i];
+            double cs = 0.0;
+            for (int gi : b.members) cs += single[gi];
             if (!b.fused) {
-                total += cf;
-                plan.push_back(std::move(b));
+                total += cs;
                 continue;
             }
-            double cs = 0.0;
-            for (int gi : b.members) cs += cost(single(gi));
-            if (cs < cf) {
-                total += cs;
-                for (int gi : b.members) plan.push_back(single(gi));
-            } else {
-                total += cf;
-                plan.push_back(std::move(b));
-            }
+            const double cf = cost(b);
+            fuse[i] = cf <= cs;
+            total += fuse[i] ? cf : cs;
         }
-        if (total < best) {
-            best = total;
-            out.swap(plan);
+        if (total < choice.predicted_ms) {
+            choice.predicted_ms = total;
+            choice.kmax = kmax;
+            choice.fuse.swap(fuse);
         }
     }
-    if (predicted_ms) *predicted_ms = best;
 }

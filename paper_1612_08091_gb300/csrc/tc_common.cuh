@@ -1,5 +1,5 @@
 // tc_common.cuh -- inline-PTX helpers shared by the tensor-core block
-// kernels (fused_kernel.cu: 5-qubit blocks, fused6_kernel.cu: 6-qubit
+// kernels (fused_kernel.cu: 5-qubit blocks, tmem_block_kernel.cu: 5- and 6-qubit
 // blocks): mbarriers with bounded waits, tcgen05 fences, shared-memory
 // matrix descriptors, MMA commit, tensor-memory loads and stores, and the
 // bf16 hi/lo split of an amplitude.

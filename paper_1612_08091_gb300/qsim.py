@@ -119,7 +119,7 @@ def _ints(seq):
 class Simulator:
     """An n-qubit register on the GPU behind the libqsim C ABI."""
 
-    def __init__(self, n, precision="c128", fusion="none", kmax=5, device=None, stream=None, torch_memory=True,
+    def __init__(self, n, precision="c128", fusion="none", kmax=6, device=None, stream=None, torch_memory=True,
                  tc_terms=3, tensor_cores=True, norm_tracking=True, c128_df=False):
         import torch
 
@@ -277,7 +277,7 @@ class Simulator:
         self._check(self.lib.sim_set_stream(self.h, stream.cuda_stream if hasattr(stream, "cuda_stream")
                                             else int(stream)), "sim_set_stream")
 
-    def set_fusion(self, mode, kmax=5):
+    def set_fusion(self, mode, kmax=6):
         self._check(self.lib.sim_set_fusion(self.h, _FUSE[mode], int(kmax)), "sim_set_fusion")
 
     def stats(self):

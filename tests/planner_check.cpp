@@ -1,0 +1,215 @@
+// Host-side checks of the fusion planner (paper_1612_08091_gb300/csrc/planner.cpp),
+// built and run by tests/test_planner_cpu.py without a GPU.
+//
+//  1. block_matrix: the fused block of random gates (dense on 1-3 targets,
+//     X, diagonal, with and without controls) equals the ordered product of
+//     the gates embedded element by element, computed here independently.
+//  2. plan_greedy on random circuits: every gate is executed exactly once;
+//     gates sharing a qubit keep their program order; a dense block spans at
+//     most kmax qubits and contains its members' qubits; a diagonal block
+//     holds only diagonal gates and its table is the diagonal of the product;
+//     plan_greedy_each hands out the same items as plan_greedy.
+#include <algorithm>
+#include <cstdio>
+#include <random>
+
+#include "../paper_1612_08091_gb300/csrc/internal.h"
+
+namespace {
+
+std::mt19937_64 rng(1612);
+std::uniform_real_distribution<double> unif(-1.0, 1.0);
+
+// kind 0 dense (1..3 targets), 1 X, 2 diagonal; targets and controls drawn from pool
+GateRec random_gate(const std::vector<int> &pool, int kind) {
+    std::vector<int> perm = pool;
+    std::shuffle(perm.begin(), perm.end(), rng);
+    GateRec g;
+    const int k = (int)pool.size();
+    g.t = kind == 0 ? 1 + (int)(rng() % (uint64_t)std::min(3, k)) : 1;
+    const int nc = std::min<int>((int)(rng() % 3), k - g.t);
+    for (int j = 0; j < g.t; ++j) {
+        g.targets[j] = perm[j];
+        g.tmask |= 1ull << perm[j];
+    }
+    for (int j = 0; j < nc; ++j) {
+        g.controls.push_back(perm[g.t + j]);
+        g.cmask |= 1ull << perm[g.t + j];
+    }
+    const int T = 1 << g.t;
+    g.m.assign((size_t)T * T, cd(0.0, 0.0));
+    if (kind == 1) {
+        g.kind = GK_X;
+        g.m[1] = g.m[2] = 1.0;
+    } else if (kind == 2) {
+        g.kind = GK_DIAG1;
+        g.diag = true;
+        for (int r = 0; r < T; ++r) g.m[(size_t)r * T + r] = std::polar(1.0, 3.0 * unif(rng));
+    } else {
+        g.kind = GK_DENSE;
+        for (auto &z : g.m) z = cd(unif(rng), unif(rng));
+    }
+    return g;
+}
+
+// the gate as a D x D matrix on the block qubits S (bit j of an index = S[j])
+std::vector<cd> embed(const GateRec &g, const std::vector<int> &S) {
+    const int k = (int)S.size(), D = 1 << k, T = 1 << g.t;
+    auto bit = [&](int x, int qubit) {
+        for (int j = 0; j < k; ++j)
+            if (S[j] == qubit) return (x >> j) & 1;
+        return -1;
+    };
+    std::vector<cd> G((size_t)D * D, cd(0.0, 0.0));
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            bool same = true;  // bits outside the targets agree
+            for (int j = 0; j < k; ++j) {
+                bool target = false;
+                for (int t = 0; t < g.t; ++t) target |= g.targets[t] == S[j];
+                if (!target && ((r >> j) & 1) != ((c >> j) & 1)) same = false;
+            }
+            if (!same) continue;
+            bool on = true;
+            for (int cq : g.controls) on = on && bit(c, cq) == 1;
+            if (!on) {
+                G[(size_t)r * D + c] = r == c ? 1.0 : 0.0;
+                continue;
+            }
+            int ri = 0, ci = 0;
+            for (int t = 0; t < g.t; ++t) {
+                ri |= bit(r, g.targets[t]) << t;
+                ci |= bit(c, g.targets[t]) << t;
+            }
+            G[(size_t)r * D + c] = g.m[(size_t)ri * T + ci];
+        }
+    return G;
+}
+
+std::vector<cd> matmul(const std::vector<cd> &A, const std::vector<cd> &B, int D) {
+    std::vector<cd> C((size_t)D * D, cd(0.0, 0.0));
+    for (int r = 0; r < D; ++r)
+        for (int m = 0; m < D; ++m)
+            for (int c = 0; c < D; ++c) C[(size_t)r * D + c] += A[(size_t)r * D + m] * B[(size_t)m * D + c];
+    return C;
+}
+
+int check_block_matrix() {
+    double worst = 0.0;
+    for (int trial = 0; trial < 300; ++trial) {
+        const int k = 2 + trial % 5, n = 10;
+        std::vector<int> all(n);
+        for (int i = 0; i < n; ++i) all[i] = i;
+        std::shuffle(all.begin(), all.end(), rng);
+        std::vector<int> S(all.begin(), all.begin() + k);
+        std::sort(S.begin(), S.end());
+        const int D = 1 << k;
+        std::vector<GateRec> q;
+        PlanItem it;
+        it.fused = true;
+        it.k = k;
+        for (int j = 0; j < k; ++j) it.qubits[j] = S[j];
+        std::vector<cd> ref((size_t)D * D, cd(0.0, 0.0));
+        for (int i = 0; i < D; ++i) ref[(size_t)i * D + i] = 1.0;
+        for (int gi = 0; gi < 6; ++gi) {
+            q.push_back(random_gate(S, (int)(rng() % 3)));
+            it.members.push_back(gi);
+            ref = matmul(embed(q.back(), S), ref, D);
+        }
+        block_matrix(q, it);
+        for (size_t i = 0; i < ref.size(); ++i) worst = std::max(worst, std::abs(it.m[i] - ref[i]));
+    }
+    printf("block_matrix: max |difference| %.3e over 300 blocks\n", worst);
+    return worst < 1e-12 ? 0 : 1;
+}
+
+int check_plans() {
+    int bad = 0;
+    for (int trial = 0; trial < 60; ++trial) {
+        const int n = 8 + trial % 9, kmax = 2 + trial % 5, G = 40 + (int)(rng() % 80);
+        std::vector<int> all(n);
+        for (int i = 0; i < n; ++i) all[i] = i;
+        std::vector<GateRec> q;
+        for (int i = 0; i < G; ++i) {
+            std::shuffle(all.begin(), all.end(), rng);
+            const int width = 1 + (int)(rng() % 4);
+            std::vector<int> pool(all.begin(), all.begin() + width);
+            q.push_back(random_gate(pool, (int)(rng() % 3)));
+        }
+        std::vector<PlanItem> plan;
+        plan_greedy(q, n, kmax, plan);
+        std::vector<PlanItem> streamed;
+        plan_greedy_each(q, n, kmax, [&](PlanItem &it) {
+            streamed.push_back(it);
+            return 0;
+        });
+        // executed order: items in order, members in order
+        std::vector<int> order, seen(G, 0);
+        for (size_t i = 0; i < plan.size(); ++i) {
+            const PlanItem &it = plan[i];
+            if (streamed.size() != plan.size() || streamed[i].members != it.members || streamed[i].k != it.k) ++bad;
+            uint64_t S = 0;
+            for (int j = 0; j < it.k; ++j) S |= 1ull << it.qubits[j];
+            for (int gi : it.members) {
+                order.push_back(gi);
+                seen[gi]++;
+                const uint64_t m = q[gi].tmask | q[gi].cmask;
+                if (it.fused && !it.diag_block && (m & ~S)) ++bad;
+                if (it.diag_block && (!q[gi].diag || (m & ~it.dmask))) ++bad;
+            }
+            if (it.fused && !it.diag_block) {
+                if (it.k > kmax || it.k != __builtin_popcountll(S)) ++bad;
+                std::vector<int> Sv(it.qubits, it.qubits + it.k);
+                const int D = 1 << it.k;
+                std::vector<cd> ref((size_t)D * D, cd(0.0, 0.0));
+                for (int d = 0; d < D; ++d) ref[(size_t)d * D + d] = 1.0;
+                for (int gi : it.members) ref = matmul(embed(q[gi], Sv), ref, D);
+                for (size_t e = 0; e < ref.size(); ++e)
+                    if (std::abs(it.m[e] - ref[e]) > 1e-12) {
+                        ++bad;
+                        break;
+                    }
+            }
+            if (it.diag_block) {
+                std::vector<int> Sv;
+                for (int b = 0; b < 64; ++b)
+                    if ((it.dmask >> b) & 1ull) Sv.push_back(b);
+                const int D = 1 << (int)Sv.size();
+                std::vector<cd> ref((size_t)D * D, cd(0.0, 0.0));
+                for (int d = 0; d < D; ++d) ref[(size_t)d * D + d] = 1.0;
+                for (int gi : it.members) ref = matmul(embed(q[gi], Sv), ref, D);
+                for (int d = 0; d < D; ++d)
+                    if (std::abs(it.dtab[d] - ref[(size_t)d * D + d]) > 1e-12) {
+                        ++bad;
+                        break;
+                    }
+            }
+        }
+        for (int gi = 0; gi < G; ++gi)
+            if (seen[gi] != 1) ++bad;
+        // program order on every shared qubit
+        std::vector<int> at(G);
+        for (size_t i = 0; i < order.size(); ++i) at[order[i]] = (int)i;
+        for (int a = 0; a < G; ++a)
+            for (int b = a + 1; b < G; ++b)
+                if (((q[a].tmask | q[a].cmask) & (q[b].tmask | q[b].cmask)) && at[a] > at[b]) {
+                    // commuting diagonal gates may be reordered inside one diagonal block
+                    bool both_diag_same_block = false;
+                    for (const PlanItem &it : plan)
+                        if (it.diag_block && std::count(it.members.begin(), it.members.end(), a) &&
+                            std::count(it.members.begin(), it.members.end(), b))
+                            both_diag_same_block = true;
+                    if (!both_diag_same_block) ++bad;
+                }
+    }
+    printf("plan_greedy: %d violations over 60 random circuits\n", bad);
+    return bad == 0 ? 0 : 1;
+}
+
+}  // namespace
+
+int main() {
+    const int a = check_block_matrix();
+    const int b = check_plans();
+    return a | b;
+}

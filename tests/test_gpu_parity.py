@@ -258,8 +258,8 @@ def test_grover_closed_form(qs, prec, fusion):
     check_state(got, want, prec)
 
 
-@pytest.mark.parametrize("prec,fusion,kmax", [("c128", "none", 5), ("c64", "greedy", 5), ("c64", "greedy", 4),
-                                              ("c64", "greedy", 2)])
+@pytest.mark.parametrize("prec,fusion,kmax", [("c128", "none", 5), ("c64", "greedy", 6), ("c64", "greedy", 5),
+                                              ("c64", "greedy", 4), ("c64", "greedy", 2)])
 def test_random_circuit_n20(qs, oracle_mod, prec, fusion, kmax):
     n = 20
     ops = cg.random_u3_brickwork(n, 10, seed=8091)

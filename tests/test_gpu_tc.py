@@ -63,8 +63,8 @@ def test_fused_block_placements(qs, oracle_mod, n, S, terms):
 def test_tc_matches_cuda_core_blocks(qs):
     n = 18
     ops = cg.random_u3_brickwork(n, 6, seed=5)
-    with qs.Simulator(n, precision="c64", fusion="greedy") as a, \
-            qs.Simulator(n, precision="c64", fusion="greedy", tensor_cores=False) as b:
+    with qs.Simulator(n, precision="c64", fusion="greedy", kmax=5) as a, \
+            qs.Simulator(n, precision="c64", fusion="greedy", kmax=5, tensor_cores=False) as b:
         a.set_profiling(True)
         a.run(ops)
         b.run(ops)
