@@ -98,6 +98,19 @@ struct TmArgs {
     uint64_t rdep[64];         // address bits of block row r
 };
 
+// 32-byte global accesses (one whole sector per thread): four adjacent
+// amplitudes as two float4 (the address is 32-byte aligned)
+__device__ __forceinline__ void ld_v8(const float2 *p, float4 &a, float4 &b) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+__device__ __forceinline__ void st_v8(float2 *p, const float4 &a, const float4 &b) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
 // D(tmem) (+)= A(tmem) * B(smem)^T, M = 128, K = 16
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
@@ -109,9 +122,13 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
         : "memory");
 }
 
-// PAIR: qubit 0 is in S, so rows r and r+1 (r even) are adjacent amplitudes
-// and move as one 16-byte access.
-template <int K, bool PAIR>
+// W: amplitudes per global access.  W = 2: qubit 0 is in S, so rows r and
+// r+1 (r even) are adjacent amplitudes and move as one 16-byte access.  W = 4:
+// qubits 0 and 1 are in S, rows 4j..4j+3 are adjacent and move as one
+// 32-byte access; the tile columns are then at least 4 amplitudes apart, and
+// narrower accesses would use half a sector per instruction.  W = 1: 8-byte
+// accesses, the columns being adjacent amplitudes.
+template <int K, int W>
 __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tmem(const TmArgs args) {
     using Sh = TmShape<K>;
     extern __shared__ unsigned char smem_raw[];
@@ -169,13 +186,18 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
         float4 v[Sh::kRows / 2];  // rows 2j, 2j+1 of this column: (re, im, re, im)
         auto load_tile = [&](uint64_t tt) {
             const float2 *p = args.psi + insert_zeros(tt, args.vspec) + coff;
+            if constexpr (W == 4) {
 #pragma unroll
-            for (int j = 0; j < Sh::kRows / 2; ++j) {
-                if (PAIR) {
-                    v[j] = *(const float4 *)(p + args.rdep[2 * j]);
-                } else {
-                    const float2 a = p[args.rdep[2 * j]], b = p[args.rdep[2 * j + 1]];
-                    v[j] = make_float4(a.x, a.y, b.x, b.y);
+                for (int j = 0; j < Sh::kRows / 4; ++j) ld_v8(p + args.rdep[4 * j], v[2 * j], v[2 * j + 1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < Sh::kRows / 2; ++j) {
+                    if constexpr (W == 2) {
+                        v[j] = *(const float4 *)(p + args.rdep[2 * j]);
+                    } else {
+                        const float2 a = p[args.rdep[2 * j]], b = p[args.rdep[2 * j + 1]];
+                        v[j] = make_float4(a.x, a.y, b.x, b.y);
+                    }
                 }
             }
         };
@@ -191,12 +213,19 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) {
                     const int r = chunk * 16 + q;
-                    if (PAIR) {
-                        *(float4 *)(p + args.rdep[r]) = make_float4(d[2 * q] * scale, d[2 * q + 1] * scale,
-                                                                     d[2 * q + 2] * scale, d[2 * q + 3] * scale);
+                    const float4 o = make_float4(d[2 * q] * scale, d[2 * q + 1] * scale, d[2 * q + 2] * scale,
+                                                 d[2 * q + 3] * scale);
+                    if constexpr (W == 4) {
+                        if (q % 4 == 0) {
+                            const float4 o2 = make_float4(d[2 * q + 4] * scale, d[2 * q + 5] * scale,
+                                                          d[2 * q + 6] * scale, d[2 * q + 7] * scale);
+                            st_v8(p + args.rdep[r], o, o2);
+                        }
+                    } else if constexpr (W == 2) {
+                        *(float4 *)(p + args.rdep[r]) = o;
                     } else {
-                        p[args.rdep[r]] = make_float2(d[2 * q] * scale, d[2 * q + 1] * scale);
-                        p[args.rdep[r + 1]] = make_float2(d[2 * q + 2] * scale, d[2 * q + 3] * scale);
+                        p[args.rdep[r]] = make_float2(o.x, o.y);
+                        p[args.rdep[r + 1]] = make_float2(o.z, o.w);
                     }
                 }
             }
@@ -335,7 +364,9 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
             if ((r >> j) & 1) d |= 1ull << qubits[j];
         a.rdep[r] = d;
     }
-    const bool pair = qubits[0] == 0;
+    // amplitudes per global access (see k_block_tmem)
+    const int W = (qubits[0] == 0 && qubits[1] == 1) ? 4 : (qubits[0] == 0 ? 2 : 1);
+    const int wi = W == 4 ? 2 : W - 1;
 
     std::vector<unsigned char> rec;
     build_operand(m, K, nsplit, rec);
@@ -343,11 +374,11 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
     int rc = stage_operand(s, rec.data(), rec.size(), &dev_rec);
     if (rc) return rc;
 
-    auto kernel = pair ? k_block_tmem<K, true> : k_block_tmem<K, false>;
+    auto kernel = W == 4 ? k_block_tmem<K, 4> : (W == 2 ? k_block_tmem<K, 2> : k_block_tmem<K, 1>);
     const int dev = s->device;
     if (dev < 0 || dev >= 64) return QSIM_ENOTSUP;
-    static int smem_for[2][64][4] = {{{0}}};  // [pair][device][nsplit]: dynamic shared memory to request
-    int &smem = smem_for[pair ? 1 : 0][dev][nsplit];
+    static int smem_for[3][64][4] = {{{0}}};  // [access width][device][nsplit]: dynamic shared memory to request
+    int &smem = smem_for[wi][dev][nsplit];
     if (!smem) {
         // At most kCtasPerSm CTAs per SM, as many as the tensor memory holds
         // (512 columns).  If registers and shared memory would let another
@@ -367,8 +398,8 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return cuda_err(s, e, "tmem block kernel attribute");
         if (getenv("QSIM_DEBUG"))
-            fprintf(stderr, "qsim: k_block_tmem<%d,%d> regs %d smem %d (registers allow %d CTAs/SM, cap %d)\n", K,
-                    pair ? 1 : 0, fa.numRegs, bytes, by_regs, cap);
+            fprintf(stderr, "qsim: k_block_tmem<%d,%d> regs %d smem %d (registers allow %d CTAs/SM, cap %d)\n", K, W,
+                    fa.numRegs, bytes, by_regs, cap);
         smem = bytes;
     }
     a.psi = (float2 *)s->state;
