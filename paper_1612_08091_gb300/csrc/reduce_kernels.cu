@@ -4,11 +4,14 @@
 // Measurement in the computational basis with collapse of the register is
 // the paper's Measure operation (ProjectQ paper, Sec. 4 listing 1; Appendix
 // A.1 teleportation; Appendix A.3 measure-and-reset).  The sums behind it
-// are accumulated in FP64: per-thread partial sums of |psi_i|^2 are formed in
-// the amplitude precision over short runs (8 terms for complex64), added in
-// FP64, reduced across the warp by shuffles and across blocks by a
-// fixed-order second stage, so every result is deterministic for a given
-// launch configuration.
+// are accumulated in FP64 where it carries precision: partial sums of
+// |psi_i|^2 are formed in the amplitude precision over short runs (8 to 32
+// terms for complex64, or a 1024-term tile reduced as a 5-level warp tree),
+// then added in FP64 and reduced across blocks by a fixed-order second stage,
+// so every result is deterministic for a given launch configuration.  FP64
+// arithmetic runs at about 1/58 of the FP32 rate on this part, so one FP64
+// add per amplitude would bound these passes below half the HBM bandwidth;
+// the complex64 relative error stays below about 2e-6.
 //
 // Expectation values <psi|P|psi> of Pauli strings P (Z-only strings in one
 // pass for all terms; strings with an X/Y part grouped by their X mask, one
@@ -68,17 +71,18 @@ __global__ void __launch_bounds__(kRedThreads) k_probs_tiles(const Amp *__restri
             for (int b = 0; b < 5; ++b)
                 if ((j >> b) & 1) Sb[b] += w;
         }
-        const double dS = (double)S;
-        const double T = warp_sum(dS);
+        // warp sums in the amplitude precision (a tree of 5 levels over
+        // the lanes' 32-term sums); each lane adds its qubit's in FP64
+        const double T = (double)warp_sum(S);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            const double a = warp_sum(((lane >> q) & 1) ? dS : 0.0);
-            if (lane == q) accA += a;
+            const R a = warp_sum(((lane >> q) & 1) ? S : (R)0);
+            if (lane == q) accA += (double)a;
         }
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
-            const double a = warp_sum((double)Sb[b]);
-            if (lane == 5 + b) accA += a;
+            const R a = warp_sum(Sb[b]);
+            if (lane == 5 + b) accA += (double)a;
         }
         const uint64_t base = tile << 10;
         if (lane >= 10 && lane < n && ((base >> lane) & 1ull)) accA += T;
@@ -336,14 +340,25 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_x(const Amp *__restrict_
 // ---------------------------------------------------------------------------
 // full-register sampling
 // ---------------------------------------------------------------------------
-// Chunk sums: chunk b = [b*len, (b+1)*len), summed in FP64.
+// Chunk sums: chunk b = [b*len, (b+1)*len), summed in FP64 over runs of 16
+// terms per thread formed in the amplitude precision (16 loads in flight).
 template <typename Amp>
 __global__ void __launch_bounds__(kRedThreads) k_chunk_sums(const Amp *__restrict__ psi, uint64_t len,
                                                             double *__restrict__ sums) {
+    typedef typename AmpTraits<Amp>::real R;
     __shared__ double sh[32];
     const Amp *p = psi + (uint64_t)blockIdx.x * len;
     double acc = 0.0;
-    for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) acc += (double)norm2(p[i]);
+    const uint64_t step = (uint64_t)blockDim.x * 16;
+    for (uint64_t i0 = threadIdx.x; i0 < len; i0 += step) {
+        R run = 0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint64_t i = i0 + (uint64_t)u * blockDim.x;
+            if (i < len) run += norm2(p[i]);
+        }
+        acc += (double)run;
+    }
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) sums[blockIdx.x] = acc;
 }
