@@ -185,6 +185,46 @@ def kernel_traffic(kernel, n):
     return rec["bytes_per_launch"] * 2.0 ** (n - rec["n"])
 
 
+def measure_ops(sim, n, terms, u, stream, peak, b, reps=3):
+    """CUDA-event time (median of reps, after one warm call) and HBM
+    bandwidth of each read or measurement on the current register.  Bytes
+    are algorithmic: what the operation must read and write, counted in
+    whole 32-byte sectors (DRAM's access granularity)."""
+    import torch
+
+    N = 2.0 ** n
+    # the half of the amplitudes with bit q set spans every 32-byte sector
+    # when q < log2(32 / b): then the least traffic is the whole state
+    def half(q):
+        return N * b if (1 << q) * b < 32 else N / 2 * b
+    ops = [
+        ("probs_all", lambda: sim.probs_all(), N * b, "P(q=1) for every q and the norm: one read"),
+        ("prob_q0", lambda: sim.prob(0), half(0), "P(q0=1): the amplitudes with bit 0 set (every sector)"),
+        ("prob_top", lambda: sim.prob(n - 1), half(n - 1), "P(q%d=1): reads the half with the top bit set" % (n - 1)),
+        ("expect_zz", lambda: sim.expect(terms), N * b, "sum_i Z_i Z_i+1 (%d terms): one read" % len(terms)),
+        ("measure_q0", lambda: sim.measure(0, u), 2 * N * b + half(0),
+         "measure qubit 0 and collapse: read all (sums), read the kept amplitudes (every sector), write all"),
+        ("measure_all", lambda: sim.measure_all(u), 2 * N * b,
+         "sample all qubits and collapse to the basis state: read all, write all"),
+    ]
+    out = {}
+    for name, fn, nbytes, what in ops:
+        fn()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        out[name] = {"ms": ms, "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak, "bytes": nbytes,
+                     "what": what}
+    return out
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -338,6 +378,12 @@ def run_ours(args):
                 "alg_bytes_per_launch": per_launch_bytes, "launches_per_step": dom["launches"] / args.steps,
                 "share_of_gate_time": dom["total_ms"] / step_ms_total if step_ms_total else None}
 
+    # the reads and measurements of the step, one at a time on the same
+    # register (outside the timed region): each against the HBM roofline
+    # with its algorithmic bytes
+    measurements = measure_ops(sim, n, terms, u, stream, peak, 8 if args.precision == "c64" else 16) \
+        if rank == 0 else None
+
     plain = plain_df = None
     if not args.no_plain and rank == 0 and args.plain_layers > 0:
         sim.close()
@@ -397,6 +443,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof,
             "kernel_times": kt,
+            "measurements": measurements,
             "plain_c128": plain,
             "plain_c128_double_float": plain_df,
             "cpu_baseline": cpu,

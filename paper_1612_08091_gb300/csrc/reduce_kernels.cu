@@ -11,7 +11,7 @@
 // so every result is deterministic for a given launch configuration.  FP64
 // arithmetic runs at about 1/58 of the FP32 rate on this part, so one FP64
 // add per amplitude would bound these passes below half the HBM bandwidth;
-// the complex64 relative error stays below about 2e-6.
+// the complex64 relative error stays below about 3e-6.
 //
 // Expectation values <psi|P|psi> of Pauli strings P (Z-only strings in one
 // pass for all terms; strings with an X/Y part grouped by their X mask, one
@@ -60,6 +60,8 @@ __global__ void __launch_bounds__(kRedThreads) k_probs_tiles(const Amp *__restri
     __shared__ double sh[kRedThreads / 32][2 * 32 + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double accA = 0.0, accB = 0.0, accN = 0.0;
+    R fA = 0, fB = 0, fN = 0;  // the last <= 16 tiles, in the amplitude precision
+    int pending = 0;
     for (uint64_t tile = (uint64_t)blockIdx.x * nw + warp; tile < ntiles; tile += (uint64_t)gridDim.x * nw) {
         const Amp *p = psi + (tile << 10) + lane;
         R S = 0, Sb[5] = {0, 0, 0, 0, 0};
@@ -72,23 +74,35 @@ __global__ void __launch_bounds__(kRedThreads) k_probs_tiles(const Amp *__restri
                 if ((j >> b) & 1) Sb[b] += w;
         }
         // warp sums in the amplitude precision (a tree of 5 levels over
-        // the lanes' 32-term sums); each lane adds its qubit's in FP64
-        const double T = (double)warp_sum(S);
+        // the lanes' 32-term sums); lane q collects qubit q (and q + 32)
+        const R T = warp_sum(S);
+        R mine = 0;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const R a = warp_sum(((lane >> q) & 1) ? S : (R)0);
-            if (lane == q) accA += (double)a;
+            if (lane == q) mine = a;
         }
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
             const R a = warp_sum(Sb[b]);
-            if (lane == 5 + b) accA += (double)a;
+            if (lane == 5 + b) mine = a;
         }
         const uint64_t base = tile << 10;
-        if (lane >= 10 && lane < n && ((base >> lane) & 1ull)) accA += T;
-        if (lane + 32 < n && ((base >> (lane + 32)) & 1ull)) accB += T;
-        accN += T;
+        if (lane >= 10 && lane < n && ((base >> lane) & 1ull)) mine = T;
+        fA += mine;
+        if (lane + 32 < n && ((base >> (lane + 32)) & 1ull)) fB += T;
+        fN += T;
+        if (++pending == 16) {  // FP64 beyond 16 tiles
+            accA += (double)fA;
+            accB += (double)fB;
+            accN += (double)fN;
+            fA = fB = fN = 0;
+            pending = 0;
+        }
     }
+    accA += (double)fA;
+    accB += (double)fB;
+    accN += (double)fN;
     sh[warp][1 + lane] = accA;
     sh[warp][33 + lane] = accB;
     if (lane == 0) sh[warp][0] = accN;
@@ -138,12 +152,23 @@ __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const Amp *__restric
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     double acc = 0.0;
-    while (g < ngroups) {
-        R run = 0;
-#pragma unroll 1
-        for (int r = 0; r < 8 && g < ngroups; ++r, g += stride) run += norm2(psi[insert_zeros(g, ins) | value]);
-        acc += (double)run;
+    R run = 0;  // up to 4 rounds in the amplitude precision, FP64 beyond
+    int rounds = 0;
+    for (; g < ngroups; g += 16 * stride) {
+        // the 16 indices first, then 16 loads in flight per thread
+        uint64_t idx[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) idx[r] = insert_zeros(g + (uint64_t)r * stride, ins) | value;
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+            if (g + (uint64_t)r * stride < ngroups) run += norm2(psi[idx[r]]);
+        if (++rounds == 4) {
+            acc += (double)run;
+            run = 0;
+            rounds = 0;
+        }
     }
+    acc += (double)run;
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -158,17 +183,81 @@ __global__ void __launch_bounds__(kRedThreads) k_split_sum(const Amp *__restrict
     const uint64_t bit = 1ull << q, lowmask = bit - 1ull;
     uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     double a0 = 0.0, a1 = 0.0;
-    while (g < npairs) {
-        R r0 = 0, r1 = 0;
-#pragma unroll 1
-        for (int r = 0; r < 8 && g < npairs; ++r, g += stride) {
-            const uint64_t i0 = ((g & ~lowmask) << 1) | (g & lowmask);
-            r0 += norm2(psi[i0]);
-            r1 += norm2(psi[i0 | bit]);
+    R r0 = 0, r1 = 0;  // up to 4 rounds in the amplitude precision, FP64 beyond
+    int rounds = 0;
+    for (; g < npairs; g += 8 * stride) {
+        // 16 loads in flight per thread
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint64_t gr = g + (uint64_t)r * stride;
+            if (gr < npairs) {
+                const uint64_t i0 = ((gr & ~lowmask) << 1) | (gr & lowmask);
+                r0 += norm2(psi[i0]);
+                r1 += norm2(psi[i0 | bit]);
+            }
         }
-        a0 += (double)r0;
-        a1 += (double)r1;
+        if (++rounds == 4) {
+            a0 += (double)r0;
+            a1 += (double)r1;
+            r0 = r1 = 0;
+            rounds = 0;
+        }
     }
+    a0 += (double)r0;
+    a1 += (double)r1;
+    a0 = block_sum(a0, sh);
+    a1 = block_sum(a1, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a0;
+        partials[2 * blockIdx.x + 1] = a1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one qubit's halves in tiles:  S0 = sum over bit q = 0, S1 = over bit q = 1
+// ---------------------------------------------------------------------------
+// Tiles of 1024 consecutive amplitudes as in k_probs_tiles (lane l reads
+// index tile*1024 + 32*j + l): bit q of an element is a lane bit (q < 5), a
+// run bit (q < 10) or a bit of the tile index.  With only_set and q >= 10,
+// only the tiles with bit q set are read (tile t' of ntiles = 2^(n-11) gets a
+// 1 inserted at bit q - 10): half the state.
+template <typename Amp>
+__global__ void __launch_bounds__(kRedThreads) k_bit_sums(const Amp *__restrict__ psi, int q, uint64_t ntiles,
+                                                          int only_set, double *__restrict__ partials) {
+    typedef typename AmpTraits<Amp>::real R;
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double a0 = 0.0, a1 = 0.0;
+    R f0 = 0, f1 = 0;  // the last <= 16 tiles, in the amplitude precision
+    int pending = 0;
+    const int tq = q - 10;
+    for (uint64_t t = (uint64_t)blockIdx.x * nw + warp; t < ntiles; t += (uint64_t)gridDim.x * nw) {
+        uint64_t tile = t;
+        if (only_set && tq >= 0) tile = ((t >> tq) << (tq + 1)) | (1ull << tq) | (t & ((1ull << tq) - 1ull));
+        const Amp *p = psi + (tile << 10) + lane;
+        R w[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) w[j] = norm2(p[j * 32]);
+        R s0 = 0, s1 = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int bit = q < 5 ? (lane >> q) & 1 : (q < 10 ? (j >> (q - 5)) & 1 : (int)((tile >> tq) & 1ull));
+            if (bit)
+                s1 += w[j];
+            else
+                s0 += w[j];
+        }
+        f0 += s0;
+        f1 += s1;
+        if (++pending == 16) {  // FP64 beyond 16 tiles
+            a0 += (double)f0;
+            a1 += (double)f1;
+            f0 = f1 = 0;
+            pending = 0;
+        }
+    }
+    a0 += (double)f0;
+    a1 += (double)f1;
     a0 = block_sum(a0, sh);
     a1 = block_sum(a1, sh);
     if (threadIdx.x == 0) {
@@ -189,11 +278,86 @@ __device__ __forceinline__ float2 scale_amp(float2 a, double, float shi, float s
     return make_float2(fmaf(a.x, shi, a.x * slo), fmaf(a.y, shi, a.y * slo));
 }
 
+// One qubit q kept at value b: amplitude pairs (2k, 2k+1) move as one
+// 16-byte (complex64) or two 16-byte (complex128) accesses; a pair that is
+// dropped entirely is written as zeros without being read.
+__device__ __forceinline__ void ld_pair(const float2 *p, float2 &a, float2 &b) {
+    const float4 v = *(const float4 *)p;
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void st_pair(float2 *p, float2 a, float2 b) { *(float4 *)p = make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ void ld_pair(const double2 *p, double2 &a, double2 &b) {
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void st_pair(double2 *p, double2 a, double2 b) {
+    p[0] = a;
+    p[1] = b;
+}
+
+template <typename Amp>
+__global__ void k_collapse_bit(Amp *__restrict__ psi, uint64_t npairs, int q, int b, double s, float shi,
+                               float slo) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    Amp zero;
+    zero.x = 0;
+    zero.y = 0;
+    uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    // 4 pairs per thread per round: the kept ones' loads go out together
+    for (; k < npairs; k += 4 * stride) {
+        Amp v0[4], v1[4];
+        bool keep[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint64_t kr = k + (uint64_t)r * stride;
+            const uint64_t i = 2 * kr;
+            keep[r] = kr < npairs && (q == 0 || (int)((i >> q) & 1ull) == b);
+            if (keep[r]) ld_pair(psi + i, v0[r], v1[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint64_t kr = k + (uint64_t)r * stride;
+            if (kr >= npairs) continue;
+            const uint64_t i = 2 * kr;
+            if (!keep[r]) {
+                st_pair(psi + i, zero, zero);
+            } else if (q == 0) {
+                st_pair(psi + i, b ? zero : scale_amp(v0[r], s, shi, slo), b ? scale_amp(v1[r], s, shi, slo) : zero);
+            } else {
+                st_pair(psi + i, scale_amp(v0[r], s, shi, slo), scale_amp(v1[r], s, shi, slo));
+            }
+        }
+    }
+}
+
 template <typename Amp>
 __global__ void k_collapse_mask(Amp *__restrict__ psi, uint64_t N, uint64_t mask, uint64_t value, double s,
                                 float shi, float slo) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    // 8 elements per thread per round: the kept ones' loads go out together
+    for (; i + 7 * stride < N; i += 8 * stride) {
+        Amp v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint64_t k = i + (uint64_t)r * stride;
+            if ((k & mask) == value) v[r] = psi[k];
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const uint64_t k = i + (uint64_t)r * stride;
+            Amp z;
+            if ((k & mask) == value) {
+                z = scale_amp(v[r], s, shi, slo);
+            } else {
+                z.x = 0;
+                z.y = 0;
+            }
+            psi[k] = z;
+        }
+    }
+    for (; i < N; i += stride) {
         if ((i & mask) == value) {
             psi[i] = scale_amp(psi[i], s, shi, slo);
         } else {
@@ -212,14 +376,28 @@ __global__ void k_collapse_mask(Amp *__restrict__ psi, uint64_t N, uint64_t mask
 // A warp owns tiles of 1024 amplitudes as in k_probs_tiles.  With j the
 // run index (bits 5..9) and l the lane (bits 0..4), each lane forms the
 // Walsh-Hadamard transform W^(m) = sum_j w_j (-1)^{popc(j & m)} of its 32
-// weights; a term then contributes c_k (-1)^{popc((tile|l) & z_k)} W^(m_k)
-// with m_k = bits 5..9 of z_k.  W^ is kept per warp in shared memory.
+// weights; a term then contributes c_k (-1)^{popc(l & zl_k)}
+// (-1)^{popc(tile & zh_k)} W^(m_k) with zl_k, m_k, zh_k = bits 0..4, 5..9
+// and 10.. of z_k.  W^ is kept per warp in shared memory.  Terms with the
+// same (zl, m) form a group whose tile-dependent signs fold into one
+// coefficient per tile, so the lanes' work scales with the groups (11 for a
+// nearest-neighbour ZZ chain), not with the terms.
+// Coefficients come in both precisions so that the complex64 kernel does
+// no FP64 arithmetic per term (FP64, conversions included, runs at 1/58 of
+// the FP32 rate here); tile indices and zh fit 32 bits (n <= 36).
 constexpr int kMaxZTerms = 96;
 struct ZTerms {
-    int nt;
-    double c[kMaxZTerms];
-    uint64_t z[kMaxZTerms];
+    int nt, ng;
+    double c[kMaxZTerms];   // terms, grouped: group g owns [first[g], first[g+1])
+    float cf[kMaxZTerms];   // the same, rounded to float
+    unsigned zh[kMaxZTerms];
+    int first[kMaxZTerms + 1];
+    int zl[kMaxZTerms], m[kMaxZTerms];
 };
+static_assert(sizeof(ZTerms) <= 4000, "kernel parameter size");
+
+__device__ __forceinline__ float zcoef(const ZTerms &T, int k, float) { return T.cf[k]; }
+__device__ __forceinline__ double zcoef(const ZTerms &T, int k, double) { return T.c[k]; }
 
 constexpr int kZThreads = 128;
 
@@ -231,6 +409,8 @@ __global__ void __launch_bounds__(kZThreads) k_expect_z_tiles(const Amp *__restr
     __shared__ double sh[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double acc = 0.0;
+    R facc = 0;  // the last <= 16 tiles, in the amplitude precision
+    int pending = 0;
     for (uint64_t tile = (uint64_t)blockIdx.x * nw + warp; tile < ntiles; tile += (uint64_t)gridDim.x * nw) {
         const Amp *p = psi + (tile << 10) + lane;
         R w[32];
@@ -251,19 +431,26 @@ __global__ void __launch_bounds__(kZThreads) k_expect_z_tiles(const Amp *__restr
 #pragma unroll
         for (int m = 0; m < 32; ++m) wh[warp][m][lane] = w[m];
         __syncwarp();
-        const uint64_t idx = (tile << 10) | (uint64_t)lane;
         R e = 0;
-        for (int k = 0; k < T.nt; ++k) {
-            const uint64_t z = T.z[k];
-            const int m = (int)((z >> 5) & 31u);
-            const int par = (__popcll(idx & z & ~0x3E0ull)) & 1;
-            const R v = wh[warp][m][lane];
-            const R c = (R)T.c[k];
-            e += par ? -c * v : c * v;
+        const unsigned t32 = (unsigned)tile;
+        for (int g = 0; g < T.ng; ++g) {
+            R c = 0;  // the group's coefficient for this tile (warp-uniform)
+            for (int k = T.first[g]; k < T.first[g + 1]; ++k) {
+                const R ck = zcoef(T, k, R(0));
+                c += (__popc(t32 & T.zh[k]) & 1) ? -ck : ck;
+            }
+            const R v = wh[warp][T.m[g]][lane];
+            e += (__popc(lane & T.zl[g]) & 1) ? -c * v : c * v;
         }
         __syncwarp();
-        acc += (double)e;
+        facc += e;
+        if (++pending == 16) {  // FP64 beyond 16 tiles
+            acc += (double)facc;
+            facc = 0;
+            pending = 0;
+        }
     }
+    acc += (double)facc;
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
@@ -275,7 +462,11 @@ __global__ void k_expect_z_small(const Amp *__restrict__ psi, uint64_t N, const 
     for (uint64_t i = threadIdx.x; i < N; i += blockDim.x) {
         const double w = (double)norm2(psi[i]);
         double f = 0.0;
-        for (int k = 0; k < T.nt; ++k) f += (__popcll(i & T.z[k]) & 1) ? -T.c[k] : T.c[k];
+        for (int g = 0; g < T.ng; ++g)
+            for (int k = T.first[g]; k < T.first[g + 1]; ++k) {
+                const uint64_t z = (uint64_t)T.zl[g] | ((uint64_t)T.m[g] << 5) | ((uint64_t)T.zh[k] << 10);
+                f += (__popcll(i & z) & 1) ? -T.c[k] : T.c[k];
+            }
         acc += w * f;
     }
     acc = block_sum(acc, sh);
@@ -365,16 +556,23 @@ __global__ void __launch_bounds__(kRedThreads) k_chunk_sums(const Amp *__restric
 
 // Inclusive FP64 scan of |psi_i|^2 over one chunk, starting from `carry`;
 // writes the first index whose running sum exceeds `target` (or ~0 if none)
-// and that amplitude.  One block of 1024 threads.
+// and that amplitude.  One block of 1024 threads; per step thread t owns the
+// run of kSearchRun consecutive amplitudes at off + t * kSearchRun: run sums
+// (FP64) are scanned across the block, and the one thread whose run crosses
+// the target scans its own amplitudes.
 struct SearchOut {
     unsigned long long index;
     double re, im;
     double total;
 };
 
+constexpr int kSearchThreads = 1024;
+constexpr int kSearchRun = 32;
+
 template <typename Amp>
-__global__ void __launch_bounds__(1024) k_chunk_search(const Amp *__restrict__ psi, uint64_t begin, uint64_t len,
-                                                       double carry, double target, SearchOut *out) {
+__global__ void __launch_bounds__(kSearchThreads) k_chunk_search(const Amp *__restrict__ psi, uint64_t begin,
+                                                                 uint64_t len, double carry, double target,
+                                                                 SearchOut *out) {
     __shared__ double wsum[32];
     __shared__ unsigned long long found;
     __shared__ double s_carry;
@@ -384,11 +582,14 @@ __global__ void __launch_bounds__(1024) k_chunk_search(const Amp *__restrict__ p
         s_carry = carry;
     }
     __syncthreads();
-    for (uint64_t off = 0; off < len; off += blockDim.x) {
-        const uint64_t i = begin + off + threadIdx.x;
-        const bool valid = off + threadIdx.x < len;
-        double w = valid ? (double)norm2(psi[i]) : 0.0;
-        // inclusive warp scan
+    const uint64_t step = (uint64_t)kSearchThreads * kSearchRun;
+    for (uint64_t off = 0; off < len; off += step) {
+        const uint64_t r0 = off + (uint64_t)threadIdx.x * kSearchRun;  // this thread's run, relative to begin
+        double run = 0.0;
+        for (int k = 0; k < kSearchRun; ++k)
+            if (r0 + k < len) run += (double)norm2(psi[begin + r0 + k]);
+        // inclusive scan of the run sums over the block
+        double w = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const double t = __shfl_up_sync(0xffffffffu, w, o);
@@ -406,8 +607,19 @@ __global__ void __launch_bounds__(1024) k_chunk_search(const Amp *__restrict__ p
             wsum[lane] = v;  // inclusive over warps
         }
         __syncthreads();
-        const double c = s_carry + (warp > 0 ? wsum[warp - 1] : 0.0) + w;
-        if (valid && c > target) atomicMin(&found, (unsigned long long)i);
+        const double before = s_carry + (warp > 0 ? wsum[warp - 1] : 0.0) + (w - run);  // sum ahead of this run
+        if (r0 < len && before + run > target) {
+            // the first crossing inside this run: the partial sums are formed
+            // in the order of `run`, so the last one equals it and crosses
+            double part = 0.0;
+            uint64_t hit = r0;
+            for (int k = 0; k < kSearchRun && r0 + k < len; ++k) {
+                part += (double)norm2(psi[begin + r0 + k]);
+                hit = r0 + k;
+                if (before + part > target) break;
+            }
+            atomicMin(&found, (unsigned long long)(begin + hit));
+        }
         __syncthreads();
         if (found != ~0ull) break;
         if (threadIdx.x == 0) s_carry += wsum[31];
@@ -522,8 +734,30 @@ int probs_all_t(qsim *s, double *p1, double *norm2_out) {
     return QSIM_OK;
 }
 
+// S0, S1 of qubit q by tiles (n >= 10); only_set: S1 alone, reading only
+// the tiles with bit q set where q >= 10.
+template <typename Amp>
+int bit_sums_t(qsim *s, int q, bool only_set, double *s0, double *s1) {
+    const int n = s->n;
+    const uint64_t ntiles = (1ull << (n - 10)) >> ((only_set && q >= 10) ? 1 : 0);
+    const unsigned grid = grid_for(ntiles, kRedThreads / 32, kReduceBlocks);
+    k_bit_sums<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, q, ntiles, only_set ? 1 : 0,
+                                                          ws_partials(s));
+    s->stats.launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(s, e, "bit sums launch");
+    double v[2];
+    int rc = finalize(s, grid, 2, v);
+    if (rc) return rc;
+    if (s0) *s0 = v[0];
+    *s1 = v[1];
+    return QSIM_OK;
+}
+
 template <typename Amp>
 int masked_sum_t(qsim *s, uint64_t mask, uint64_t value, double *out) {
+    if (s->n >= 10 && __builtin_popcountll(mask) == 1 && value == mask)
+        return bit_sums_t<Amp>(s, __builtin_ctzll(mask), true, nullptr, out);
     const InsertSpec ins = make_spec(mask);
     const uint64_t ngroups = 1ull << (s->n - ins.m);
     const unsigned grid = grid_for(ngroups, kRedThreads, kReduceBlocks);
@@ -536,6 +770,7 @@ int masked_sum_t(qsim *s, uint64_t mask, uint64_t value, double *out) {
 
 template <typename Amp>
 int split_sum_t(qsim *s, int q, double *s0, double *s1) {
+    if (s->n >= 10) return bit_sums_t<Amp>(s, q, false, s0, s1);
     const uint64_t npairs = 1ull << (s->n - 1);
     const unsigned grid = grid_for(npairs, kRedThreads, kReduceBlocks);
     k_split_sum<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, npairs, q, ws_partials(s));
@@ -555,6 +790,14 @@ int collapse_t(qsim *s, uint64_t mask, uint64_t value, double scale) {
     const uint64_t N = 1ull << s->n;
     const float shi = (float)scale;
     const float slo = (float)(scale - (double)shi);
+    if (s->n >= 1 && __builtin_popcountll(mask) == 1) {
+        const int q = __builtin_ctzll(mask);
+        const uint64_t npairs = N >> 1;
+        const unsigned grid = grid_for(npairs, 256, kSMs * 16);
+        k_collapse_bit<Amp><<<grid, 256, 0, s->stream>>>((Amp *)s->state, npairs, q, value ? 1 : 0, scale, shi, slo);
+        s->stats.launches++;
+        return cuda_err(s, cudaGetLastError(), "collapse launch");
+    }
     const unsigned grid = grid_for(N, 256, kSMs * 16);
     k_collapse_mask<Amp><<<grid, 256, 0, s->stream>>>((Amp *)s->state, N, mask, value, scale, shi, slo);
     s->stats.launches++;
@@ -573,10 +816,25 @@ int expect_t(qsim *s, const qsim_pauli *terms, int nterms, double *out) {
     for (size_t b0 = 0; b0 < zonly.size(); b0 += kMaxZTerms) {
         ZTerms T{};
         T.nt = (int)std::min<size_t>(kMaxZTerms, zonly.size() - b0);
+        // group the batch's terms by their bits inside a tile (0..9)
+        std::vector<int> ord(T.nt);
+        for (int k = 0; k < T.nt; ++k) ord[k] = zonly[b0 + k];
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int a, int b) { return (terms[a].zmask & 0x3FFull) < (terms[b].zmask & 0x3FFull); });
+        T.ng = 0;
         for (int k = 0; k < T.nt; ++k) {
-            T.c[k] = terms[zonly[b0 + k]].coeff;
-            T.z[k] = terms[zonly[b0 + k]].zmask;
+            const uint64_t z = terms[ord[k]].zmask;
+            if (k == 0 || (z & 0x3FFull) != (terms[ord[k - 1]].zmask & 0x3FFull)) {
+                T.first[T.ng] = k;
+                T.zl[T.ng] = (int)(z & 31u);
+                T.m[T.ng] = (int)((z >> 5) & 31u);
+                ++T.ng;
+            }
+            T.c[k] = terms[ord[k]].coeff;
+            T.cf[k] = (float)terms[ord[k]].coeff;
+            T.zh[k] = (unsigned)(z >> 10);
         }
+        T.first[T.ng] = T.nt;
         double v;
         if (n < 10) {
             k_expect_z_small<Amp><<<1, 256, 0, s->stream>>>((const Amp *)s->state, N, T, ws_result(s));
@@ -658,7 +916,7 @@ int measure_all_t(qsim *s, double u, uint64_t *outcome) {
     bool done = false;
     for (; b < nchunks && !done; ++b) {
         if (sums[b] > 0.0 && prefix + sums[b] > target) {
-            k_chunk_search<Amp><<<1, 1024, 0, s->stream>>>((const Amp *)s->state, (uint64_t)b * len, len, prefix,
+            k_chunk_search<Amp><<<1, kSearchThreads, 0, s->stream>>>((const Amp *)s->state, (uint64_t)b * len, len, prefix,
                                                            target, dout);
             s->stats.launches++;
             e = cudaGetLastError();
