@@ -16,11 +16,18 @@
 // (largest circuits first) until the batch is done; there is no waiting on
 // other CTAs.  A circuit of n <= m qubits (m = 12..14, tuned) lives in the
 // CTA's shared memory; a larger one lives in a per-CTA pair of global
-// buffers and is processed in cache-blocked tiles of 2^m amplitudes: a low
-// pass gathers each chunk through the previous layer's CNOT permutation and
-// applies the gates on qubits 0..m-1, a high pass (tiles made of runs of
-// 2^(m-h) amplitudes times the h = n-m top qubits) applies the gates on the
-// top qubits.  Amplitudes are complex64 in FP32 arithmetic; energies
+// buffers and is processed in chunks of 2^g amplitudes (g = min(m, 13)):
+//   pair pass: the ladder permutation of the previous layer maps the
+//     destination chunks hi and hi ^ (2^h - 1) (h = n - g) onto the same two
+//     source chunks S, S ^ 1 with S = hi ^ (hi << 1): an element at offset o
+//     of source chunk S ^ p lands in chunk hi if parity(o) == p, else in its
+//     partner, at offset prefix_xor(o).  Both source chunks are read whole
+//     (coalesced), scattered into the two destination chunks in shared
+//     memory, get the gates on qubits 0..g-1, and are written back whole;
+//   high pass: tiles made of runs of 2^(g-h) amplitudes times the h top
+//     qubits get the gates on the top qubits, in place.
+// The energy is read after one more pair pass that applies the last layer's
+// permutation.  Amplitudes are complex64 in FP32 arithmetic; energies
 // accumulate per thread in FP32 over a few terms and in FP64 beyond.
 #include <cuda_runtime.h>
 
@@ -50,44 +57,35 @@ struct VqeArgs {
     const long long *aoff;
     const double *angles;
     double *energies;
-    unsigned int *counter;
-    int count;
+    unsigned int *counter;  // this launch's queue
+    int begin, end;   // its circuits: order[begin..end)
     int m;            // qubits held in shared memory
+    int g;            // chunk bits of the global-memory path (two chunks fit in shared memory)
     float2 *gbuf;     // per-CTA global buffers (two of gstride amplitudes each)
     size_t gstride;
     double h;
 };
 
-struct Gate1 {
-    float2 u00, u01, u10, u11;
+// A layer's rotations factor as (prod_q RZ(phi_q)) (prod_q RY(theta_q)):
+// RZ and RY on one qubit keep their order, and gates on different qubits
+// commute.  RY(theta) = [[c, -s], [s, c]] (c, s = cos, sin theta/2) is real,
+// so on complex amplitudes it costs 4 FP32 operations per amplitude instead
+// of the 8 of a general 2x2; the RZ part is diagonal,
+//   prod_q RZ(phi_q) |i> = exp(i (sum_{q in i} phi_q - Phi/2)) |i>,
+// Phi = sum_q phi_q, and is applied as one complex factor per amplitude from
+// two small tables (low and high bits) while the amplitudes move anyway.
+struct Rot {
+    float c, s;
 };
 
-// U = RZ(phi) RY(theta):
-// [[c e^{-i phi/2}, -s e^{-i phi/2}], [s e^{i phi/2}, c e^{i phi/2}]]
-__device__ __forceinline__ Gate1 make_gate(double theta, double phi) {
-    float s, c, sp, cp;
-    sincosf((float)(0.5 * theta), &s, &c);
-    sincosf((float)(0.5 * phi), &sp, &cp);
-    Gate1 g;
-    g.u00 = make_float2(c * cp, -c * sp);
-    g.u01 = make_float2(-s * cp, s * sp);
-    g.u10 = make_float2(s * cp, s * sp);
-    g.u11 = make_float2(c * cp, c * sp);
-    return g;
-}
-
-__device__ __forceinline__ void apply_pair(float2 *x, unsigned i0, unsigned i1, const Gate1 &g) {
+__device__ __forceinline__ void apply_pair(float2 *x, unsigned i0, unsigned i1, const Rot &g) {
     const float2 a = x[i0], b = x[i1];
-    float2 na = cmul(g.u00, a);
-    na = cfma(g.u01, b, na);
-    float2 nb = cmul(g.u10, a);
-    nb = cfma(g.u11, b, nb);
-    x[i0] = na;
-    x[i1] = nb;
+    x[i0] = make_float2(g.c * a.x - g.s * b.x, g.c * a.y - g.s * b.y);
+    x[i1] = make_float2(g.s * a.x + g.c * b.x, g.s * a.y + g.c * b.y);
 }
 
-// Gate on bit `bit` of a 2^k-amplitude array in shared memory.
-__device__ __forceinline__ void gate_smem(float2 *x, int k, int bit, const Gate1 &g) {
+// Rotation on bit `bit` of a 2^k-amplitude array in shared memory.
+__device__ __forceinline__ void gate_smem(float2 *x, int k, int bit, const Rot &g) {
     const unsigned half = 1u << (k - 1);
     const unsigned lowmask = (1u << bit) - 1u;
     for (unsigned p = threadIdx.x; p < half; p += blockDim.x) {
@@ -98,6 +96,16 @@ __device__ __forceinline__ void gate_smem(float2 *x, int k, int bit, const Gate1
 }
 
 __device__ __forceinline__ unsigned ladder_src(unsigned y, unsigned mask) { return (y ^ (y << 1)) & mask; }
+
+// inverse of y -> y ^ (y << 1): bit k of the result is the XOR of bits 0..k
+__device__ __forceinline__ unsigned prefix_xor(unsigned x) {
+    x ^= x << 1;
+    x ^= x << 2;
+    x ^= x << 4;
+    x ^= x << 8;
+    x ^= x << 16;
+    return x;
+}
 
 // Gates on `nb` bits of a 2^k-amplitude array in shared memory, applied four
 // bits at a time in registers: each thread loads the 16 amplitudes of a group
@@ -112,7 +120,7 @@ __device__ __forceinline__ void cswap(int &a, int &b) {
     b = hi;
 }
 
-__device__ void gates_blocked(float2 *x, int k, const int *bit, const Gate1 *g, int nb, const Gate1 *ident) {
+__device__ void gates_blocked(float2 *x, int k, const int *bit, const Rot *g, int nb, const Rot *ident) {
     if (k < 4) {
         // fewer than four bits in the array: one pass per gate
         for (int j = 0; j < nb; ++j) gate_smem(x, k, bit[j], g[j]);
@@ -121,10 +129,10 @@ __device__ void gates_blocked(float2 *x, int k, const int *bit, const Gate1 *g, 
     for (int g0 = 0; g0 < nb; g0 += 4) {
         // the group's four bits (padded with identity gates on unused bits)
         int p0, p1, p2, p3;
-        const Gate1 *q0, *q1, *q2, *q3;
+        const Rot *q0, *q1, *q2, *q3;
         {
             int pos[4];
-            const Gate1 *gg[4];
+            const Rot *gg[4];
             unsigned used = 0;
             int cnt = 0;
 #pragma unroll
@@ -167,19 +175,15 @@ __device__ void gates_blocked(float2 *x, int k, const int *bit, const Gate1 *g, 
                 v[r] = x[base | ((r & 1) ? m0 : 0u) | ((r & 2) ? m1 : 0u) | ((r & 4) ? m2 : 0u) | ((r & 8) ? m3 : 0u)];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const Gate1 *G = j == 0 ? q0 : j == 1 ? q1 : j == 2 ? q2 : q3;
-                const float2 u00 = G->u00, u01 = G->u01, u10 = G->u10, u11 = G->u11;
+                const Rot *G = j == 0 ? q0 : j == 1 ? q1 : j == 2 ? q2 : q3;
+                const float c = G->c, sn = G->s;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     if ((r >> j) & 1) continue;
                     const int r1 = r | (1 << j);
                     const float2 a = v[r], bb = v[r1];
-                    float2 na = cmul(u00, a);
-                    na = cfma(u01, bb, na);
-                    float2 nb2 = cmul(u10, a);
-                    nb2 = cfma(u11, bb, nb2);
-                    v[r] = na;
-                    v[r1] = nb2;
+                    v[r] = make_float2(c * a.x - sn * bb.x, c * a.y - sn * bb.y);
+                    v[r1] = make_float2(sn * a.x + c * bb.x, sn * a.y + c * bb.y);
                 }
             }
 #pragma unroll
@@ -231,49 +235,85 @@ __device__ float x_chunk(const float2 *x, int k, int bit) {
     return acc;
 }
 
-template <int T>
-__global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
+// t[j] = extra * prod over the set bits i of j (i < kb) of ph[i]
+__device__ void build_phase_table(float2 *t, int kb, const float2 *ph, float2 extra) {
+    for (unsigned j = threadIdx.x; j < (1u << kb); j += blockDim.x) {
+        float2 z = extra;
+        for (int i = 0; i < kb; ++i)
+            if ((j >> i) & 1u) z = cmul(z, ph[i]);
+        t[j] = z;
+    }
+}
+
+// GLOBAL = false: circuits of n <= m qubits, each held in one CTA's shared
+// memory.  GLOBAL = true: larger circuits in per-CTA global buffers, two
+// CTAs per SM so that one CTA's loads, arithmetic and stores overlap the
+// other's.
+template <int T, bool GLOBAL>
+__global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A) {
     constexpr int kRegAmps = RegAmps<T>::value;
     extern __shared__ float2 sm[];
     __shared__ int s_idx;
     __shared__ double s_red[32];
-    __shared__ Gate1 s_gate[32];   // this layer's RZ RY per qubit; [31] = identity
-    __shared__ int s_bit[32];      // array bit of each gate in the current pass
-    if (threadIdx.x == 0) {
-        s_gate[31].u00 = make_float2(1.f, 0.f);
-        s_gate[31].u01 = make_float2(0.f, 0.f);
-        s_gate[31].u10 = make_float2(0.f, 0.f);
-        s_gate[31].u11 = make_float2(1.f, 0.f);
-    }
-    const Gate1 *ident = &s_gate[31];
+    __shared__ Rot s_rot[32];       // this layer's RY per qubit; [31] = identity
+    __shared__ float2 s_ph[32];     // e^{i phi_q}
+    __shared__ int s_bit[32];       // array bit of each rotation in the current pass
+    __shared__ float2 s_tlo[128];   // phases of index bits 0..6 (times e^{-i Phi/2})
+    __shared__ float2 s_thi[128];   // phases of the next bits of a chunk or register
+    __shared__ float2 s_ttop[256];  // phases of the top h qubits (global-memory path)
+    __shared__ float2 s_gph;        // e^{-i Phi/2}
+    if (threadIdx.x == 0) s_rot[31] = Rot{1.f, 0.f};
+    const Rot *ident = &s_rot[31];
+    // the layer's rotations, per-qubit phases and the global factor
+    auto layer_setup = [&](const double *al, int n) {
+        if (threadIdx.x < (unsigned)n) {
+            float sn, c, sp, cp;
+            sincosf((float)(0.5 * al[threadIdx.x]), &sn, &c);
+            sincosf((float)al[n + threadIdx.x], &sp, &cp);
+            s_rot[threadIdx.x] = Rot{c, sn};
+            s_ph[threadIdx.x] = make_float2(cp, sp);
+        }
+        if (threadIdx.x == 0) {
+            double Phi = 0.0;
+            for (int q = 0; q < n; ++q) Phi += al[n + q];
+            float sp, cp;
+            sincosf((float)(-0.5 * Phi), &sp, &cp);
+            s_gph = make_float2(cp, sp);
+        }
+        __syncthreads();
+    };
     for (;;) {
-        if (threadIdx.x == 0) s_idx = (int)atomicAdd(A.counter, 1u);
+        if (threadIdx.x == 0) s_idx = A.begin + (int)atomicAdd(A.counter, 1u);
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
-        if (idx >= A.count) break;
+        if (idx >= A.end) break;
         const int c = A.order[idx];
         const int n = A.nq[c], L = A.nl[c];
         const double *ang = A.angles + A.aoff[c];
         const unsigned N = 1u << n;
         double zz = 0.0, xx = 0.0;
-        if (n <= A.m) {
+        if constexpr (!GLOBAL) {
             // --- shared-memory resident circuit -------------------------------
             for (unsigned i = threadIdx.x; i < N; i += T) sm[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
             __syncthreads();
+            const int klo = n < 7 ? n : 7;
             for (int l = 0; l < L; ++l) {
-                if (threadIdx.x < (unsigned)n) {
-                    s_gate[threadIdx.x] = make_gate(ang[2 * l * n + threadIdx.x], ang[2 * l * n + n + threadIdx.x]);
-                    s_bit[threadIdx.x] = threadIdx.x;
-                }
-                __syncthreads();
-                gates_blocked(sm, n, s_bit, s_gate, n, ident);
-                // CNOT ladder as one permutation through registers
+                const double *al = ang + 2 * l * n;
+                if (threadIdx.x < (unsigned)n) s_bit[threadIdx.x] = threadIdx.x;
+                layer_setup(al, n);
+                build_phase_table(s_tlo, klo, s_ph, s_gph);
+                build_phase_table(s_thi, n - klo, s_ph + klo, make_float2(1.f, 0.f));
+                gates_blocked(sm, n, s_bit, s_rot, n, ident);  // ends with a barrier
+                // the RZ phases and the CNOT ladder as one pass through registers
                 float2 v[kRegAmps];
 #pragma unroll
                 for (int j = 0; j < kRegAmps; ++j) {
                     const unsigned y = threadIdx.x + (unsigned)j * T;
-                    if (y < N) v[j] = sm[ladder_src(y, N - 1)];
+                    if (y < N) {
+                        const unsigned x = ladder_src(y, N - 1);
+                        v[j] = cmul(sm[x], cmul(s_tlo[x & 127u], s_thi[x >> 7]));
+                    }
                 }
                 __syncthreads();
 #pragma unroll
@@ -286,83 +326,98 @@ __global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
             zz = (double)zz_chunk(sm, n, 0ull, n);
             for (int q = 0; q < n; ++q) xx += (double)x_chunk(sm, n, q);
         } else {
-            // --- global-memory circuit, cache-blocked tiles of 2^m --------------
-            // Each layer is two passes over the state in the per-CTA buffers:
-            //   low pass:  chunks of 2^m consecutive amplitudes; the chunk is
-            //              gathered through the previous layer's CNOT-ladder
-            //              permutation psi'[y] = psi[y ^ (y << 1)] from the
-            //              source buffer, gets the gates on qubits 0..m-1 in
-            //              shared memory and is written to the other buffer;
-            //   high pass: tiles of runs of 2^(m-h) amplitudes times the h top
-            //              qubits, in place, gates on qubits m..n-1.
-            // The last layer's permutation is applied by the energy passes'
-            // gathers.  Global loads are issued in batches of 8 per thread so
-            // their latencies overlap.
-            const int m = A.m, h = n - m, lowrun = m - h;  // lowrun >= 5 by construction
+            // --- global-memory circuit, chunks of 2^g ----------------------------
+            const int g = A.g, h = n - g, lowrun = g - h;  // h >= 1 and lowrun >= 0 (n <= 2g)
             float2 *src = A.gbuf + (size_t)blockIdx.x * 2 * A.gstride;
             float2 *dst = src + A.gstride;
-            const unsigned M = 1u << m, nchunks = 1u << h, mask = N - 1;
-            constexpr int kB = T >= 1024 ? 4 : 8;
+            const unsigned G = 1u << g, nchunks = 1u << h, hmask = nchunks - 1u, gmask = G - 1u;
+            constexpr int kL = 8;  // loads in flight per thread per round
             for (unsigned i = threadIdx.x; i < N; i += T) src[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
             __syncthreads();
             bool permuted = false;  // src holds the state before a pending ladder permutation
-            auto gather_chunk = [&](const float2 *from, unsigned ch) {
-                for (unsigned i0 = threadIdx.x; i0 < M; i0 += T * kB) {
-                    float2 v[kB];
+            // chunks a = pr and b = pr ^ hmask into sm[0..G) and sm[G..2G),
+            // through the pending permutation if any
+            auto load_pair = [&](const float2 *from, unsigned pr) {
+                const unsigned S = permuted ? ((pr ^ (pr << 1)) & hmask) : pr;
+                for (unsigned e0 = threadIdx.x; e0 < 2 * G; e0 += T * kL) {
+                    float2 v[kL];
 #pragma unroll
-                    for (int u = 0; u < kB; ++u) {
-                        const unsigned i = i0 + u * T;
-                        const unsigned y = (ch << m) | i;
-                        if (i < M) v[u] = from[permuted ? ladder_src(y, mask) : y];
+                    for (int u = 0; u < kL; ++u) {
+                        const unsigned e = e0 + u * T;  // e < G: source chunk S, else S ^ 1 (or b)
+                        const unsigned c = e < G ? S : (permuted ? S ^ 1u : pr ^ hmask);
+                        if (e < 2 * G) v[u] = from[((size_t)c << g) | (e & gmask)];
                     }
 #pragma unroll
-                    for (int u = 0; u < kB; ++u) {
-                        const unsigned i = i0 + u * T;
-                        if (i < M) sm[i] = v[u];
+                    for (int u = 0; u < kL; ++u) {
+                        const unsigned e = e0 + u * T;
+                        if (e >= 2 * G) continue;
+                        if (permuted) {
+                            const unsigned o = e & gmask, p = e >= G ? 1u : 0u;
+                            const unsigned to_b = ((unsigned)__popc(o) & 1u) ^ p;
+                            sm[(to_b ? G : 0u) + (prefix_xor(o) & gmask)] = v[u];
+                        } else {
+                            sm[e] = v[u];
+                        }
                     }
+                }
+                __syncthreads();
+            };
+            // chunks a, b back to global memory, with the phases of the
+            // chunk bits 0..g-1 applied if `phased`
+            auto store_pair = [&](float2 *to, unsigned pr, bool phased) {
+                const unsigned hb = pr ^ hmask;
+                for (unsigned e = threadIdx.x; e < 2 * G; e += T) {
+                    const unsigned o = e & gmask;
+                    float2 v = sm[e];
+                    if (phased) v = cmul(v, cmul(s_tlo[o & 127u], s_thi[o >> 7]));
+                    to[((size_t)(e < G ? pr : hb) << g) | o] = v;
                 }
                 __syncthreads();
             };
             auto tile_index = [&](unsigned t, unsigned e) {
                 const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
-                return lo | (t << lowrun) | (top << m);
+                return lo | (t << lowrun) | (top << g);
             };
-            auto gather_tile = [&](const float2 *from, unsigned t, bool through_perm) {
-                for (unsigned e0 = threadIdx.x; e0 < M; e0 += T * kB) {
-                    float2 v[kB];
+            auto load_tile = [&](const float2 *from, unsigned t) {
+                for (unsigned e0 = threadIdx.x; e0 < G; e0 += T * kL) {
+                    float2 v[kL];
 #pragma unroll
-                    for (int u = 0; u < kB; ++u) {
+                    for (int u = 0; u < kL; ++u) {
                         const unsigned e = e0 + u * T;
-                        const unsigned y = tile_index(t, e);
-                        if (e < M) v[u] = from[through_perm ? ladder_src(y, mask) : y];
+                        if (e < G) v[u] = from[tile_index(t, e)];
                     }
 #pragma unroll
-                    for (int u = 0; u < kB; ++u) {
+                    for (int u = 0; u < kL; ++u) {
                         const unsigned e = e0 + u * T;
-                        if (e < M) sm[e] = v[u];
+                        if (e < G) sm[e] = v[u];
                     }
                 }
                 __syncthreads();
             };
             for (int l = 0; l < L; ++l) {
                 const double *al = ang + 2 * l * n;
-                if (threadIdx.x < (unsigned)n) s_gate[threadIdx.x] = make_gate(al[threadIdx.x], al[n + threadIdx.x]);
-                if (threadIdx.x < (unsigned)m) s_bit[threadIdx.x] = threadIdx.x;
-                if (threadIdx.x < (unsigned)h) s_bit[m + threadIdx.x] = lowrun + threadIdx.x;
+                if (threadIdx.x < (unsigned)g) s_bit[threadIdx.x] = threadIdx.x;
+                if (threadIdx.x < (unsigned)h) s_bit[g + threadIdx.x] = lowrun + threadIdx.x;
+                layer_setup(al, n);
+                build_phase_table(s_tlo, 7, s_ph, s_gph);
+                build_phase_table(s_thi, g - 7, s_ph + 7, make_float2(1.f, 0.f));
+                build_phase_table(s_ttop, h, s_ph + g, make_float2(1.f, 0.f));
                 __syncthreads();
-                // low pass: src (through the pending permutation) -> dst
-                for (unsigned ch = 0; ch < nchunks; ++ch) {
-                    gather_chunk(src, ch);
-                    gates_blocked(sm, m, s_bit, s_gate, m, ident);
-                    float2 *g = dst + ((size_t)ch << m);
-                    for (unsigned i = threadIdx.x; i < M; i += T) g[i] = sm[i];
-                    __syncthreads();
+                // pair pass: src (through the pending permutation) -> dst, RY
+                // on qubits 0..g-1 over both chunks at once, their RZ phases
+                // on the way out
+                for (unsigned pr = 0; pr < nchunks / 2; ++pr) {
+                    load_pair(src, pr);
+                    gates_blocked(sm, g + 1, s_bit, s_rot, g, ident);
+                    store_pair(dst, pr, true);
                 }
-                // high pass on dst, in place
+                // high pass on dst, in place: RY on the top qubits, then
+                // their RZ phases on the way out
                 for (unsigned t = 0; t < nchunks; ++t) {
-                    gather_tile(dst, t, false);
-                    gates_blocked(sm, m, s_bit + m, s_gate + m, h, ident);
-                    for (unsigned e = threadIdx.x; e < M; e += T) dst[tile_index(t, e)] = sm[e];
+                    load_tile(dst, t);
+                    gates_blocked(sm, g, s_bit + g, s_rot + g, h, ident);
+                    for (unsigned e = threadIdx.x; e < G; e += T)
+                        dst[tile_index(t, e)] = cmul(sm[e], s_ttop[e >> lowrun]);
                     __syncthreads();
                 }
                 float2 *tmp = src;
@@ -370,17 +425,19 @@ __global__ void __launch_bounds__(T, 1) k_vqe_batch(const VqeArgs A) {
                 dst = tmp;
                 permuted = true;  // this layer's CNOT ladder is still to be applied
             }
-            // energy of the permuted state, read through the permutation
+            // the last permutation, with the ZZ terms and the X terms of
+            // qubits 0..g-1 read on the way; then the top qubits' X terms
             float zf = 0.f, xf = 0.f;
-            for (unsigned ch = 0; ch < nchunks; ++ch) {
-                gather_chunk(src, ch);
-                zf += zz_chunk(sm, m, (unsigned long long)ch << m, n);
-                for (int q = 0; q < m; ++q) xf += x_chunk(sm, m, q);
-                __syncthreads();
+            for (unsigned pr = 0; pr < nchunks / 2; ++pr) {
+                load_pair(src, pr);
+                zf += zz_chunk(sm, g, (unsigned long long)pr << g, n);
+                zf += zz_chunk(sm + G, g, (unsigned long long)(pr ^ hmask) << g, n);
+                for (int q = 0; q < g; ++q) xf += x_chunk(sm, g + 1, q);
+                store_pair(dst, pr, false);
             }
             for (unsigned t = 0; t < nchunks; ++t) {
-                gather_tile(src, t, permuted);
-                for (int q = m; q < n; ++q) xf += x_chunk(sm, m, lowrun + (q - m));
+                load_tile(dst, t);
+                for (int q = g; q < n; ++q) xf += x_chunk(sm, g, lowrun + (q - g));
                 __syncthreads();
             }
             zz = (double)zf;
@@ -435,13 +492,38 @@ int reg_amps(int threads) { return threads == 256 ? RegAmps<256>::value : thread
 
 typedef void (*VqeKernel)(const VqeArgs);
 VqeKernel kernel_for(int threads) {
-    return threads == 256 ? k_vqe_batch<256> : threads == 512 ? k_vqe_batch<512> : k_vqe_batch<1024>;
+    return threads == 256 ? k_vqe_batch<256, false> : threads == 512 ? k_vqe_batch<512, false>
+                                                                     : k_vqe_batch<1024, false>;
+}
+
+// The global-memory kernel: 256 threads, chunks of 2^12 amplitudes (a pair
+// of them is 64 KB of shared memory), two CTAs per SM (measured faster than
+// three, which force the registers down to 80 and spill).
+constexpr int kGlobalThreads = 256;
+constexpr int kGlobalBits = 12;
+constexpr size_t kGlobalSmem = (size_t)16 << kGlobalBits;
+
+// circuits with more than m qubits: a prefix of the order (sorted by size)
+int count_large(const qsim_batch *b, int m) {
+    int k = 0;
+    while (k < b->count && b->nq[b->order[k]] > m) ++k;
+    return k;
 }
 
 bool config_valid(const qsim_batch *b, int threads, int m) {
-    if ((1 << m) > reg_amps(threads) * threads) return false;  // in-place permutation through registers
-    if (b->nmax > m && (b->nmax - m) > m - 5) return false;  // top-qubit tiles need runs of >= 32
-    return true;
+    (void)b;
+    return (1 << m) <= reg_amps(threads) * threads;  // in-place permutation through registers
+}
+
+int occupancy_global(const qsim_batch *b, int *grid) {
+    VqeKernel k = k_vqe_batch<kGlobalThreads, true>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGlobalSmem);
+    if (e != cudaSuccess) return QSIM_ECUDA;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGlobalThreads, kGlobalSmem);
+    if (e != cudaSuccess || per_sm < 1) return QSIM_ENOTSUP;
+    *grid = std::min(b->sms * per_sm, b->max_grid);
+    return QSIM_OK;
 }
 
 int occupancy(const qsim_batch *b, int threads, int m, int *grid) {
@@ -462,6 +544,9 @@ int berr(qsim_batch *b, int code, const std::string &msg) {
 }
 
 int launch(qsim_batch *b, int threads, int m, int grid) {
+    const int large = count_large(b, m);
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned int), b->stream);
+    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
     VqeArgs a;
     a.order = b->d_order;
     a.nq = b->d_nq;
@@ -469,17 +554,31 @@ int launch(qsim_batch *b, int threads, int m, int grid) {
     a.aoff = b->d_aoff;
     a.angles = b->d_angles;
     a.energies = b->d_energies;
-    a.counter = b->d_counter;
-    a.count = b->count;
     a.m = m;
+    a.g = kGlobalBits;
     a.gbuf = b->d_gbuf;
     a.gstride = b->gstride;
     a.h = b->h;
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream);
-    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
-    kernel_for(threads)<<<grid, threads, (size_t)8 << m, b->stream>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    if (large > 0) {
+        // the larger circuits first, several CTAs per SM
+        int ggrid = 0;
+        const int rc = occupancy_global(b, &ggrid);
+        if (rc) return berr(b, rc, "occupancy query failed");
+        a.counter = b->d_counter;
+        a.begin = 0;
+        a.end = large;
+        k_vqe_batch<kGlobalThreads, true><<<ggrid, kGlobalThreads, kGlobalSmem, b->stream>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    }
+    if (large < b->count) {
+        a.counter = b->d_counter + 1;
+        a.begin = large;
+        a.end = b->count;
+        kernel_for(threads)<<<grid, threads, (size_t)8 << m, b->stream>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    }
     return QSIM_OK;
 }
 
@@ -559,13 +658,12 @@ int sim_batch_create(int count, const int *nqubits, const int *layers, double h,
         b->nmin = std::min(b->nmin, nqubits[i]);
     }
     b->nangles = off;
-    // largest (most work) first
+    // largest first: by qubits, then layers (so the circuits above any
+    // shared-memory threshold m are a prefix of the order)
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
-        const double wx = std::ldexp((double)(b->nl[x] + 1), b->nq[x]);
-        const double wy = std::ldexp((double)(b->nl[y] + 1), b->nq[y]);
-        return wx > wy;
+        return b->nq[x] != b->nq[y] ? b->nq[x] > b->nq[y] : b->nl[x] > b->nl[y];
     });
     cudaGetDevice(&b->device);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
