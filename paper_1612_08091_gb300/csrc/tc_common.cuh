@@ -1,6 +1,7 @@
 // tc_common.cuh -- inline-PTX helpers shared by the tensor-core block
 // kernels (fused_kernel.cu: 5-qubit blocks, tmem_block_kernel.cu: 5- and 6-qubit
-// blocks): mbarriers with bounded waits, tcgen05 fences, shared-memory
+// blocks) and the batched variational kernel (vqe_kernel.cu: bulk copies):
+// mbarriers with bounded waits, bulk copies, tcgen05 fences, shared-memory
 // matrix descriptors, MMA commit, tensor-memory loads and stores, and the
 // bf16 hi/lo split of an amplitude.
 #pragma once
@@ -49,15 +50,32 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// One bulk copy global -> shared completing on `bar` (which expects `bytes`).
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+// Arrive on `bar` (count 1) and add `bytes` to the transaction count its
+// current phase waits for.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+
+// Bulk copy global -> shared of `bytes` (16-byte aligned addresses, a
+// multiple of 16 bytes), completing its bytes on `bar`.
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+
+// One bulk copy global -> shared completing on `bar` (which expects `bytes`).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    mbar_expect_tx(bar, bytes);
+    bulk_copy(dst, src, bytes, bar);
+}
+
+// Order this thread's earlier generic-proxy accesses (to global memory, or
+// to this CTA's shared memory) before its later async-proxy (bulk copy)
+// accesses.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // 64-bit shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of
 // 128 B, 8-row groups 1024 B apart.

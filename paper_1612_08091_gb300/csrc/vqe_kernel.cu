@@ -42,8 +42,10 @@
 
 #include "../../include/qsim.h"
 #include "common.cuh"
+#include "tc_common.cuh"
 
 using namespace qsim_dev;
+using namespace qsim_tc;
 
 namespace {
 
@@ -58,6 +60,7 @@ struct VqeArgs {
     const double *angles;
     double *energies;
     unsigned int *counter;  // this launch's queue
+    unsigned int *err;      // error flag (a bounded wait gave up)
     int begin, end;   // its circuits: order[begin..end)
     int m;            // qubits held in shared memory
     int g;            // chunk bits of the global-memory path (two chunks fit in shared memory)
@@ -84,13 +87,14 @@ __device__ __forceinline__ void apply_pair(float2 *x, unsigned i0, unsigned i1, 
     x[i1] = make_float2(g.s * a.x + g.c * b.x, g.s * a.y + g.c * b.y);
 }
 
-// Rotation on bit `bit` of a 2^k-amplitude array in shared memory.
-__device__ __forceinline__ void gate_smem(float2 *x, int k, int bit, const Rot &g) {
+// Rotation pairing the elements i and i ^ mask of a 2^k-amplitude array in
+// shared memory (mask's lowest bit, the pivot, is 0 in i).
+__device__ __forceinline__ void gate_smem(float2 *x, int k, unsigned mask, const Rot &g) {
     const unsigned half = 1u << (k - 1);
-    const unsigned lowmask = (1u << bit) - 1u;
+    const unsigned lowmask = (mask & (0u - mask)) - 1u;
     for (unsigned p = threadIdx.x; p < half; p += blockDim.x) {
         const unsigned i0 = ((p & ~lowmask) << 1) | (p & lowmask);
-        apply_pair(x, i0, i0 | (1u << bit), g);
+        apply_pair(x, i0, i0 ^ mask, g);
     }
     __syncthreads();
 }
@@ -107,40 +111,52 @@ __device__ __forceinline__ unsigned prefix_xor(unsigned x) {
     return x;
 }
 
-// Gates on `nb` bits of a 2^k-amplitude array in shared memory, applied four
-// bits at a time in registers: each thread loads the 16 amplitudes of a group
-// that differ only in four of the bits, applies those bits' gates there and
-// stores them back, so a layer of k one-qubit gates costs ceil(k/4) passes
-// over shared memory instead of k.  bit[j] is the array bit of gate g[j];
-// a group of fewer than four bits is padded with identity gates on other
-// bits.
+// Rotations g[0..nb) on a 2^k-amplitude array in shared memory, applied four
+// at a time in registers: each thread loads the 16 amplitudes of a group,
+// applies the four rotations there and stores them back, so a layer of k
+// one-qubit rotations costs ceil(k/4) passes over shared memory instead of k.
+// Rotation j pairs the elements i and i ^ mask[j]: a single bit for an array
+// in index order, two adjacent bits for the source-ordered buffers of the
+// global-memory path.  The lowest bit of each mask (its pivot) must differ
+// between the masks; a group is a base with zeros at its pivots XOR any
+// subset of its masks.  A group of fewer than four rotations is padded with
+// identity rotations on other bits.
+//
+// logical_pairs: the array is a pair buffer of the global-memory path in
+// source order, and mask[j] = 3 << k_j stands for logical qubit k_j.  The
+// element of a pair whose logical bit k_j is 0 is the one whose bits 0..k_j
+// have even parity; within a group that parity is the base's, so the
+// rotation is applied with s -> -s where the base's parity is odd.  This
+// needs groups without identity padding (nb a multiple of 4).
 __device__ __forceinline__ void cswap(int &a, int &b) {
     const int lo = a < b ? a : b, hi = a < b ? b : a;
     a = lo;
     b = hi;
 }
 
-__device__ void gates_blocked(float2 *x, int k, const int *bit, const Rot *g, int nb, const Rot *ident) {
+__device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot *g, int nb, const Rot *ident,
+                              bool logical_pairs = false) {
     if (k < 4) {
         // fewer than four bits in the array: one pass per gate
-        for (int j = 0; j < nb; ++j) gate_smem(x, k, bit[j], g[j]);
+        for (int j = 0; j < nb; ++j) gate_smem(x, k, mask[j], g[j]);
         return;
     }
     for (int g0 = 0; g0 < nb; g0 += 4) {
         // the group's four bits (padded with identity gates on unused bits)
-        int p0, p1, p2, p3;
+        unsigned m0, m1, m2, m3;
         const Rot *q0, *q1, *q2, *q3;
+        int s0, s1, s2, s3;  // the pivots, sorted, for the zero insertion
         {
-            int pos[4];
+            unsigned ms[4];
             const Rot *gg[4];
-            unsigned used = 0;
+            unsigned used = 0;  // pivots taken
             int cnt = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (g0 + j < nb) {
-                    pos[j] = bit[g0 + j];
+                    ms[j] = mask[g0 + j];
                     gg[j] = &g[g0 + j];
-                    used |= 1u << pos[j];
+                    used |= ms[j] & (0u - ms[j]);
                     cnt = j + 1;
                 }
             int b = 0;
@@ -148,20 +164,19 @@ __device__ void gates_blocked(float2 *x, int k, const int *bit, const Rot *g, in
             for (int j = 0; j < 4; ++j)
                 if (j >= cnt) {
                     while ((used >> b) & 1u) ++b;
-                    pos[j] = b;
+                    ms[j] = 1u << b;
                     gg[j] = ident;
                     used |= 1u << b;
                 }
-            p0 = pos[0]; p1 = pos[1]; p2 = pos[2]; p3 = pos[3];
+            m0 = ms[0]; m1 = ms[1]; m2 = ms[2]; m3 = ms[3];
             q0 = gg[0]; q1 = gg[1]; q2 = gg[2]; q3 = gg[3];
+            s0 = __ffs(m0) - 1; s1 = __ffs(m1) - 1; s2 = __ffs(m2) - 1; s3 = __ffs(m3) - 1;
         }
-        int s0 = p0, s1 = p1, s2 = p2, s3 = p3;  // sorted copy for the zero insertion
         cswap(s0, s1);
         cswap(s2, s3);
         cswap(s0, s2);
         cswap(s1, s3);
         cswap(s1, s2);
-        const unsigned m0 = 1u << p0, m1 = 1u << p1, m2 = 1u << p2, m3 = 1u << p3;
         const unsigned ngroups = 1u << (k - 4);
         for (unsigned gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
             unsigned base = gi;
@@ -172,11 +187,14 @@ __device__ void gates_blocked(float2 *x, int k, const int *bit, const Rot *g, in
             float2 v[16];
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                v[r] = x[base | ((r & 1) ? m0 : 0u) | ((r & 2) ? m1 : 0u) | ((r & 4) ? m2 : 0u) | ((r & 8) ? m3 : 0u)];
+                v[r] = x[base ^ ((r & 1) ? m0 : 0u) ^ ((r & 2) ? m1 : 0u) ^ ((r & 4) ? m2 : 0u) ^ ((r & 8) ? m3 : 0u)];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const Rot *G = j == 0 ? q0 : j == 1 ? q1 : j == 2 ? q2 : q3;
-                const float c = G->c, sn = G->s;
+                const unsigned mj = j == 0 ? m0 : j == 1 ? m1 : j == 2 ? m2 : m3;
+                const float c = G->c;
+                float sn = G->s;
+                if (logical_pairs && (__popc(base & ((mj & (0u - mj)) * 2u - 1u)) & 1)) sn = -sn;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     if ((r >> j) & 1) continue;
@@ -188,7 +206,7 @@ __device__ void gates_blocked(float2 *x, int k, const int *bit, const Rot *g, in
             }
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                x[base | ((r & 1) ? m0 : 0u) | ((r & 2) ? m1 : 0u) | ((r & 4) ? m2 : 0u) | ((r & 8) ? m3 : 0u)] = v[r];
+                x[base ^ ((r & 1) ? m0 : 0u) ^ ((r & 2) ? m1 : 0u) ^ ((r & 4) ? m2 : 0u) ^ ((r & 8) ? m3 : 0u)] = v[r];
         }
         __syncthreads();
     }
@@ -249,6 +267,13 @@ __device__ void build_phase_table(float2 *t, int kb, const float2 *ph, float2 ex
 // memory.  GLOBAL = true: larger circuits in per-CTA global buffers, two
 // CTAs per SM so that one CTA's loads, arithmetic and stores overlap the
 // other's.
+// Order of the pair pass's 12 rotations, taken four at a time.  A group's
+// pivot bits are the same in all lanes' addresses at each access, so a group
+// holding qubits 0..3 (the bank bits of 8-byte elements) would be a 16-way
+// bank conflict; spread as {0,4,5,6} {1,7,8,9} {2,3,10,11} the conflicts are
+// 2-, 2- and 4-way.
+__constant__ int kPairOrder[12] = {0, 4, 5, 6, 1, 7, 8, 9, 2, 3, 10, 11};
+
 template <int T, bool GLOBAL>
 __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A) {
     constexpr int kRegAmps = RegAmps<T>::value;
@@ -256,13 +281,24 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
     __shared__ int s_idx;
     __shared__ double s_red[32];
     __shared__ Rot s_rot[32];       // this layer's RY per qubit; [31] = identity
+    __shared__ Rot s_rotp[32];      // the pair pass's rotations, in kPairOrder
     __shared__ float2 s_ph[32];     // e^{i phi_q}
-    __shared__ int s_bit[32];       // array bit of each rotation in the current pass
+    __shared__ unsigned s_mask[32]; // XOR mask of each rotation in the current pass
     __shared__ float2 s_tlo[128];   // phases of index bits 0..6 (times e^{-i Phi/2})
     __shared__ float2 s_thi[128];   // phases of the next bits of a chunk or register
     __shared__ float2 s_ttop[256];  // phases of the top h qubits (global-memory path)
     __shared__ float2 s_gph;        // e^{-i Phi/2}
-    if (threadIdx.x == 0) s_rot[31] = Rot{1.f, 0.f};
+    __shared__ __align__(8) uint64_t s_bar[1];  // bulk-copy completion (global-memory path)
+    __shared__ uint32_t s_phase;
+    if (threadIdx.x == 0) {
+        s_rot[31] = Rot{1.f, 0.f};
+        if (GLOBAL) {
+            mbar_init(s_bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            s_phase = 0;
+        }
+    }
+    __syncthreads();
     const Rot *ident = &s_rot[31];
     // the layer's rotations, per-qubit phases and the global factor
     auto layer_setup = [&](const double *al, int n) {
@@ -300,11 +336,11 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
             const int klo = n < 7 ? n : 7;
             for (int l = 0; l < L; ++l) {
                 const double *al = ang + 2 * l * n;
-                if (threadIdx.x < (unsigned)n) s_bit[threadIdx.x] = threadIdx.x;
+                if (threadIdx.x < (unsigned)n) s_mask[threadIdx.x] = 1u << threadIdx.x;
                 layer_setup(al, n);
                 build_phase_table(s_tlo, klo, s_ph, s_gph);
                 build_phase_table(s_thi, n - klo, s_ph + klo, make_float2(1.f, 0.f));
-                gates_blocked(sm, n, s_bit, s_rot, n, ident);  // ends with a barrier
+                gates_blocked(sm, n, s_mask, s_rot, n, ident);  // ends with a barrier
                 // the RZ phases and the CNOT ladder as one pass through registers
                 float2 v[kRegAmps];
 #pragma unroll
@@ -327,48 +363,66 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
             for (int q = 0; q < n; ++q) xx += (double)x_chunk(sm, n, q);
         } else {
             // --- global-memory circuit, chunks of 2^g ----------------------------
+            // Data arrive by bulk copies completing on an mbarrier (no
+            // register staging): a pair pass copies the two source chunks
+            // whole and works on them in source order, where logical qubit
+            // k < g pairs the elements p and p ^ (3 << k); the store reads
+            // each destination element at its source position.  Every wait
+            // is bounded; on time-out the CTA raises the error flag and
+            // stops.
             const int g = A.g, h = n - g, lowrun = g - h;  // h >= 1 and lowrun >= 0 (n <= 2g)
             float2 *src = A.gbuf + (size_t)blockIdx.x * 2 * A.gstride;
             float2 *dst = src + A.gstride;
             const unsigned G = 1u << g, nchunks = 1u << h, hmask = nchunks - 1u, gmask = G - 1u;
-            constexpr int kL = 8;  // loads in flight per thread per round
+            const unsigned run_bytes = 8u << lowrun;  // a high-pass tile is 2^h runs of 2^lowrun amplitudes
             for (unsigned i = threadIdx.x; i < N; i += T) src[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
             __syncthreads();
             bool permuted = false;  // src holds the state before a pending ladder permutation
-            // chunks a = pr and b = pr ^ hmask into sm[0..G) and sm[G..2G),
-            // through the pending permutation if any
-            auto load_pair = [&](const float2 *from, unsigned pr) {
-                const unsigned S = permuted ? ((pr ^ (pr << 1)) & hmask) : pr;
-                for (unsigned e0 = threadIdx.x; e0 < 2 * G; e0 += T * kL) {
-                    float2 v[kL];
-#pragma unroll
-                    for (int u = 0; u < kL; ++u) {
-                        const unsigned e = e0 + u * T;  // e < G: source chunk S, else S ^ 1 (or b)
-                        const unsigned c = e < G ? S : (permuted ? S ^ 1u : pr ^ hmask);
-                        if (e < 2 * G) v[u] = from[((size_t)c << g) | (e & gmask)];
-                    }
-#pragma unroll
-                    for (int u = 0; u < kL; ++u) {
-                        const unsigned e = e0 + u * T;
-                        if (e >= 2 * G) continue;
-                        if (permuted) {
-                            const unsigned o = e & gmask, p = e >= G ? 1u : 0u;
-                            const unsigned to_b = ((unsigned)__popc(o) & 1u) ^ p;
-                            sm[(to_b ? G : 0u) + (prefix_xor(o) & gmask)] = v[u];
-                        } else {
-                            sm[e] = v[u];
-                        }
-                    }
+            bool failed = false;
+            // wait for the current copy phase; uniform verdict over the CTA
+            auto wait_copies = [&]() {
+                bool ok = mbar_wait(s_bar, s_phase);
+                if (!ok) ok = mbar_wait(s_bar, s_phase);  // give copies in flight a second bound
+                __syncthreads();
+                if (threadIdx.x == 0) s_phase ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) atomicOr(A.err, 1u);
+                    return false;
                 }
+                return true;
+            };
+            // chunks pr and pr ^ hmask (through the pending permutation: the
+            // source chunks S and S ^ 1, S = pr ^ (pr << 1)) into sm[0..2G)
+            // every thread orders its generic stores to global memory and its
+            // shared-memory accesses before the bulk copies that follow
+            auto before_copies = [&]() {
+                fence_proxy_async_global();
+                fence_proxy_async_smem();
                 __syncthreads();
             };
-            // chunks a, b back to global memory, with the phases of the
-            // chunk bits 0..g-1 applied if `phased`
+            auto load_pair = [&](const float2 *from, unsigned pr) {
+                const unsigned S = permuted ? ((pr ^ (pr << 1)) & hmask) : pr;
+                const unsigned ca = S, cb = permuted ? S ^ 1u : pr ^ hmask;
+                before_copies();
+                if (threadIdx.x == 0) {
+                    mbar_expect_tx(s_bar, 16u * G);
+                    bulk_copy(sm, from + ((size_t)ca << g), 8u * G, s_bar);
+                    bulk_copy(sm + G, from + ((size_t)cb << g), 8u * G, s_bar);
+                }
+                return wait_copies();
+            };
+            // physical position in the pair buffer of logical element e
+            // (e < G: chunk pr, else chunk pr ^ hmask; offset e & gmask)
+            auto pair_pos = [&](unsigned e) {
+                if (!permuted) return e;
+                const unsigned gl = ((e ^ (e << 1)) & gmask);
+                return ((((unsigned)__popc(gl) & 1u) ^ (e >> g)) << g) | gl;
+            };
             auto store_pair = [&](float2 *to, unsigned pr, bool phased) {
                 const unsigned hb = pr ^ hmask;
                 for (unsigned e = threadIdx.x; e < 2 * G; e += T) {
                     const unsigned o = e & gmask;
-                    float2 v = sm[e];
+                    float2 v = sm[pair_pos(e)];
                     if (phased) v = cmul(v, cmul(s_tlo[o & 127u], s_thi[o >> 7]));
                     to[((size_t)(e < G ? pr : hb) << g) | o] = v;
                 }
@@ -378,44 +432,57 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                 const unsigned lo = e & ((1u << lowrun) - 1u), top = e >> lowrun;
                 return lo | (t << lowrun) | (top << g);
             };
+            // tile t: run `top` (2^lowrun amplitudes at t << lowrun | top << g)
+            // to sm[top << lowrun]
             auto load_tile = [&](const float2 *from, unsigned t) {
-                for (unsigned e0 = threadIdx.x; e0 < G; e0 += T * kL) {
-                    float2 v[kL];
-#pragma unroll
-                    for (int u = 0; u < kL; ++u) {
-                        const unsigned e = e0 + u * T;
-                        if (e < G) v[u] = from[tile_index(t, e)];
-                    }
-#pragma unroll
-                    for (int u = 0; u < kL; ++u) {
-                        const unsigned e = e0 + u * T;
-                        if (e < G) sm[e] = v[u];
-                    }
+                if (run_bytes < 16) {  // runs below the bulk-copy granule: plain loads
+                    for (unsigned e = threadIdx.x; e < G; e += T) sm[e] = from[tile_index(t, e)];
+                    __syncthreads();
+                    return true;
                 }
+                before_copies();
+                if (threadIdx.x == 0) mbar_expect_tx(s_bar, 8u * G);
                 __syncthreads();
+                for (unsigned top = threadIdx.x; top < nchunks; top += T) {
+                    bulk_copy(sm + (top << lowrun), from + ((size_t)t << lowrun) + ((size_t)top << g), run_bytes,
+                              s_bar);
+                }
+                return wait_copies();
             };
-            for (int l = 0; l < L; ++l) {
+            for (int l = 0; l < L && !failed; ++l) {
                 const double *al = ang + 2 * l * n;
-                if (threadIdx.x < (unsigned)g) s_bit[threadIdx.x] = threadIdx.x;
-                if (threadIdx.x < (unsigned)h) s_bit[g + threadIdx.x] = lowrun + threadIdx.x;
                 layer_setup(al, n);
                 build_phase_table(s_tlo, 7, s_ph, s_gph);
                 build_phase_table(s_thi, g - 7, s_ph + 7, make_float2(1.f, 0.f));
                 build_phase_table(s_ttop, h, s_ph + g, make_float2(1.f, 0.f));
+                // rotation masks of the pair pass (in the pair buffer's order),
+                // grouped as kPairOrder
+                if (threadIdx.x < (unsigned)g) {
+                    const int q = kPairOrder[threadIdx.x];
+                    s_mask[threadIdx.x] = (permuted ? 3u : 1u) << q;
+                    s_rotp[threadIdx.x] = s_rot[q];
+                }
+                if (threadIdx.x < (unsigned)h) s_mask[g + threadIdx.x] = 1u << (lowrun + threadIdx.x);
                 __syncthreads();
                 // pair pass: src (through the pending permutation) -> dst, RY
                 // on qubits 0..g-1 over both chunks at once, their RZ phases
                 // on the way out
-                for (unsigned pr = 0; pr < nchunks / 2; ++pr) {
-                    load_pair(src, pr);
-                    gates_blocked(sm, g + 1, s_bit, s_rot, g, ident);
+                for (unsigned pr = 0; pr < nchunks / 2 && !failed; ++pr) {
+                    if (!load_pair(src, pr)) {
+                        failed = true;
+                        break;
+                    }
+                    gates_blocked(sm, g + 1, s_mask, s_rotp, g, ident, permuted);
                     store_pair(dst, pr, true);
                 }
                 // high pass on dst, in place: RY on the top qubits, then
                 // their RZ phases on the way out
-                for (unsigned t = 0; t < nchunks; ++t) {
-                    load_tile(dst, t);
-                    gates_blocked(sm, g, s_bit + g, s_rot + g, h, ident);
+                for (unsigned t = 0; t < nchunks && !failed; ++t) {
+                    if (!load_tile(dst, t)) {
+                        failed = true;
+                        break;
+                    }
+                    gates_blocked(sm, g, s_mask + g, s_rot + g, h, ident);
                     for (unsigned e = threadIdx.x; e < G; e += T)
                         dst[tile_index(t, e)] = cmul(sm[e], s_ttop[e >> lowrun]);
                     __syncthreads();
@@ -428,20 +495,41 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
             // the last permutation, with the ZZ terms and the X terms of
             // qubits 0..g-1 read on the way; then the top qubits' X terms
             float zf = 0.f, xf = 0.f;
-            for (unsigned pr = 0; pr < nchunks / 2; ++pr) {
-                load_pair(src, pr);
-                zf += zz_chunk(sm, g, (unsigned long long)pr << g, n);
-                zf += zz_chunk(sm + G, g, (unsigned long long)(pr ^ hmask) << g, n);
-                for (int q = 0; q < g; ++q) xf += x_chunk(sm, g + 1, q);
+            for (unsigned pr = 0; pr < nchunks / 2 && !failed; ++pr) {
+                if (!load_pair(src, pr)) {
+                    failed = true;
+                    break;
+                }
+                const unsigned hb = pr ^ hmask;
+                for (unsigned e = threadIdx.x; e < 2 * G; e += T) {
+                    const unsigned long long gi = ((unsigned long long)(e < G ? pr : hb) << g) | (e & gmask);
+                    const float w = norm2(sm[pair_pos(e)]);
+                    zf += w * (float)((n - 1) - 2 * __popcll((gi ^ (gi >> 1)) & ((1ull << (n - 1)) - 1ull)));
+                }
+                for (int q = 0; q < g; ++q) {
+                    // logical pairs (e, e ^ 2^q) are the buffer pairs (p, p ^ (3 << q))
+                    // (single bits if no layer ran: the buffer is in logical order);
+                    // Re(conj(a) b) does not depend on which of the two is which
+                    const unsigned msk = (permuted ? 3u : 1u) << q, low = (1u << q) - 1u;
+                    for (unsigned u = threadIdx.x; u < G; u += T) {
+                        const unsigned p0 = ((u & ~low) << 1) | (u & low);
+                        const float2 a = sm[p0], b = sm[p0 ^ msk];
+                        xf += 2.f * (a.x * b.x + a.y * b.y);
+                    }
+                }
                 store_pair(dst, pr, false);
             }
-            for (unsigned t = 0; t < nchunks; ++t) {
-                load_tile(dst, t);
+            for (unsigned t = 0; t < nchunks && !failed; ++t) {
+                if (!load_tile(dst, t)) {
+                    failed = true;
+                    break;
+                }
                 for (int q = g; q < n; ++q) xf += x_chunk(sm, g, lowrun + (q - g));
                 __syncthreads();
             }
             zz = (double)zf;
             xx = (double)xf;
+            if (failed) break;  // the error flag is set; this CTA stops
         }
         const double zzs = block_sum_d(zz, s_red);
         const double xxs = block_sum_d(xx, s_red);
@@ -477,6 +565,7 @@ struct qsim_batch {
     int max_grid = 0;
     // pinned staging
     double *h_angles = nullptr, *h_energies = nullptr;
+    unsigned int *h_flag = nullptr;  // the device error flag after a run
     // tuned launch configuration and its graph
     int threads = 512, m = 13, grid = 0;
     cudaGraphExec_t graph = nullptr;
@@ -501,7 +590,9 @@ VqeKernel kernel_for(int threads) {
 // three, which force the registers down to 80 and spill).
 constexpr int kGlobalThreads = 256;
 constexpr int kGlobalBits = 12;
+static_assert(kGlobalBits == 12, "kPairOrder lists the 12 chunk qubits");
 constexpr size_t kGlobalSmem = (size_t)16 << kGlobalBits;
+static_assert(kGlobalBits % 4 == 0, "pair-pass rotation groups must not need identity padding");
 
 // circuits with more than m qubits: a prefix of the order (sorted by size)
 int count_large(const qsim_batch *b, int m) {
@@ -545,7 +636,8 @@ int berr(qsim_batch *b, int code, const std::string &msg) {
 
 int launch(qsim_batch *b, int threads, int m, int grid) {
     const int large = count_large(b, m);
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned int), b->stream);
+    // the two queues' counters and the error flag
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(unsigned int), b->stream);
     if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
     VqeArgs a;
     a.order = b->d_order;
@@ -554,6 +646,7 @@ int launch(qsim_batch *b, int threads, int m, int grid) {
     a.aoff = b->d_aoff;
     a.angles = b->d_angles;
     a.energies = b->d_energies;
+    a.err = b->d_counter + 2;
     a.m = m;
     a.g = kGlobalBits;
     a.gbuf = b->d_gbuf;
@@ -598,6 +691,7 @@ int build_graph(qsim_batch *b) {
     cudaMemcpyAsync(b->d_angles, b->h_angles, sizeof(double) * b->nangles, cudaMemcpyHostToDevice, b->stream);
     rc = launch(b, b->threads, b->m, grid);
     cudaMemcpyAsync(b->h_energies, b->d_energies, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->stream);
+    cudaMemcpyAsync(b->h_flag, b->d_counter + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream);
     e = cudaStreamEndCapture(b->stream, &g);
     if (rc) return rc;
     if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
@@ -711,7 +805,8 @@ int sim_batch_create(int count, const int *nqubits, const int *layers, double h,
     p += 256;
     b->d_gbuf = (float2 *)p;
     if (cudaMallocHost((void **)&b->h_angles, sizeof(double) * std::max<long long>(1, b->nangles)) != cudaSuccess ||
-        cudaMallocHost((void **)&b->h_energies, sizeof(double) * count) != cudaSuccess) {
+        cudaMallocHost((void **)&b->h_energies, sizeof(double) * count) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_flag, sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         sim_batch_destroy(b);
         return QSIM_ENOMEM;
@@ -747,6 +842,7 @@ int sim_batch_destroy(qsim_batch *b) {
     if (b->own_mem && b->mem) cudaFree(b->mem);
     if (b->h_angles) cudaFreeHost(b->h_angles);
     if (b->h_energies) cudaFreeHost(b->h_energies);
+    if (b->h_flag) cudaFreeHost(b->h_flag);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return QSIM_OK;
@@ -764,6 +860,7 @@ int sim_batch_run(qsim_batch *b, const double *angles, double *energies) {
     cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
+    if (*b->h_flag) return berr(b, QSIM_ETIMEOUT, "a bounded wait for bulk copies gave up; energies not computed");
     std::memcpy(energies, b->h_energies, sizeof(double) * b->count);
     return QSIM_OK;
 }
