@@ -227,6 +227,53 @@ def measure_ops(sim, n, terms, u, stream, peak, b, reps=3):
         ms = statistics.median(times)
         out[name] = {"ms": ms, "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak, "bytes": nbytes,
                      "what": what}
+
+    # a diagonal block: every controlled phase and RZ among 12 qubits, fused
+    # by the planner into one pass (timed by the library's per-launch events,
+    # so the host's table build is not counted)
+    dq = list(range(n - 12, n))
+    diag_ops = [cg.op("R", (j,), (k,), (0.1 * (j + k),)) for j in dq for k in dq if k < j]
+    diag_ops += [cg.op("RZ", (j,), (), (0.3 + 0.01 * j,)) for j in dq]
+    sim.flush()
+    sim.set_profiling(True)
+    times, passes = [], []
+    for rep in range(reps + 1):
+        sim.reset_stats()
+        sim.run(diag_ops)
+        sim.flush()
+        kt = sim.kernel_times()
+        passes.append(sim.stats()["passes"])
+        if rep and "block_diag" in kt:
+            times.append(kt["block_diag"]["total_ms"] / kt["block_diag"]["launches"])
+    sim.set_profiling(False)
+    if times:
+        ms = statistics.median(times)
+        out["diag_block_12q"] = {"ms": ms, "GB/s": 2 * N * b / ms / 1e6, "frac": 2 * N * b / ms / 1e6 / peak,
+                                 "bytes": 2 * N * b, "passes": passes[-1],
+                                 "what": "%d diagonal gates on qubits %d..%d (controlled phases, RZ) as one "
+                                         "multiply-by-table pass: read all, write all" % (len(diag_ops), dq[0], dq[-1])}
+
+    # an emulated classical function: x -> 7x mod 1021 on 10 qubits (identity
+    # above 1020), one gather/scatter pass
+    perm = [(7 * x) % 1021 if x < 1021 else x for x in range(1024)]
+    for name, qs in (("permute_low10", list(range(10))), ("permute_high10", list(range(n - 10, n)))):
+        def fn(qs=qs):
+            sim.apply_permutation(perm, qs)
+            sim.flush()
+        fn()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        out[name] = {"ms": ms, "GB/s": 2 * N * b / ms / 1e6, "frac": 2 * N * b / ms / 1e6 / peak,
+                     "bytes": 2 * N * b,
+                     "what": "x -> 7x mod 1021 on qubits %d..%d: read all, write all" % (qs[0], qs[-1])}
     return out
 
 

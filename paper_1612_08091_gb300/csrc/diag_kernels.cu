@@ -13,7 +13,8 @@
 //
 // The table and five 256-entry bit-gather tables (index bits 0..39 -> bits
 // of the table index) are copied to shared memory per CTA; each thread
-// handles 16 bytes of amplitudes per step (two complex64 or one complex128).
+// handles 16 bytes of amplitudes per access (two complex64 or one
+// complex128), four accesses in flight.
 // complex128 uses FP64 products, or double-float products when the handle
 // runs complex128 gates in double-float arithmetic.
 #include <cuda_runtime.h>
@@ -48,25 +49,47 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_block(Amp *__restrict__ p
                gather[768 + ((i >> 24) & 255)] | gather[1024 + ((i >> 32) & 255)];
     };
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    constexpr int kU = 4;  // 16-byte accesses in flight per thread
     if (sizeof(Amp) == 8) {
-        // two complex64 per 16-byte access
+        // two complex64 per 16-byte access; the second's table index adds
+        // index bit 0 to the first's
         float4 *p4 = (float4 *)psi;
-        for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < N / 2; j += stride) {
-            float4 v = p4[j];
-            const float2 a = cmul(((const float2 *)d)[tidx(2 * j)], make_float2(v.x, v.y));
-            const float2 b = cmul(((const float2 *)d)[tidx(2 * j + 1)], make_float2(v.z, v.w));
-            p4[j] = make_float4(a.x, a.y, b.x, b.y);
+        const float2 *df = (const float2 *)d;
+        const unsigned bit0 = gather[1];
+        for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j0 < N / 2; j0 += kU * stride) {
+            float4 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (j0 + u * stride < N / 2) v[u] = p4[j0 + u * stride];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint64_t j = j0 + u * stride;
+                if (j >= N / 2) continue;
+                const unsigned t0 = tidx(2 * j);
+                const float2 a = cmul(df[t0], make_float2(v[u].x, v[u].y));
+                const float2 b = cmul(df[t0 | bit0], make_float2(v[u].z, v[u].w));
+                p4[j] = make_float4(a.x, a.y, b.x, b.y);
+            }
         }
     } else {
         double2 *p2 = (double2 *)psi;
         const double2 *dd = (const double2 *)d;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
-            const double2 z = dd[tidx(i)];
-            if (use_df) {
-                const qsim_df::C2 u = qsim_df::split(z);
-                p2[i] = qsim_df::to_double(qsim_df::cmul(u, qsim_df::split(p2[i])));
-            } else {
-                p2[i] = cmul(z, p2[i]);
+        for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < N; i0 += kU * stride) {
+            double2 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (i0 + u * stride < N) v[u] = p2[i0 + u * stride];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint64_t i = i0 + u * stride;
+                if (i >= N) continue;
+                const double2 z = dd[tidx(i)];
+                if (use_df) {
+                    const qsim_df::C2 w = qsim_df::split(z);
+                    p2[i] = qsim_df::to_double(qsim_df::cmul(w, qsim_df::split(v[u])));
+                } else {
+                    p2[i] = cmul(z, v[u]);
+                }
             }
         }
     }
