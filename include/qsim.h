@@ -200,8 +200,10 @@ int sim_reset_stats(qsim *s);
  * launch is bracketed by CUDA events on the handle's stream; the times are
  * collected (stream synchronised) by sim_get_kernel_times, which returns one
  * row per kernel class seen since profiling was switched on.  Class names:
- * "gate_dense", "gate_phase", "gate_diag", "gate_x", "block_tc",
- * "block_dense". */
+ * "gate_dense", "gate_phase", "gate_diag", "gate_x" (plain gates),
+ * "block_tc" (4- and 5-qubit blocks on the tensor cores), "block_tc6"
+ * (6-qubit blocks), "block_dense" (blocks on CUDA cores), "block_diag"
+ * (diagonal blocks). */
 typedef struct qsim_kernel_time {
     char name[24];
     uint64_t launches;
@@ -210,19 +212,23 @@ typedef struct qsim_kernel_time {
 } qsim_kernel_time;
 
 /* on: 0 off, 1 per-class times, 2 per-class times and per-launch records
- * (features of the planned item and its duration) for sim_get_item_times. */
+ * (features of the planned item and its cost) for sim_get_item_times. */
 int sim_set_profiling(qsim *s, int on);
 int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nrows);
 
 /* ---------------------------------------------------------------------------
  * Learned fusion planner (not in the paper).  With profiling mode 2 the
  * library records, for every gate or block launch, 16 features of the
- * planned item and its event-timed duration; a cost model trained on these
- * records (sim_mlp_*) predicts the log of a launch's duration in ms, and
- * QSIM_FUSE_MLP plans with it: greedy blocks for kmax = 1..5, each block
- * either fused or left as plain gates, whichever is predicted faster; the
- * plan with the lowest predicted total is executed.  Without a loaded model
- * QSIM_FUSE_MLP falls back to greedy fusion.
+ * planned item and its cost: the larger of its event-timed device duration
+ * and the host time spent issuing it (block matrix, operand record,
+ * staging, launch), since small registers are host-bound.  A cost model
+ * trained on these records (sim_mlp_*) predicts the log of an item's cost
+ * in ms, and QSIM_FUSE_MLP plans with it: the greedy plans for kmax = 2 up
+ * to the handle's block width limit (kmax, at most 6 on the complex64
+ * tensor-core path, else 5) and the all-plain plan, each block either fused
+ * or left as plain gates, whichever is predicted cheaper; the plan with the
+ * lowest predicted total is executed, its blocks launched as they are
+ * formed.  Without a loaded model QSIM_FUSE_MLP falls back to greedy fusion.
  * Feature order: n/32, bytes per amplitude/16, fused, on tensor cores,
  * width/5, gates/32, plain dense, plain phase, plain diagonal, plain X,
  * controls/8, log2(fraction of amplitudes touched)/8, lowest qubit/32,
@@ -230,7 +236,8 @@ int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nro
  * --------------------------------------------------------------------------- */
 
 /* Copy out (and clear) the per-launch records: feats holds 16 floats per
- * record, ms one float; *nitems receives the number of records available
+ * record, ms one float (the cost above, in ms); *nitems receives the number
+ * of records available
  * (records are cleared only when all of them fit in max_items). */
 int sim_get_item_times(qsim *s, float *feats, float *ms, int max_items, int *nitems);
 
@@ -238,7 +245,7 @@ int sim_get_item_times(qsim *s, float *feats, float *ms, int max_items, int *nit
  * W2[h][h], b2[h], w3[h], b3); count 0 unloads it.  Copied. */
 int sim_set_cost_model(qsim *s, const float *params, int count, int hidden);
 
-/* Predicted duration (ms) of the last plan made by the learned planner. */
+/* Predicted cost (ms) of the last plan made by the learned planner. */
 int sim_plan_stats(qsim *s, double *predicted_ms);
 
 /* The cost model's network, trained on the GPU by the library's own
@@ -259,8 +266,9 @@ int sim_mlp_train(qsim_mlp *m, const float *X, const float *T, int n, int epochs
 
 /* ---------------------------------------------------------------------------
  * Batched variational sweep (not in the paper).  A batch of hardware-
- * efficient-ansatz circuits of different sizes is evaluated in one
- * persistent launch, captured in a CUDA graph and replayed per call.
+ * efficient-ansatz circuits of different sizes is evaluated in two
+ * persistent launches (circuits larger than shared memory, then the rest),
+ * captured in one CUDA graph and replayed per call.
  * Circuit c has nqubits[c] qubits (2..24) and layers[c] layers; it starts in
  * |0...0>, each layer applies RY(theta) to every qubit, RZ(phi) to every
  * qubit, then CNOT(q -> q+1) for q = 0..n-2 in order.  The result is the
@@ -284,8 +292,10 @@ int sim_batch_create(int count, const int *nqubits, const int *layers, double h,
 
 /* Evaluate all circuits.  angles (host): for each circuit in order, for each
  * layer, n RY angles (qubit 0..n-1) then n RZ angles; energies (host):
- * count doubles.  The first call captures the graph (angles H2D, queue
- * reset, persistent kernel, energies D2H); later calls replay it. */
+ * count doubles.  The first call captures the graph (angles H2D, queue and
+ * error-flag reset, the two persistent kernels, energies and flag D2H);
+ * later calls replay it.  QSIM_ETIMEOUT if a bounded device wait gave up
+ * (energies then not written). */
 int sim_batch_run(qsim_batch *b, const double *angles, double *energies);
 
 /* Time every candidate launch configuration (threads per CTA 256/512/1024,
@@ -293,9 +303,10 @@ int sim_batch_run(qsim_batch *b, const double *angles, double *energies);
  * runs each after one warm-up, keep the fastest (median) and report it. */
 int sim_batch_autotune(qsim_batch *b, const double *angles, int reps, int *threads, int *m);
 
-/* Set the launch configuration by hand (QSIM_EINVAL if it cannot run this
- * batch: 2^m must be <= 32 * threads, and the largest circuit must satisfy
- * n - m <= m - 5). */
+/* Set the launch configuration of the small-circuit kernel by hand
+ * (QSIM_EINVAL if it cannot run: 2^m must be <= 32 * threads for 256 and
+ * 512 threads, <= 16 * 1024 for 1024); circuits with more than m qubits go
+ * to the global-memory kernel (256 threads, 2^12-amplitude chunks). */
 int sim_batch_set_config(qsim_batch *b, int threads, int m);
 
 int sim_batch_destroy(qsim_batch *b);
