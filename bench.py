@@ -58,7 +58,7 @@ def parse():
                          "instead of the 4096-circuit mix")
     ap.add_argument("--vqe-config", default=None, metavar="THREADS,M",
                     help="vqe workload: fixed launch configuration instead of the autotuner's")
-    ap.add_argument("--workload", default="random", choices=["random", "vqe", "planner"],
+    ap.add_argument("--workload", default="random", choices=["random", "vqe", "planner", "qft", "grover", "fig6"],
                     help="random: the headline line; vqe / planner: secondary measurements")
     return ap.parse_args()
 
@@ -637,6 +637,111 @@ def run_planner(args):
     return 0
 
 
+def run_circuit(args):
+    """The structured circuits of the method's examples, fused complex64
+    (greedy, kmax 6) against plain complex128 (one launch per gate, timed on
+    a sample of the first gates and extrapolated per amplitude update):
+      qft    -- QFT on 30 qubits applied to a seeded basis state x; checked
+                against 2^{-n/2} exp(2 pi i x y / 2^n) on sampled amplitudes;
+      grover -- Grover search on 28 qubits: 20 iterations timed, the full
+                r = floor(pi/4 sqrt(2^n)) extrapolated; the marked amplitude
+                checked against (-1)^r sin((2r+1) theta) for the 20;
+      fig6   -- the paper's benchmark circuit on 30 qubits: H on all, the
+                controlled-Rz chain, H on all; checked by its norm."""
+    import math
+
+    import torch
+
+    import paper_1612_08091_gb300 as q
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    w = args.workload
+    basis = 0
+    if w == "qft":
+        n = 30
+        basis = int(cg.random_basis_state(n, SEED))
+        ops = cg.qft_ops(n)
+        what = "QFT on %d qubits of the basis state x = %d (seed %d)" % (n, basis, SEED)
+        full_iters = None
+    elif w == "grover":
+        n = 28
+        marked = int(cg.grover_marked(n, 2017))
+        iters = 20
+        full_iters = cg.grover_iterations(n)
+        ops = cg.grover_ops(n, marked, iterations=iters)
+        what = ("Grover search on %d qubits, marked item %d (seed 2017): %d of the r = %d iterations timed"
+                % (n, marked, iters, full_iters))
+    else:
+        n = 30
+        ops = cg.hadamard_crz_chain(n, SEED)
+        what = "H on all %d qubits, controlled-Rz chain (angles seed %d), H on all" % (n, SEED)
+        full_iters = None
+    upd = amp_updates(ops, n)
+
+    def timed(sim, ops_, reps):
+        ts = []
+        for _ in range(args.warmup + reps):
+            sim.reset(basis)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.run(ops_)
+            sim.flush()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(ts[args.warmup:])
+
+    with q.Simulator(n, precision="c64", fusion="greedy", stream=stream) as sim:
+        t_fused = timed(sim, ops, args.steps)
+        sim.reset_stats()
+        sim.reset(basis)
+        sim.run(ops)
+        sim.flush()
+        passes = sim.stats()["passes"]
+        check = {}
+        if w == "qft":
+            rng = np.random.default_rng(SEED + 1)
+            rnd = [int(i) for i in rng.integers(0, 1 << n, 256)]
+            got = np.array([sim.get_amplitudes(i, 1)[0] for i in rnd] + list(sim.get_amplitudes(0, 4096)))
+            ys = rnd + list(range(4096))
+            # exact integer phase x*y mod 2^n, then to an angle
+            want = np.array([np.exp(2j * math.pi * ((basis * y) % (1 << n)) / float(1 << n)) for y in ys])
+            want *= 2.0 ** (-n / 2)
+            check = {"max_abs_error": float(np.max(np.abs(got - want))), "amplitude": 2.0 ** (-n / 2),
+                     "sampled": int(len(ys))}
+        elif w == "grover":
+            theta = math.asin(2.0 ** (-n / 2))
+            a = sim.get_amplitudes(marked, 1)[0]
+            want = (-1) ** iters * math.sin((2 * iters + 1) * theta)
+            check = {"marked_amplitude": [float(a.real), float(a.imag)], "closed_form": want,
+                     "abs_error": float(abs(a - want))}
+        else:
+            _, nrm = sim.probs_all()
+            check = {"norm2": nrm}
+    torch.cuda.empty_cache()
+
+    # plain complex128 on a sample of the first gates
+    sample = ops[: min(len(ops), 64)]
+    with q.Simulator(n, precision="c128", fusion="none", stream=stream) as ps:
+        t_plain_sample = timed(ps, sample, 1)
+    rate_plain = amp_updates(sample, n) / t_plain_sample
+    out = {"metric": "%s: fused complex64 vs plain complex128" % w, "value": upd / t_fused, "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_fused,
+           "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+           "config": {"workload": what, "n_qubits": n, "gates": len(ops), "passes": passes,
+                      "amp_updates": upd, "fusion": "greedy", "kmax": 6},
+           "plain_c128": {"value": rate_plain, "unit": UNIT, "sample": "first %d gates, one launch per gate, fp64"
+                          % len(sample), "extrapolated_ms": 1e3 * upd / rate_plain,
+                          "speedup_of_fused": (upd / t_fused) / rate_plain},
+           "check": check}
+    if full_iters:
+        out["config"]["extrapolated_full_search_s"] = t_fused * full_iters / iters
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -645,6 +750,8 @@ def main():
         return run_vqe(args)
     if args.workload == "planner":
         return run_planner(args)
+    if args.workload in ("qft", "grover", "fig6"):
+        return run_circuit(args)
     return run_ours(args)
 
 
