@@ -277,6 +277,20 @@ def measure_ops(sim, n, terms, u, stream, peak, b, reps=3):
     return out
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -341,7 +355,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": workload_name(n, args.depth), "n_qubits": n, "precision": "c128",
                    "fusion": "none", "parallelism": "replicas"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                          "sample": "%d gates of the workload per step on the FP64 oracle, %d qubits" % (g, n)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -475,7 +489,7 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         v, dt, threads, g = oracle_sample(n, ops, args.cpu_gates)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
                "sample": "%d gates of the %d-qubit workload on the FP64 oracle (%.1f s)" % (g, n, dt)}
 
     if rank == 0:
@@ -550,6 +564,27 @@ def run_vqe(args):
             e = b.run(angles)
             ts.append(time.perf_counter() - t0)
     t = statistics.median(ts)
+
+    # the two classes alone, same launch configuration: circuits held in
+    # shared memory (n <= m) and circuits in global memory (n > m)
+    def class_time(sel):
+        cs = [c for c in circuits if sel(c)]
+        if not cs:
+            return None, 0
+        ang = q.hea_angles(cs)
+        with q.Batch([c["n"] for c in cs], [c["L"] for c in cs]) as bb:
+            bb.set_config(*cfg)
+            for _ in range(args.warmup):
+                bb.run(ang)
+            tt = []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                bb.run(ang)
+                tt.append(time.perf_counter() - t0)
+        return statistics.median(tt), len(cs)
+
+    t_res, n_res = class_time(lambda c: c["n"] <= cfg[1])
+    t_glob, n_glob = class_time(lambda c: c["n"] > cfg[1])
     # HBM bytes of the circuits above the shared-memory size m: the initial
     # |0> write, per layer a pair pass and a top-qubit pass (each reads and
     # writes the state), the final permutation pass and the energy read
@@ -563,6 +598,13 @@ def run_vqe(args):
                       "amp_updates_per_step": upd, "autotuned": {"threads": cfg[0], "smem_qubits": cfg[1]},
                       "autotune_s": tune_s, "timing": "host clock around sim_batch_run (graph replay: angles "
                                                       "H2D, persistent kernel, energies D2H)"},
+           "classes": {
+               "shared_memory": {"circuits": n_res, "ms": None if t_res is None else 1e3 * t_res,
+                                 "bound": "on chip (shared memory, FP32)"},
+               "global_memory": {"circuits": n_glob, "ms": None if t_glob is None else 1e3 * t_glob,
+                                 "GB/s": None if not t_glob else hbm / t_glob / 1e9,
+                                 "frac": None if not t_glob else hbm / t_glob / 1e9 / peak},
+               "timing": "each class alone as its own batch, same launch configuration"},
            "roofline": {"bound": "hbm", "achieved": hbm / t / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": hbm / t / 1e9 / peak, "peak_source": peak_kind, "traffic": None,
                         "bytes_per_step": hbm,
