@@ -91,9 +91,10 @@ typedef struct qsim_opts {
     int no_tensor_cores;    /* non-zero: run complex64 blocks on the CUDA cores */
     int no_norm_tracking;   /* non-zero: do not rescale tensor-core block outputs by the
                                previous block pass's input/output norm ratio */
-    int c128_double_float;  /* non-zero: complex128 one-qubit dense, diagonal and phase gates
-                               compute in FP32 pairs (about 2^-45 relative error per result,
-                               one FP64 add per component) instead of FP64 arithmetic */
+    int c128_double_float;  /* non-zero: complex128 gates (one-qubit dense, diagonal and
+                               phase gates, multi-target dense gates) and fused blocks
+                               (dense and diagonal) compute in FP32 pairs (about 2^-45
+                               relative error per product) instead of FP64 arithmetic */
 } qsim_opts;
 
 /* A Pauli-sum term c * P.  Qubit q of P is X if bit q is set in xmask only,

@@ -98,6 +98,9 @@ __device__ __forceinline__ C2 cdot2(const C2 &u0, const C2 &x0, const C2 &u1, co
     return r;
 }
 
+// a + b (complex)
+__device__ __forceinline__ C2 cadd(const C2 &a, const C2 &b) { return C2{add(a.re, b.re), add(a.im, b.im)}; }
+
 // u * x (complex)
 __device__ __forceinline__ C2 cmul(const C2 &u, const C2 &x) {
     C2 r;

@@ -78,7 +78,7 @@ struct qsim {
     bool tc_enabled = true;
     int tc_terms = 3;
     bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
-    bool c128_df = false;       // complex128 one-qubit gates in double-float arithmetic
+    bool c128_df = false;       // complex128 gates and blocks in double-float arithmetic
     int tc_variant = 3;         // 4-5-qubit blocks: 3 k_block_tmem<5> (state operand in tensor memory);
                                 // 0 k_block_tc<2>, 1 k_block_tc_ws, 2 k_block_tc<1> (state operand in shared memory)
     int tc_streaming = 0;       // streaming (evict-first) cache hints on the block kernel's loads and stores
