@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-gates", type=int, default=6, help="gates of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--fused-c128-layers", type=int, default=6,
+                    help="layers of the circuit timed as complex128 double-float fused blocks (0: skip)")
     ap.add_argument("--vqe-uniform", default=None, metavar="COUNT,QUBITS,LAYERS",
                     help="vqe workload: COUNT circuits of QUBITS qubits and LAYERS layers (seeded angles) "
                          "instead of the 4096-circuit mix")
@@ -450,20 +452,22 @@ def run_ours(args):
     measurements = measure_ops(sim, n, terms, u, stream, peak, 8 if args.precision == "c64" else 16) \
         if rank == 0 else None
 
-    plain = plain_df = None
+    plain = plain_df = fused_df = None
     if not args.no_plain and rank == 0 and args.plain_layers > 0:
         sim.close()
         torch.cuda.empty_cache()
-        # the first `plain_layers` layers of the same circuit
-        cnt = 0
-        for layer in range(args.plain_layers):
-            cnt += n + len(range(layer % 2, n - 1, 2))
-        sample = ops[:cnt]
-        def plain_sample(df):
-            with q.Simulator(n, precision="c128", fusion="none", stream=stream, c128_df=df) as ps:
+        def layers_prefix(nl):
+            cnt = 0
+            for layer in range(nl):
+                cnt += n + len(range(layer % 2, n - 1, 2))
+            return ops[:cnt]
+
+        def plain_sample(df, sample, fusion="none", kmax=6):
+            with q.Simulator(n, precision="c128", fusion=fusion, kmax=kmax, stream=stream, c128_df=df) as ps:
                 ps.run(sample[: n])  # warm-up on the same register
                 ps.flush()
                 torch.cuda.synchronize()
+                ps.reset_stats()
                 ps.set_profiling(True)
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
@@ -473,18 +477,26 @@ def run_ours(args):
                 b.record(stream)
                 torch.cuda.synchronize()
                 pkt = ps.kernel_times()
+                pst = ps.stats()
             ps_s = a.elapsed_time(b) / 1e3
             torch.cuda.empty_cache()
             return {"value": amp_updates(sample, n) / ps_s, "unit": UNIT, "precision": "c128",
                     "arithmetic": "double-float (fp32 pairs, ~2^-45 relative)" if df else "fp64",
-                    "fusion": "none",
-                    "sample": "first %d layers (%d gates) of the same %d-qubit circuit, one launch per gate"
-                              % (args.plain_layers, len(sample), n),
+                    "fusion": fusion if fusion == "none" else "%s, kmax %d" % (fusion, kmax),
+                    "sample": "first %d gates of the same %d-qubit circuit, %s"
+                              % (len(sample), n, "one launch per gate" if fusion == "none"
+                                 else "%d fused passes" % pst["passes"]),
                     "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
                                     "GB/s": v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9} for k, v in pkt.items()}}
 
-        plain = plain_sample(False)
-        plain_df = plain_sample(True)
+        # the first `plain_layers` layers of the same circuit, one launch per
+        # gate; and complex128 fused blocks in double-float arithmetic over
+        # the first `fused_c128_layers` layers (4-qubit blocks: the block
+        # arithmetic, not HBM, bounds complex128 blocks)
+        plain = plain_sample(False, layers_prefix(args.plain_layers))
+        plain_df = plain_sample(True, layers_prefix(args.plain_layers))
+        if args.fused_c128_layers > 0:
+            fused_df = plain_sample(True, layers_prefix(args.fused_c128_layers), "greedy", 4)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -512,6 +524,7 @@ def run_ours(args):
             "measurements": measurements,
             "plain_c128": plain,
             "plain_c128_double_float": plain_df,
+            "fused_c128_double_float": fused_df,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes},
             "clocks": clk,
