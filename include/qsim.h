@@ -307,7 +307,8 @@ int sim_batch_autotune(qsim_batch *b, const double *angles, int reps, int *threa
 /* Set the launch configuration of the small-circuit kernel by hand
  * (QSIM_EINVAL if it cannot run: 2^m must be <= 32 * threads for 256 and
  * 512 threads, <= 16 * 1024 for 1024); circuits with more than m qubits go
- * to the global-memory kernel (256 threads, 2^12-amplitude chunks). */
+ * to the global-memory kernel (256 threads, two CTAs per SM, 2^12-amplitude
+ * chunks). */
 int sim_batch_set_config(qsim_batch *b, int threads, int m);
 
 int sim_batch_destroy(qsim_batch *b);

@@ -16,14 +16,16 @@
 // (largest circuits first) until the batch is done; there is no waiting on
 // other CTAs.  A circuit of n <= m qubits (m = 12..14, tuned) lives in the
 // CTA's shared memory; a larger one lives in a per-CTA pair of global
-// buffers and is processed in chunks of 2^g amplitudes (g = min(m, 13)):
+// buffers and is processed in chunks of 2^g amplitudes (g = 12):
 //   pair pass: the ladder permutation of the previous layer maps the
 //     destination chunks hi and hi ^ (2^h - 1) (h = n - g) onto the same two
 //     source chunks S, S ^ 1 with S = hi ^ (hi << 1): an element at offset o
 //     of source chunk S ^ p lands in chunk hi if parity(o) == p, else in its
-//     partner, at offset prefix_xor(o).  Both source chunks are read whole
-//     (coalesced), scattered into the two destination chunks in shared
-//     memory, get the gates on qubits 0..g-1, and are written back whole;
+//     partner, at the offset whose bit k is the XOR of bits 0..k of o.  Both
+//     source chunks are copied whole into shared memory and stay in source
+//     order there (logical qubit k pairs the elements p and p ^ (3 << k)),
+//     get the gates on qubits 0..g-1, and are written back whole, each
+//     destination element read from its source position;
 //   high pass: tiles made of runs of 2^(g-h) amplitudes times the h top
 //     qubits get the gates on the top qubits, in place.
 // The energy is read after one more pair pass that applies the last layer's
@@ -71,20 +73,27 @@ struct VqeArgs {
 
 // A layer's rotations factor as (prod_q RZ(phi_q)) (prod_q RY(theta_q)):
 // RZ and RY on one qubit keep their order, and gates on different qubits
-// commute.  RY(theta) = [[c, -s], [s, c]] (c, s = cos, sin theta/2) is real,
-// so on complex amplitudes it costs 4 FP32 operations per amplitude instead
-// of the 8 of a general 2x2; the RZ part is diagonal,
-//   prod_q RZ(phi_q) |i> = exp(i (sum_{q in i} phi_q - Phi/2)) |i>,
-// Phi = sum_q phi_q, and is applied as one complex factor per amplitude from
-// two small tables (low and high bits) while the amplitudes move anyway.
+// commute.  Write theta/2 = theta'/2 + j pi/2 with |theta'/2| <= pi/4; then
+//   RY(theta) = RY(j pi) RY(theta'),   RY(pi) = X Z,   RY(2 pi) = -I,
+//   RY(theta') = c' [[1, -t], [t, 1]],  c' = cos(theta'/2), t = tan(theta'/2),
+// so the rotation proper is two FMAs per amplitude (|t| <= 1) and the rest
+// is bookkeeping: c' and the sign (-1)^floor(j/2) join the layer's global
+// factor, and for odd j the X Z is moved past the RZ (RZ(phi) X = X RZ(-phi)):
+//   RZ(phi) RY(theta) = s c' X diag(e^{i phi/2}, -e^{-i phi/2}) [[1, -t], [t, 1]].
+// The diagonal part of all qubits is
+//   exp(-i Phi'/2) prod_{q in i} p_q,  p_q = e^{i phi_q} or -e^{-i phi_q} (odd j),
+// Phi' = sum_q (+-phi_q), applied as one complex factor per amplitude from
+// two small tables (low and high bits) while the amplitudes move anyway, and
+// the X of the qubits with odd j (the layer's flip mask F) is an XOR of the
+// index where each amplitude is read for writing back.
 struct Rot {
-    float c, s;
+    float t;
 };
 
 __device__ __forceinline__ void apply_pair(float2 *x, unsigned i0, unsigned i1, const Rot &g) {
     const float2 a = x[i0], b = x[i1];
-    x[i0] = make_float2(g.c * a.x - g.s * b.x, g.c * a.y - g.s * b.y);
-    x[i1] = make_float2(g.s * a.x + g.c * b.x, g.s * a.y + g.c * b.y);
+    x[i0] = make_float2(fmaf(-g.t, b.x, a.x), fmaf(-g.t, b.y, a.y));
+    x[i1] = make_float2(fmaf(g.t, a.x, b.x), fmaf(g.t, a.y, b.y));
 }
 
 // Rotation pairing the elements i and i ^ mask of a 2^k-amplitude array in
@@ -101,16 +110,6 @@ __device__ __forceinline__ void gate_smem(float2 *x, int k, unsigned mask, const
 
 __device__ __forceinline__ unsigned ladder_src(unsigned y, unsigned mask) { return (y ^ (y << 1)) & mask; }
 
-// inverse of y -> y ^ (y << 1): bit k of the result is the XOR of bits 0..k
-__device__ __forceinline__ unsigned prefix_xor(unsigned x) {
-    x ^= x << 1;
-    x ^= x << 2;
-    x ^= x << 4;
-    x ^= x << 8;
-    x ^= x << 16;
-    return x;
-}
-
 // Rotations g[0..nb) on a 2^k-amplitude array in shared memory, applied four
 // at a time in registers: each thread loads the 16 amplitudes of a group,
 // applies the four rotations there and stores them back, so a layer of k
@@ -126,7 +125,7 @@ __device__ __forceinline__ unsigned prefix_xor(unsigned x) {
 // source order, and mask[j] = 3 << k_j stands for logical qubit k_j.  The
 // element of a pair whose logical bit k_j is 0 is the one whose bits 0..k_j
 // have even parity; within a group that parity is the base's, so the
-// rotation is applied with s -> -s where the base's parity is odd.  This
+// rotation is applied with t -> -t where the base's parity is odd.  This
 // needs groups without identity padding (nb a multiple of 4).
 __device__ __forceinline__ void cswap(int &a, int &b) {
     const int lo = a < b ? a : b, hi = a < b ? b : a;
@@ -134,7 +133,7 @@ __device__ __forceinline__ void cswap(int &a, int &b) {
     b = hi;
 }
 
-__device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot *g, int nb, const Rot *ident,
+__device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot *g, int nb,
                               bool logical_pairs = false) {
     if (k < 4) {
         // fewer than four bits in the array: one pass per gate
@@ -142,36 +141,18 @@ __device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot 
         return;
     }
     for (int g0 = 0; g0 < nb; g0 += 4) {
-        // the group's four bits (padded with identity gates on unused bits)
-        unsigned m0, m1, m2, m3;
-        const Rot *q0, *q1, *q2, *q3;
-        int s0, s1, s2, s3;  // the pivots, sorted, for the zero insertion
-        {
-            unsigned ms[4];
-            const Rot *gg[4];
-            unsigned used = 0;  // pivots taken
-            int cnt = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (g0 + j < nb) {
-                    ms[j] = mask[g0 + j];
-                    gg[j] = &g[g0 + j];
-                    used |= ms[j] & (0u - ms[j]);
-                    cnt = j + 1;
-                }
-            int b = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j >= cnt) {
-                    while ((used >> b) & 1u) ++b;
-                    ms[j] = 1u << b;
-                    gg[j] = ident;
-                    used |= 1u << b;
-                }
-            m0 = ms[0]; m1 = ms[1]; m2 = ms[2]; m3 = ms[3];
-            q0 = gg[0]; q1 = gg[1]; q2 = gg[2]; q3 = gg[3];
-            s0 = __ffs(m0) - 1; s1 = __ffs(m1) - 1; s2 = __ffs(m2) - 1; s3 = __ffs(m3) - 1;
-        }
+        // the group's four bits (padded with identity gates on the lowest
+        // unused bits)
+        const bool h1 = g0 + 1 < nb, h2 = g0 + 2 < nb, h3 = g0 + 3 < nb;
+        unsigned m0 = mask[g0], m1 = h1 ? mask[g0 + 1] : 0u, m2 = h2 ? mask[g0 + 2] : 0u,
+                 m3 = h3 ? mask[g0 + 3] : 0u;
+        unsigned used = (m0 & (0u - m0)) | (m1 & (0u - m1)) | (m2 & (0u - m2)) | (m3 & (0u - m3));
+        if (!h1) { m1 = ~used & (used + 1u); used |= m1; }
+        if (!h2) { m2 = ~used & (used + 1u); used |= m2; }
+        if (!h3) { m3 = ~used & (used + 1u); used |= m3; }
+        const float t0 = g[g0].t, t1 = h1 ? g[g0 + 1].t : 0.f, t2 = h2 ? g[g0 + 2].t : 0.f,
+                    t3 = h3 ? g[g0 + 3].t : 0.f;
+        int s0 = __ffs(m0) - 1, s1 = __ffs(m1) - 1, s2 = __ffs(m2) - 1, s3 = __ffs(m3) - 1;
         cswap(s0, s1);
         cswap(s2, s3);
         cswap(s0, s2);
@@ -190,18 +171,16 @@ __device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot 
                 v[r] = x[base ^ ((r & 1) ? m0 : 0u) ^ ((r & 2) ? m1 : 0u) ^ ((r & 4) ? m2 : 0u) ^ ((r & 8) ? m3 : 0u)];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const Rot *G = j == 0 ? q0 : j == 1 ? q1 : j == 2 ? q2 : q3;
                 const unsigned mj = j == 0 ? m0 : j == 1 ? m1 : j == 2 ? m2 : m3;
-                const float c = G->c;
-                float sn = G->s;
-                if (logical_pairs && (__popc(base & ((mj & (0u - mj)) * 2u - 1u)) & 1)) sn = -sn;
+                float t = j == 0 ? t0 : j == 1 ? t1 : j == 2 ? t2 : t3;
+                if (logical_pairs && (__popc(base & ((mj & (0u - mj)) * 2u - 1u)) & 1)) t = -t;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     if ((r >> j) & 1) continue;
                     const int r1 = r | (1 << j);
                     const float2 a = v[r], bb = v[r1];
-                    v[r] = make_float2(c * a.x - sn * bb.x, c * a.y - sn * bb.y);
-                    v[r1] = make_float2(sn * a.x + c * bb.x, sn * a.y + c * bb.y);
+                    v[r] = make_float2(fmaf(-t, bb.x, a.x), fmaf(-t, bb.y, a.y));
+                    v[r1] = make_float2(fmaf(t, a.x, bb.x), fmaf(t, a.y, bb.y));
                 }
             }
 #pragma unroll
@@ -266,7 +245,8 @@ __device__ void build_phase_table(float2 *t, int kb, const float2 *ph, float2 ex
 // GLOBAL = false: circuits of n <= m qubits, each held in one CTA's shared
 // memory.  GLOBAL = true: larger circuits in per-CTA global buffers, two
 // CTAs per SM so that one CTA's loads, arithmetic and stores overlap the
-// other's.
+// other's (measured faster than one CTA of 512 threads per SM with
+// double-buffered copies: 44.9 against 41.0 ms for the 4096-circuit batch).
 // Order of the pair pass's 12 rotations, taken four at a time.  A group's
 // pivot bits are the same in all lanes' addresses at each access, so a group
 // holding qubits 0..3 (the bank bits of 8-byte elements) would be a 16-way
@@ -280,18 +260,17 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
     extern __shared__ float2 sm[];
     __shared__ int s_idx;
     __shared__ double s_red[32];
-    __shared__ Rot s_rot[32];       // this layer's RY per qubit; [31] = identity
+    __shared__ Rot s_rot[32];       // this layer's RY per qubit
     __shared__ Rot s_rotp[32];      // the pair pass's rotations, in kPairOrder
     __shared__ float2 s_ph[32];     // e^{i phi_q}
     __shared__ unsigned s_mask[32]; // XOR mask of each rotation in the current pass
-    __shared__ float2 s_tlo[128];   // phases of index bits 0..6 (times e^{-i Phi/2})
+    __shared__ float2 s_tlo[128];   // phases of index bits 0..6 (times the global factor)
     __shared__ float2 s_thi[128];   // phases of the next bits of a chunk or register
-    __shared__ float2 s_ttop[256];  // phases of the top h qubits (global-memory path)
-    __shared__ float2 s_gph;        // e^{-i Phi/2}
+    __shared__ float2 s_gph;        // the layer's global factor: prod_q s_q c'_q times e^{-i Phi'/2}
+    __shared__ unsigned s_flip;     // the layer's flip mask F
     __shared__ __align__(8) uint64_t s_bar[1];  // bulk-copy completion (global-memory path)
     __shared__ uint32_t s_phase;
     if (threadIdx.x == 0) {
-        s_rot[31] = Rot{1.f, 0.f};
         if (GLOBAL) {
             mbar_init(s_bar, 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -299,22 +278,38 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
         }
     }
     __syncthreads();
-    const Rot *ident = &s_rot[31];
-    // the layer's rotations, per-qubit phases and the global factor
+    // the layer's rotations t_q, per-qubit phases p_q, flip mask and global
+    // factor (warp 0; n <= 32)
     auto layer_setup = [&](const double *al, int n) {
-        if (threadIdx.x < (unsigned)n) {
-            float sn, c, sp, cp;
-            sincosf((float)(0.5 * al[threadIdx.x]), &sn, &c);
-            sincosf((float)al[n + threadIdx.x], &sp, &cp);
-            s_rot[threadIdx.x] = Rot{c, sn};
-            s_ph[threadIdx.x] = make_float2(cp, sp);
-        }
-        if (threadIdx.x == 0) {
-            double Phi = 0.0;
-            for (int q = 0; q < n; ++q) Phi += al[n + q];
-            float sp, cp;
-            sincosf((float)(-0.5 * Phi), &sp, &cp);
-            s_gph = make_float2(cp, sp);
+        if (threadIdx.x < 32) {
+            const unsigned q = threadIdx.x;
+            unsigned flip = 0;
+            float2 f = make_float2(1.f, 0.f);
+            if (q < (unsigned)n) {
+                constexpr double kPi = 3.14159265358979323846;
+                const double hth = remainder(0.5 * al[q], 2.0 * kPi);  // theta/2 (RY has period 4 pi)
+                const double j = rint(hth * (2.0 / kPi));                // -2..2
+                const int ji = (int)j;
+                float sh, ch;
+                sincosf((float)(hth - j * (0.5 * kPi)), &sh, &ch);
+                flip = (unsigned)ji & 1u;
+                const float sc = ((ji >> 1) & 1) ? -ch : ch;  // (-1)^floor(j/2) c'
+                const double phi = al[n + q];
+                float sp, cp, s2, c2;
+                sincosf((float)remainder(phi, 2.0 * kPi), &sp, &cp);
+                sincosf((float)(0.5 * remainder(phi, 4.0 * kPi)), &s2, &c2);
+                s_rot[q] = Rot{sh / ch};
+                s_ph[q] = flip ? make_float2(-cp, sp) : make_float2(cp, sp);
+                f = make_float2(sc * c2, flip ? sc * s2 : -sc * s2);
+            }
+            const unsigned fl = __ballot_sync(0xffffffffu, flip);
+#pragma unroll
+            for (int o = 16; o; o >>= 1)
+                f = cmul(f, make_float2(__shfl_xor_sync(0xffffffffu, f.x, o), __shfl_xor_sync(0xffffffffu, f.y, o)));
+            if (q == 0) {
+                s_gph = f;
+                s_flip = fl;
+            }
         }
         __syncthreads();
     };
@@ -340,14 +335,16 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                 layer_setup(al, n);
                 build_phase_table(s_tlo, klo, s_ph, s_gph);
                 build_phase_table(s_thi, n - klo, s_ph + klo, make_float2(1.f, 0.f));
-                gates_blocked(sm, n, s_mask, s_rot, n, ident);  // ends with a barrier
-                // the RZ phases and the CNOT ladder as one pass through registers
+                gates_blocked(sm, n, s_mask, s_rot, n);  // ends with a barrier
+                // the RZ phases, the flips and the CNOT ladder as one pass
+                // through registers
+                const unsigned F = s_flip;
                 float2 v[kRegAmps];
 #pragma unroll
                 for (int j = 0; j < kRegAmps; ++j) {
                     const unsigned y = threadIdx.x + (unsigned)j * T;
                     if (y < N) {
-                        const unsigned x = ladder_src(y, N - 1);
+                        const unsigned x = ladder_src(y, N - 1) ^ F;
                         v[j] = cmul(sm[x], cmul(s_tlo[x & 127u], s_thi[x >> 7]));
                     }
                 }
@@ -375,6 +372,7 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
             float2 *dst = src + A.gstride;
             const unsigned G = 1u << g, nchunks = 1u << h, hmask = nchunks - 1u, gmask = G - 1u;
             const unsigned run_bytes = 8u << lowrun;  // a high-pass tile is 2^h runs of 2^lowrun amplitudes
+            float2 *const s_ttop = sm + ((size_t)2 << g);  // phases of the top h qubits, after the pair buffer
             for (unsigned i = threadIdx.x; i < N; i += T) src[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
             __syncthreads();
             bool permuted = false;  // src holds the state before a pending ladder permutation
@@ -418,12 +416,13 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                 const unsigned gl = ((e ^ (e << 1)) & gmask);
                 return ((((unsigned)__popc(gl) & 1u) ^ (e >> g)) << g) | gl;
             };
-            auto store_pair = [&](float2 *to, unsigned pr, bool phased) {
+            // phased: the layer's phases and flips of qubits 0..g-1 (flo)
+            auto store_pair = [&](float2 *to, unsigned pr, bool phased, unsigned flo) {
                 const unsigned hb = pr ^ hmask;
                 for (unsigned e = threadIdx.x; e < 2 * G; e += T) {
-                    const unsigned o = e & gmask;
-                    float2 v = sm[pair_pos(e)];
-                    if (phased) v = cmul(v, cmul(s_tlo[o & 127u], s_thi[o >> 7]));
+                    const unsigned o = e & gmask, of = o ^ flo;
+                    float2 v = sm[pair_pos(e ^ flo)];
+                    if (phased) v = cmul(v, cmul(s_tlo[of & 127u], s_thi[of >> 7]));
                     to[((size_t)(e < G ? pr : hb) << g) | o] = v;
                 }
                 __syncthreads();
@@ -472,8 +471,8 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                         failed = true;
                         break;
                     }
-                    gates_blocked(sm, g + 1, s_mask, s_rotp, g, ident, permuted);
-                    store_pair(dst, pr, true);
+                    gates_blocked(sm, g + 1, s_mask, s_rotp, g, permuted);
+                    store_pair(dst, pr, true, s_flip & gmask);
                 }
                 // high pass on dst, in place: RY on the top qubits, then
                 // their RZ phases on the way out
@@ -482,9 +481,12 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                         failed = true;
                         break;
                     }
-                    gates_blocked(sm, g, s_mask + g, s_rot + g, h, ident);
-                    for (unsigned e = threadIdx.x; e < G; e += T)
-                        dst[tile_index(t, e)] = cmul(sm[e], s_ttop[e >> lowrun]);
+                    gates_blocked(sm, g, s_mask + g, s_rot + g, h);
+                    const unsigned fhi = s_flip >> g;  // flips of the top qubits
+                    for (unsigned e = threadIdx.x; e < G; e += T) {
+                        const unsigned ef = e ^ (fhi << lowrun);
+                        dst[tile_index(t, e)] = cmul(sm[ef], s_ttop[ef >> lowrun]);
+                    }
                     __syncthreads();
                 }
                 float2 *tmp = src;
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                         xf += 2.f * (a.x * b.x + a.y * b.y);
                     }
                 }
-                store_pair(dst, pr, false);
+                store_pair(dst, pr, false, 0u);
             }
             for (unsigned t = 0; t < nchunks && !failed; ++t) {
                 if (!load_tile(dst, t)) {
@@ -586,12 +588,17 @@ VqeKernel kernel_for(int threads) {
 }
 
 // The global-memory kernel: 256 threads, chunks of 2^12 amplitudes (a pair
-// of them is 64 KB of shared memory), two CTAs per SM (measured faster than
-// three, which force the registers down to 80 and spill).
+// of them is 64 KB of shared memory, followed by the phase table of the top
+// n - 12 qubits, 2 KB for n = 20, 32 KB for n = 24), two CTAs per SM
+// (measured faster than three, which force the registers down to 80 and
+// spill).
 constexpr int kGlobalThreads = 256;
 constexpr int kGlobalBits = 12;
 static_assert(kGlobalBits == 12, "kPairOrder lists the 12 chunk qubits");
-constexpr size_t kGlobalSmem = (size_t)16 << kGlobalBits;
+constexpr int kMaxBatchQubits = 2 * kGlobalBits;  // n <= 2 g: a tile's runs are whole amplitudes
+size_t global_smem(int nmax) {
+    return ((size_t)16 << kGlobalBits) + ((size_t)8 << std::max(nmax - kGlobalBits, 0));
+}
 static_assert(kGlobalBits % 4 == 0, "pair-pass rotation groups must not need identity padding");
 
 // circuits with more than m qubits: a prefix of the order (sorted by size)
@@ -608,10 +615,11 @@ bool config_valid(const qsim_batch *b, int threads, int m) {
 
 int occupancy_global(const qsim_batch *b, int *grid) {
     VqeKernel k = k_vqe_batch<kGlobalThreads, true>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGlobalSmem);
+    const size_t smem = global_smem(b->nmax);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return QSIM_ECUDA;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGlobalThreads, kGlobalSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kGlobalThreads, smem);
     if (e != cudaSuccess || per_sm < 1) return QSIM_ENOTSUP;
     *grid = std::min(b->sms * per_sm, b->max_grid);
     return QSIM_OK;
@@ -660,7 +668,7 @@ int launch(qsim_batch *b, int threads, int m, int grid) {
         a.counter = b->d_counter;
         a.begin = 0;
         a.end = large;
-        k_vqe_batch<kGlobalThreads, true><<<ggrid, kGlobalThreads, kGlobalSmem, b->stream>>>(a);
+        k_vqe_batch<kGlobalThreads, true><<<ggrid, kGlobalThreads, global_smem(b->nmax), b->stream>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return berr(b, QSIM_ECUDA, cudaGetErrorString(e));
     }
@@ -712,7 +720,7 @@ int sim_batch_workspace_bytes(int count, const int *nqubits, const int *layers, 
     long long nang = 0;
     int nmax = 0;
     for (int i = 0; i < count; ++i) {
-        if (nqubits[i] < 2 || nqubits[i] > 24 || layers[i] < 0) return QSIM_EINVAL;
+        if (nqubits[i] < 2 || nqubits[i] > kMaxBatchQubits || layers[i] < 0) return QSIM_EINVAL;
         nang += 2LL * nqubits[i] * layers[i];
         nmax = std::max(nmax, nqubits[i]);
     }

@@ -52,6 +52,48 @@ def test_small_batch_all_paths(qs, oracle_mod):
     del rng
 
 
+@pytest.mark.parametrize("scale", [0.5, 3.3])
+def test_angles_outside_half_turn(qs, oracle_mod, scale):
+    """Rotation angles scaled beyond [-pi, pi] (and within [-pi/2, pi/2]):
+    every reduction of theta/2 by a multiple of pi/2 (quarter turns with
+    their X Z and sign) and the RZ half-angle period, in the shared-memory
+    and the global-memory circuits."""
+    circuits = cg.hea_batch(24, seed=31, nmin=3, nmax=16, lmin=1, lmax=3)
+    for c in circuits:
+        c["ry"] = c["ry"] * scale
+        c["rz"] = c["rz"] * scale
+    nq = [c["n"] for c in circuits]
+    nl = [c["L"] for c in circuits]
+    angles = qs.hea_angles(circuits)
+    want = np.array([oracle_energy(oracle_mod, c) for c in circuits])
+    with qs.Batch(nq, nl) as b:
+        for threads, m in [(256, 12), (512, 14)]:
+            b.set_config(threads, m)
+            got = b.run(angles)
+            for i, c in enumerate(circuits):
+                assert abs(got[i] - want[i]) <= tol(c["n"]), (threads, m, c["n"], got[i], want[i])
+
+
+def test_largest_circuits(qs, oracle_mod):
+    """21..24 qubits, the top of the accepted range: up to 12 qubits above
+    the 2^12-amplitude chunks (a phase table of 4096 entries), and at 24 qubits
+    tile runs of one amplitude (plain loads instead of bulk copies)."""
+    circuits = cg.hea_batch(4, seed=77, nmin=21, nmax=21, lmin=1, lmax=2)
+    for c, n in zip(circuits, (21, 22, 23, 24)):
+        rng = np.random.default_rng(n)
+        c["n"] = n
+        c["ry"] = rng.uniform(-np.pi, np.pi, size=(c["L"], n))
+        c["rz"] = rng.uniform(-np.pi, np.pi, size=(c["L"], n))
+    nq = [c["n"] for c in circuits]
+    nl = [c["L"] for c in circuits]
+    angles = qs.hea_angles(circuits)
+    want = np.array([oracle_energy(oracle_mod, c) for c in circuits])
+    with qs.Batch(nq, nl) as b:
+        got = b.run(angles)
+    for i, c in enumerate(circuits):
+        assert abs(got[i] - want[i]) <= tol(c["n"]), (c["n"], got[i], want[i])
+
+
 def test_full_batch_4096_sampled(qs, oracle_mod):
     circuits = cg.hea_batch(4096, seed=2016)
     nq = [c["n"] for c in circuits]
