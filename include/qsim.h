@@ -142,7 +142,9 @@ int sim_flush(qsim *s);
  * its value is qubits[j]), 1 <= m <= 12; perm[x] = f(x) for x < 2^m must be
  * a bijection (QSIM_EINVAL otherwise).  Where all controls are |1>, the
  * amplitude of register value x moves to register value f(x).  Flushes the
- * queue, then runs at once (one pass over the touched groups). */
+ * queue, then runs at once (one pass over the touched groups; fixed points
+ * of f are not touched when the register and controls lie above the lowest
+ * 4 KB of amplitudes and f's cycles give at least one task per SM). */
 int sim_apply_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, const int *controls, int c);
 
 /* P(qubit = 1) = sum of |psi_i|^2 over indices with bit q set, accumulated
@@ -204,7 +206,8 @@ int sim_reset_stats(qsim *s);
  * "gate_dense", "gate_phase", "gate_diag", "gate_x" (plain gates),
  * "block_tc" (4- and 5-qubit blocks on the tensor cores), "block_tc6"
  * (6-qubit blocks), "block_dense" (blocks on CUDA cores), "block_diag"
- * (diagonal blocks). */
+ * (diagonal blocks), "permute" and "permute_cycles" (sim_apply_permutation:
+ * tiled through shared memory, or along the cycles of f). */
 typedef struct qsim_kernel_time {
     char name[24];
     uint64_t launches;

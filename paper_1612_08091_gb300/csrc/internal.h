@@ -99,12 +99,14 @@ struct qsim {
     double last_plan_predicted_ms = 0;
     std::vector<Pending> pending;
     struct ClassTime { uint64_t launches = 0; double ms = 0, bytes = 0; };
-    ClassTime class_time[8];
+    ClassTime class_time[16];  // indexed by KernelClass
 };
 
 enum KernelClass {
-    KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_BLOCK_DIAG, KC_BLOCK_TC6, KC_COUNT
+    KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_BLOCK_DIAG, KC_BLOCK_TC6, KC_PERMUTE,
+    KC_PERMUTE_CYCLES, KC_COUNT
 };
+static_assert(KC_COUNT <= 16, "class_time holds 16 kernel classes");
 constexpr int kMaxDiagQubits = 12;
 
 // Bytes of one amplitude.
@@ -136,7 +138,9 @@ int cuda_err(qsim *s, cudaError_t e, const char *where);
 int launch_gate_plain(qsim *s, const GateRec &g);
 int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m);
 // Emulated classical bijection on a register (perm_kernels.cu).
-int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask);
+// *cycles: whether the cycle walk ran (else the tiled kernel)
+int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask,
+                       bool *cycles);
 
 // Diagonal block: psi_i *= d[bits of i on dmask] (diag_kernels.cu).
 int launch_block_diag(qsim *s, uint64_t dmask, const cd *d);

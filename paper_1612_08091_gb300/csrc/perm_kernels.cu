@@ -23,8 +23,20 @@
 // too.  The register-value and run offsets and f^-1 come from a device
 // record (uint64 offsets, uint32 values) and are copied to shared memory
 // once per CTA.  m <= 12.
+//
+// Where the register and the controls lie above the 9 lowest qubits (8 for
+// complex128: 4 KB of contiguous amplitudes), the permutation
+// instead follows the cycles of f: for a cycle e_0 -> e_1 -> ... -> e_{L-1}
+// -> e_0 and a slice of 4 KB at the same place in every register value's
+// block, the data rotate one step along the cycle in place,
+//   new[e_{i+1}] = old[e_i],
+// walked from e_{L-1} down to e_0 with the loads of the next eight elements
+// in flight (a load of e_j always precedes the store to e_j).  Every access
+// of a CTA is 4 KB contiguous, fixed points of f are not touched, and the
+// work is (cycle, slice) tasks, longest cycles first.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -101,6 +113,108 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(Amp *__restrict__ psi,
     }
 }
 
+constexpr int kCycThreads = 256;
+constexpr int kCycDepth = 8;  // loads in flight per thread along a cycle
+
+// coff: the cycles' elements as register offsets in 16-byte units, cycle
+// by cycle, f(e_i) = e_{i+1}; cstart[j]: first element of cycle j (ncyc + 1
+// entries); a task is (cycle, slice) with the slice fastest.
+__global__ void __launch_bounds__(kCycThreads) k_permute_cycles(float4 *__restrict__ psi16, const InsertSpec ins,
+                                                                uint64_t cmask16, const uint64_t *__restrict__ coff,
+                                                                const uint32_t *__restrict__ cstart, uint32_t ncyc,
+                                                                uint64_t nslices, int amp_shift) {
+    const uint64_t ntasks = (uint64_t)ncyc * nslices;
+    for (uint64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const uint32_t cyc = (uint32_t)(task / nslices);
+        const uint64_t sl = task - (uint64_t)cyc * nslices;
+        const uint32_t b0 = cstart[cyc];
+        const int L = (int)(cstart[cyc + 1] - b0);
+        const uint64_t *e = coff + b0;
+        // this thread's 16 bytes of the slice at register value 0
+        float4 *p = psi16 + (((insert_zeros(sl << (8 + amp_shift), ins) >> amp_shift) | cmask16) + threadIdx.x);
+        const float4 first = p[e[L - 1]];
+        float4 r[kCycDepth];  // r[j] holds old[e_{L-2-j}], then the element kCycDepth further down
+#pragma unroll
+        for (int j = 0; j < kCycDepth; ++j)
+            if (L - 2 - j >= 0) r[j] = p[e[L - 2 - j]];
+        int i = L - 1;  // the element written next (from old[e_{i-1}])
+        while (i >= 1) {
+#pragma unroll
+            for (int j = 0; j < kCycDepth; ++j) {
+                if (i >= 1) {
+                    const float4 v = r[j];
+                    if (i - 1 - kCycDepth >= 0) r[j] = p[e[i - 1 - kCycDepth]];
+                    p[e[i]] = v;
+                    --i;
+                }
+            }
+        }
+        p[e[0]] = first;
+    }
+}
+
+// The cycle walk when the register and the controls leave the lowest 4 KB
+// of amplitudes contiguous and there are enough tasks to fill the GPU;
+// returns QSIM_ENOTSUP otherwise (the tiled kernel then runs).
+template <typename Amp>
+int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask) {
+    const int amp_shift = sizeof(Amp) == 8 ? 1 : 0;  // amplitudes per 16 bytes: 2 or 1
+    const int slice_bits = 8 + amp_shift;  // 4 KB slices: 512 c64 or 256 c128 amplitudes
+    const uint64_t fixed = qmask | cmask;
+    if ((fixed & ((1ull << slice_bits) - 1ull)) != 0) return QSIM_ENOTSUP;
+    const int D = 1 << m;
+    // the cycles of f, longest first
+    std::vector<std::vector<uint32_t>> cycles;
+    std::vector<char> seen(D, 0);
+    size_t total = 0;
+    for (int v = 0; v < D; ++v) {
+        if (seen[v] || (int)perm[v] == v) continue;
+        std::vector<uint32_t> cy;
+        for (uint32_t x = (uint32_t)v; !seen[x]; x = (uint32_t)perm[x]) {
+            seen[x] = 1;
+            cy.push_back(x);
+        }
+        total += cy.size();
+        cycles.push_back(std::move(cy));
+    }
+    if (cycles.empty()) return QSIM_OK;  // f is the identity
+    const int nfree = s->n - m - __builtin_popcountll(cmask);
+    const uint64_t nslices = 1ull << (nfree - slice_bits);
+    if ((uint64_t)cycles.size() * nslices < (uint64_t)kSMs) return QSIM_ENOTSUP;
+    std::stable_sort(cycles.begin(), cycles.end(),
+                     [](const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) { return a.size() > b.size(); });
+    const size_t ncyc = cycles.size();
+    std::vector<unsigned char> rec(sizeof(uint64_t) * total + sizeof(uint32_t) * (ncyc + 1));
+    uint64_t *coff = (uint64_t *)rec.data();
+    uint32_t *cstart = (uint32_t *)(rec.data() + sizeof(uint64_t) * total);
+    size_t k = 0;
+    for (size_t j = 0; j < ncyc; ++j) {
+        cstart[j] = (uint32_t)k;
+        for (uint32_t v : cycles[j]) {
+            uint64_t a = 0;
+            for (int b = 0; b < m; ++b)
+                if ((v >> b) & 1u) a |= 1ull << qubits[b];
+            coff[k++] = a >> amp_shift;
+        }
+    }
+    cstart[ncyc] = (uint32_t)k;
+    unsigned char *dev = nullptr;
+    int rc = stage_operand(s, rec.data(), rec.size(), &dev);
+    if (rc) return rc;
+    InsertSpec ins{};
+    ins.m = 0;
+    for (int b = 0; b < 64; ++b)
+        if ((fixed >> b) & 1ull) ins.pos[ins.m++] = b;
+    const uint64_t ntasks = (uint64_t)ncyc * nslices;
+    // 64 registers a thread: four CTAs of 256 threads resident per SM
+    const uint64_t grid = ntasks < (uint64_t)kSMs * 4 ? ntasks : (uint64_t)kSMs * 4;
+    k_permute_cycles<<<(unsigned)grid, kCycThreads, 0, s->stream>>>(
+        (float4 *)s->state, ins, cmask >> amp_shift, (const uint64_t *)dev,
+        (const uint32_t *)(dev + sizeof(uint64_t) * total), (uint32_t)ncyc, nslices, amp_shift);
+    s->stats.launches++;
+    return cuda_err(s, cudaGetLastError(), "permutation launch");
+}
+
 template <typename Amp>
 int permute(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask) {
     const int D = 1 << m;
@@ -166,7 +280,12 @@ int permute(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qm
 
 }  // namespace
 
-int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask) {
-    return s->prec == QSIM_C128 ? permute<double2>(s, perm, qubits, m, qmask, cmask)
-                                : permute<float2>(s, perm, qubits, m, qmask, cmask);
+int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask,
+                       bool *cycles) {
+    const bool c128 = s->prec == QSIM_C128;
+    int rc = c128 ? permute_cycles<double2>(s, perm, qubits, m, qmask, cmask)
+                  : permute_cycles<float2>(s, perm, qubits, m, qmask, cmask);
+    *cycles = rc != QSIM_ENOTSUP;
+    if (rc != QSIM_ENOTSUP) return rc;
+    return c128 ? permute<double2>(s, perm, qubits, m, qmask, cmask) : permute<float2>(s, perm, qubits, m, qmask, cmask);
 }

@@ -40,6 +40,51 @@ def test_permutation_matches_oracle(qs, oracle_mod, prec, qubits, controls):
     np.testing.assert_allclose(got, ref.psi, atol=tol)
 
 
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("kind", ["random", "add", "fixed_points", "identity"])
+def test_permutation_cycle_walk(qs, oracle_mod, prec, kind):
+    """A register above the lowest 4 KB of amplitudes (qubits 14..19 of 24,
+    one control on qubit 22; 2^17 amplitudes per register value, so even one
+    cycle makes 256 tasks of 4 KB) is permuted along the cycles of f in place:
+    a random bijection (several cycles of mixed lengths), x -> x + 5 mod 64
+    (one cycle), a bijection with fixed points, and the identity."""
+    n, qubits, controls = 24, (16, 14, 19, 15, 18, 17), (22,)
+    rng = np.random.default_rng(12)
+    D = 1 << len(qubits)
+    if kind == "random":
+        perm = rng.permutation(D)
+    elif kind == "add":
+        perm = (np.arange(D) + 5) % D
+    elif kind == "fixed_points":
+        perm = np.arange(D)
+        moved = rng.choice(D, 20, replace=False)
+        perm[moved] = moved[rng.permutation(20)]
+    else:
+        perm = np.arange(D)
+    psi = cg.random_state(n, seed=9)
+    ref = oracle_mod.OracleSim(n, psi=psi)
+    ref.apply_permutation(perm, qubits, controls)
+    with qs.Simulator(n, precision=prec) as sim:
+        sim.set_amplitudes(psi)
+        sim.set_profiling(True)
+        sim.apply_permutation(perm, qubits, controls)
+        got = sim.get_amplitudes()
+        kt = sim.kernel_times()
+    if kind != "identity":
+        assert kt.get("permute_cycles", {}).get("launches", 0) == 1, kt
+    tol = 0 if prec == "c128" else 1e-7
+    np.testing.assert_allclose(got, ref.psi, atol=tol)
+
+
+def test_permutation_tiled_when_register_is_low(qs):
+    """The tiled kernel takes registers within the lowest 4 KB of amplitudes."""
+    with qs.Simulator(16, precision="c64") as sim:
+        sim.set_profiling(True)
+        sim.apply_permutation(np.roll(np.arange(16), 3), (0, 1, 2, 3), ())
+        kt = sim.kernel_times()
+    assert kt.get("permute", {}).get("launches", 0) == 1 and "permute_cycles" not in kt, kt
+
+
 def test_permutation_rejects_non_bijection(qs):
     with qs.Simulator(6) as sim:
         with pytest.raises(qs.QsimError) as e:
