@@ -12,13 +12,16 @@
 // the simulator benchmark (Sec. 4.3.2, Fig. 7) are made of such gates.
 //
 // The table and five 256-entry bit-gather tables (index bits 0..39 -> bits
-// of the table index) are copied to shared memory per CTA; each thread
-// handles 16 bytes of amplitudes per access (two complex64 or one
-// complex128), four accesses in flight.
+// of the table index) are copied to shared memory per CTA.  A CTA takes
+// contiguous chunks of up to 2^16 amplitudes, so the table-index bits of
+// index bits 16 and above are gathered once per chunk; each thread handles
+// 16 bytes of amplitudes per access (two complex64 or one complex128),
+// eight accesses in flight.
 // complex128 uses FP64 products, or double-float products when the handle
 // runs complex128 gates in double-float arithmetic.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -33,7 +36,7 @@ namespace {
 constexpr int kDiagThreads = 256;
 
 template <typename Amp>
-__global__ void __launch_bounds__(kDiagThreads) k_diag_block(Amp *__restrict__ psi, uint64_t N, int k,
+__global__ void __launch_bounds__(kDiagThreads) k_diag_block(Amp *__restrict__ psi, uint64_t nchunks, int cb, int k,
                                                             const unsigned char *__restrict__ rec, int use_df) {
     extern __shared__ unsigned char sm_raw[];
     Amp *d = (Amp *)sm_raw;
@@ -44,51 +47,57 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_block(Amp *__restrict__ p
     for (int i = threadIdx.x; i < D; i += blockDim.x) d[i] = gd[i];
     for (int i = threadIdx.x; i < 5 * 256; i += blockDim.x) gather[i] = gg[i];
     __syncthreads();
-    auto tidx = [&](uint64_t i) {
-        return (unsigned)gather[i & 255] | gather[256 + ((i >> 8) & 255)] | gather[512 + ((i >> 16) & 255)] |
-               gather[768 + ((i >> 24) & 255)] | gather[1024 + ((i >> 32) & 255)];
-    };
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    constexpr int kU = 4;  // 16-byte accesses in flight per thread
-    if (sizeof(Amp) == 8) {
-        // two complex64 per 16-byte access; the second's table index adds
-        // index bit 0 to the first's
-        float4 *p4 = (float4 *)psi;
-        const float2 *df = (const float2 *)d;
-        const unsigned bit0 = gather[1];
-        for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j0 < N / 2; j0 += kU * stride) {
-            float4 v[kU];
+    constexpr int kU = 8;                    // 16-byte accesses in flight per thread
+    constexpr int kPer = 16 / sizeof(Amp);   // amplitudes per access
+    const unsigned units = (1u << cb) / kPer;  // accesses per chunk
+    for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const uint64_t base = ch << cb;
+        // table-index bits of index bits 16.. (constant over the chunk, cb <= 16)
+        const unsigned hi = (unsigned)gather[512 + ((base >> 16) & 255)] | gather[768 + ((base >> 24) & 255)] |
+                            gather[1024 + ((base >> 32) & 255)];
+        const unsigned lo0 = (unsigned)(base & 0xFFFFu);
+        auto tidx = [&](unsigned idx) {
+            const unsigned lo = lo0 | (idx * kPer);
+            return (unsigned)gather[lo & 255] | gather[256 + (lo >> 8)] | hi;
+        };
+        for (unsigned u0 = threadIdx.x; u0 < units; u0 += kU * kDiagThreads) {
+            if (sizeof(Amp) == 8) {
+                // two complex64 per access; the second's table index adds
+                // index bit 0 to the first's
+                float4 *p4 = (float4 *)psi + (base >> 1);
+                const float2 *df = (const float2 *)d;
+                const unsigned bit0 = gather[1];
+                float4 v[kU];
 #pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (j0 + u * stride < N / 2) v[u] = p4[j0 + u * stride];
+                for (int u = 0; u < kU; ++u)
+                    if (u0 + u * kDiagThreads < units) v[u] = p4[u0 + u * kDiagThreads];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const uint64_t j = j0 + u * stride;
-                if (j >= N / 2) continue;
-                const unsigned t0 = tidx(2 * j);
-                const float2 a = cmul(df[t0], make_float2(v[u].x, v[u].y));
-                const float2 b = cmul(df[t0 | bit0], make_float2(v[u].z, v[u].w));
-                p4[j] = make_float4(a.x, a.y, b.x, b.y);
-            }
-        }
-    } else {
-        double2 *p2 = (double2 *)psi;
-        const double2 *dd = (const double2 *)d;
-        for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < N; i0 += kU * stride) {
-            double2 v[kU];
+                for (int u = 0; u < kU; ++u) {
+                    const unsigned idx = u0 + u * kDiagThreads;
+                    if (idx >= units) continue;
+                    const unsigned t0 = tidx(idx);
+                    const float2 a = cmul(df[t0], make_float2(v[u].x, v[u].y));
+                    const float2 b = cmul(df[t0 | bit0], make_float2(v[u].z, v[u].w));
+                    p4[idx] = make_float4(a.x, a.y, b.x, b.y);
+                }
+            } else {
+                double2 *p2 = (double2 *)psi + base;
+                const double2 *dd = (const double2 *)d;
+                double2 v[kU];
 #pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (i0 + u * stride < N) v[u] = p2[i0 + u * stride];
+                for (int u = 0; u < kU; ++u)
+                    if (u0 + u * kDiagThreads < units) v[u] = p2[u0 + u * kDiagThreads];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const uint64_t i = i0 + u * stride;
-                if (i >= N) continue;
-                const double2 z = dd[tidx(i)];
-                if (use_df) {
-                    const qsim_df::C2 w = qsim_df::split(z);
-                    p2[i] = qsim_df::to_double(qsim_df::cmul(w, qsim_df::split(v[u])));
-                } else {
-                    p2[i] = cmul(z, v[u]);
+                for (int u = 0; u < kU; ++u) {
+                    const unsigned idx = u0 + u * kDiagThreads;
+                    if (idx >= units) continue;
+                    const double2 z = dd[tidx(idx)];
+                    if (use_df) {
+                        const qsim_df::C2 w = qsim_df::split(z);
+                        p2[idx] = qsim_df::to_double(qsim_df::cmul(w, qsim_df::split(v[u])));
+                    } else {
+                        p2[idx] = cmul(z, v[u]);
+                    }
                 }
             }
         }
@@ -137,11 +146,13 @@ int diag_block(qsim *s, uint64_t dmask, const cd *dt) {
         if (e != cudaSuccess) return cuda_err(s, e, "diagonal kernel attribute");
         attr[which][s->device] = true;
     }
-    const uint64_t N = 1ull << s->n;
-    const uint64_t work = sizeof(Amp) == 8 ? N / 2 : N;
-    uint64_t grid = (work + kDiagThreads - 1) / kDiagThreads;
-    if (grid > (uint64_t)kSMs * 8) grid = (uint64_t)kSMs * 8;
-    k_diag_block<Amp><<<(unsigned)grid, kDiagThreads, smem, s->stream>>>((Amp *)s->state, N, k, dev,
+    // contiguous chunks of 2^cb amplitudes (cb <= 16), at least about four
+    // per SM where the register allows
+    const int n = s->n;
+    const int cb = std::max(std::min(n, 9), std::min(16, n - 10));
+    const uint64_t nchunks = 1ull << (n - cb);
+    const uint64_t grid = nchunks < (uint64_t)kSMs * 8 ? nchunks : (uint64_t)kSMs * 8;
+    k_diag_block<Amp><<<(unsigned)grid, kDiagThreads, smem, s->stream>>>((Amp *)s->state, nchunks, cb, k, dev,
                                                                            s->c128_df ? 1 : 0);
     s->stats.launches++;
     return cuda_err(s, cudaGetLastError(), "diagonal block launch");

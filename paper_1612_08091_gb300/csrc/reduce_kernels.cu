@@ -380,7 +380,8 @@ __global__ void k_collapse_mask(Amp *__restrict__ psi, uint64_t N, uint64_t mask
 // (-1)^{popc(tile & zh_k)} W^(m_k) with zl_k, m_k, zh_k = bits 0..4, 5..9
 // and 10.. of z_k.  W^ is kept per warp in shared memory.  Terms with the
 // same (zl, m) form a group whose tile-dependent signs fold into one
-// coefficient per tile, so the lanes' work scales with the groups (11 for a
+// coefficient per tile, formed by one lane per group and broadcast by warp
+// shuffles, so the lanes' work scales with the groups (11 for a
 // nearest-neighbour ZZ chain), not with the terms.
 // Coefficients come in both precisions so that the complex64 kernel does
 // no FP64 arithmetic per term (FP64, conversions included, runs at 1/58 of
@@ -433,14 +434,21 @@ __global__ void __launch_bounds__(kZThreads) k_expect_z_tiles(const Amp *__restr
         __syncwarp();
         R e = 0;
         const unsigned t32 = (unsigned)tile;
-        for (int g = 0; g < T.ng; ++g) {
-            R c = 0;  // the group's coefficient for this tile (warp-uniform)
-            for (int k = T.first[g]; k < T.first[g + 1]; ++k) {
-                const R ck = zcoef(T, k, R(0));
-                c += (__popc(t32 & T.zh[k]) & 1) ? -ck : ck;
+        for (int g0 = 0; g0 < T.ng; g0 += 32) {
+            // lane j forms group g0 + j's coefficient for this tile; the
+            // lanes then take the groups one by one from it
+            R c = 0;
+            if (g0 + lane < T.ng)
+                for (int k = T.first[g0 + lane]; k < T.first[g0 + lane + 1]; ++k) {
+                    const R ck = zcoef(T, k, R(0));
+                    c += (__popc(t32 & T.zh[k]) & 1) ? -ck : ck;
+                }
+            const int gn = T.ng - g0 < 32 ? T.ng - g0 : 32;
+            for (int j = 0; j < gn; ++j) {
+                const R cj = __shfl_sync(0xffffffffu, c, j);
+                const R v = wh[warp][T.m[g0 + j]][lane];
+                e += (__popc(lane & T.zl[g0 + j]) & 1) ? -cj * v : cj * v;
             }
-            const R v = wh[warp][T.m[g]][lane];
-            e += (__popc(lane & T.zl[g]) & 1) ? -c * v : c * v;
         }
         __syncwarp();
         facc += e;
