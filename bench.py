@@ -649,8 +649,8 @@ def run_planner(args):
     ops = cg.random_u3_brickwork(n, 30, seed=2018)
     upd = amp_updates(ops, n)
 
-    def timed(fusion, model=None):
-        with q.Simulator(n, precision="c64", fusion=fusion) as sim:
+    def timed(fusion, model=None, n=n, ops=ops, precision="c64", df=False):
+        with q.Simulator(n, precision=precision, fusion=fusion, c128_df=df) as sim:
             if model is not None:
                 sim.set_cost_model(*model)
             res = []
@@ -668,6 +668,20 @@ def run_planner(args):
 
     t_greedy, p_greedy = timed("greedy")
     t_mlp, p_mlp = timed("mlp", (params, 32))
+
+    # complex128 in double-float arithmetic, where fused blocks are bound by
+    # FP32 arithmetic rather than HBM: a second model trained on this GPU's
+    # complex128 double-float timings (26-28 qubits), held out at 30 qubits
+    t0 = time.perf_counter()
+    X2, ms2 = costmodel.collect(sizes=(26, 27, 28), precisions=("c128",), kmaxes=(1, 2, 3, 4, 5), seed=2018,
+                                df=True)
+    collect2_s = time.perf_counter() - t0
+    params2, loss2 = costmodel.train(X2, ms2, hidden=32, epochs=300)
+    n2 = 30
+    ops2 = cg.random_u3_brickwork(n2, 10, seed=2018)
+    upd2 = amp_updates(ops2, n2)
+    t_greedy2, p_greedy2 = timed("greedy", n=n2, ops=ops2, precision="c128", df=True)
+    t_mlp2, p_mlp2 = timed("mlp", (params2, 32), n=n2, ops=ops2, precision="c128", df=True)
     # plain complex128 on the first layer, extrapolated per amplitude update
     layer = ops[: n + len(range(0, n - 1, 2))]
     with q.Simulator(n, precision="c128", fusion="none") as ps:
@@ -690,7 +704,15 @@ def run_planner(args):
            "learned": {"ms": 1e3 * t_mlp, "passes": p_mlp, "gain_over_greedy": t_greedy / t_mlp},
            "plain_c128": {"value": rate_plain, "unit": UNIT,
                           "sample": "first layer (%d gates), fp64 arithmetic" % len(layer),
-                          "extrapolated_ms": 1e3 * upd / rate_plain}}
+                          "extrapolated_ms": 1e3 * upd / rate_plain},
+           "c128_double_float": {
+               "workload": "30-qubit random U3 + CNOT brickwork, depth 10 (seed 2018), complex128 in "
+                           "double-float arithmetic",
+               "training": {"samples": int(len(ms2)), "sizes": [26, 27, 28], "collect_s": collect2_s,
+                            "train_mse_log_ms": loss2},
+               "greedy_k5": {"ms": 1e3 * t_greedy2, "passes": p_greedy2, "value": upd2 / t_greedy2},
+               "learned": {"ms": 1e3 * t_mlp2, "passes": p_mlp2, "value": upd2 / t_mlp2,
+                           "gain_over_greedy": t_greedy2 / t_mlp2}}}
     print(json.dumps(out), flush=True)
     return 0
 

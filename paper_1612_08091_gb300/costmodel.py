@@ -31,10 +31,12 @@ def training_circuits(n, seed):
     }
 
 
-def collect(sizes=(26, 27, 28), precisions=("c64", "c128"), kmaxes=(1, 2, 3, 4, 5, 6), seed=2018, repeats=1):
+def collect(sizes=(26, 27, 28), precisions=("c64", "c128"), kmaxes=(1, 2, 3, 4, 5, 6), seed=2018, repeats=1,
+            df=False):
     """Run every training circuit under every plan width and return the
     per-launch features (N x 16) and durations in ms (N).  Width 6 exists
-    only for complex64 (tensor cores), so complex128 skips it."""
+    only for complex64 (tensor cores), so complex128 skips it.  df: complex128
+    handles compute in double-float arithmetic."""
     feats, ms = [], []
     for n in sizes:
         circuits = training_circuits(n, seed + n)
@@ -43,7 +45,7 @@ def collect(sizes=(26, 27, 28), precisions=("c64", "c128"), kmaxes=(1, 2, 3, 4, 
                 if kmax > 5 and prec != "c64":
                     continue
                 fusion = "none" if kmax == 1 else "greedy"
-                with Simulator(n, precision=prec, fusion=fusion, kmax=max(kmax, 1)) as sim:
+                with Simulator(n, precision=prec, fusion=fusion, kmax=max(kmax, 1), c128_df=df) as sim:
                     for _ in range(repeats + 1):
                         for ops in circuits.values():
                             sim.reset(0)

@@ -168,7 +168,7 @@ int execute_item(qsim *s, const PlanItem &it) {
         if (s->record_items) {
             feat = (long)s->pending_feats.size();
             s->pending_feats.resize(s->pending_feats.size() + kFeatures);
-            item_features(it, s->queue, s->n, s->prec, s->tc_enabled, &s->pending_feats[feat]);
+            item_features(it, s->queue, s->n, s->prec, s->tc_enabled, s->c128_df, &s->pending_feats[feat]);
         }
         const double host_ms = it.host_ms + std::chrono::duration<double, std::milli>(h1 - h0).count();
         s->pending.push_back({cls, ev0, bytes, feat, (float)host_ms});
@@ -190,7 +190,7 @@ int flush(qsim *s) {
     const std::vector<GateRec> &q = s->queue;
     MlpChoice ch;
     if (s->fusion == QSIM_FUSE_MLP && s->cost.loaded()) {
-        plan_mlp(q, s->n, s->prec, s->tc_enabled, block_kmax(s), s->cost, ch);
+        plan_mlp(q, s->n, s->prec, s->tc_enabled, s->c128_df, block_kmax(s), s->cost, ch);
         s->last_plan_predicted_ms = ch.predicted_ms;
     }
     if (s->fusion == QSIM_FUSE_NONE || (s->fusion == QSIM_FUSE_MLP && s->cost.loaded() && ch.kmax == 1)) {

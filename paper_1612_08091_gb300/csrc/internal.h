@@ -182,7 +182,9 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
 // block), or it.dtab (a diagonal block).
 void block_matrix(const std::vector<GateRec> &q, PlanItem &it);
 // Features of one plan item (kFeatures floats).
-void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, float *f);
+// df: complex128 launches use double-float arithmetic (feature 3 = 0.5)
+void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df,
+                   float *f);
 // Learned planner: the greedy plans for kmax = 2..kmax_limit (without block
 // matrices), each block fused or left as plain gates, whichever the cost
 // model predicts cheaper, against all gates plain (kmax 1); the plan with the
@@ -194,7 +196,7 @@ struct MlpChoice {
     std::vector<char> fuse;
     double predicted_ms = 0;
 };
-void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, int kmax_limit, const CostModel &cm,
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df, int kmax_limit, const CostModel &cm,
               MlpChoice &choice);
 // Gate gi as a plan item of its own.
 PlanItem single_item(const std::vector<GateRec> &q, int n, int gi);

@@ -334,11 +334,15 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
 //  4 width/5         5 gates in item/32         6 plain dense gate   7 plain phase gate
 //  8 plain diagonal  9 plain X permutation     10 controls/8        11 log2(fraction touched)/8
 // 12 lowest qubit/32 13 highest qubit/32       14 qubits below 5 /5  15 constant 1
-void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, float *f) {
+void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df,
+                   float *f) {
     for (int i = 0; i < kFeatures; ++i) f[i] = 0.f;
     f[0] = n / 32.f;
     f[1] = (prec == QSIM_C128 ? 16.f : 8.f) / 16.f;
     f[15] = 1.f;
+    // the executor's arithmetic: 1 for complex64 tensor-core blocks (below),
+    // 0.5 for complex128 in double-float arithmetic, 0 otherwise
+    if (prec == QSIM_C128 && df) f[3] = 0.5f;
     uint64_t mask = 0;
     if (it.fused && it.diag_block) {
         f[2] = 1.f;
@@ -348,7 +352,7 @@ void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int
         mask = it.dmask;
     } else if (it.fused) {
         f[2] = 1.f;
-        f[3] = (prec == QSIM_C64 && it.k >= 4 && n >= 12 && tc_enabled) ? 1.f : 0.f;
+        if (prec == QSIM_C64 && it.k >= 4 && n >= 12 && tc_enabled) f[3] = 1.f;
         f[4] = it.k / 5.f;
         f[5] = it.ngates / 32.f;
         for (int j = 0; j < it.k; ++j) mask |= 1ull << it.qubits[j];
@@ -405,11 +409,11 @@ PlanItem single_item(const std::vector<GateRec> &q, int n, int gi) {
     return it;
 }
 
-void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, int kmax_limit, const CostModel &cm,
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df, int kmax_limit, const CostModel &cm,
               MlpChoice &choice) {
     auto cost = [&](const PlanItem &it) {
         float f[kFeatures];
-        item_features(it, q, n, prec, tc_enabled, f);
+        item_features(it, q, n, prec, tc_enabled, df, f);
         return std::exp((double)cm.predict(f));
     };
     // every gate's cost as a plain launch, predicted once

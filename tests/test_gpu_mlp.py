@@ -69,6 +69,15 @@ def test_item_time_records(qs):
     assert np.all(ms > 0)
     np.testing.assert_allclose(feats[:, 0], n / 32.0)
     np.testing.assert_allclose(feats[:, 15], 1.0)
+    # feature 3: the executor's arithmetic (0.5: complex128 in double-float)
+    for df, want in ((True, 0.5), (False, 0.0)):
+        with qs.Simulator(16, precision="c128", fusion="greedy", kmax=4, c128_df=df) as sim:
+            sim.set_profiling(2)
+            sim.run(cg.random_u3_brickwork(16, 3, seed=1))
+            sim.flush()
+            feats, ms = sim.item_times()
+        assert len(ms) > 0
+        np.testing.assert_allclose(feats[:, 3], want)
 
 
 def _wall(qs, n, ops, fusion, model=None, reps=3):
