@@ -11,18 +11,20 @@
 // at register value x moves to register value f(x).
 //
 // A CTA works on tiles of 2^m register values x 2^c runs: the c lowest
-// qubits outside the register and the controls, chosen so that a tile holds
-// 2^13 amplitudes (or all of the register's 2^m) and a run at least 32
-// bytes (one DRAM sector) where such qubits exist.
-// f acts on every run alike, so a tile maps onto
+// qubits outside the register and the controls.  When the register holds a
+// lower qubit than any run qubit, the accesses are coalesced over the
+// register value and a tile holds 2^11 amplitudes (or all of the
+// register's 2^m), small enough for eight CTAs per SM; otherwise it holds
+// 2^13 and a run is at least 32 bytes (one DRAM sector) where such qubits
+// exist.  f acts on every run alike, so a tile maps onto
 // itself: the CTA loads it into shared memory (16 loads per thread in flight
 // for complex64, 8 for complex128), the index holding the lowest address bit
 // varying fastest so that the loads are coalesced whether the register holds
 // the low qubits or the high ones; it synchronises, and writes each position
 // from its source, out(v, r) = in(f^-1(v), r), so the stores are coalesced
-// too.  The register-value and run offsets and f^-1 come from a device
-// record (uint64 offsets, uint32 values) and are copied to shared memory
-// once per CTA.  m <= 12.
+// too.  The register-value offsets (two 64-entry tables for bits 0..5 and
+// 6..11 of the value), the run offsets and f^-1 come from a device record
+// and are copied to shared memory once per CTA.  m <= 12.
 //
 // Where the register and the controls lie above the 9 lowest qubits (8 for
 // complex128: 4 KB of contiguous amplitudes), the permutation
@@ -62,27 +64,28 @@ __device__ __forceinline__ void split_e(unsigned e, int m, int c, bool v_fast, u
     }
 }
 
+// six CTAs per SM for complex64 (40 registers, no spills), three for complex128
 template <typename Amp>
-__global__ void __launch_bounds__(kPermThreads) k_permute(Amp *__restrict__ psi, uint64_t ntiles, const InsertSpec ins,
+__global__ void __launch_bounds__(kPermThreads, sizeof(Amp) == 8 ? 6 : 3) k_permute(Amp *__restrict__ psi, uint64_t ntiles, const InsertSpec ins,
                                                           uint64_t cmask, int m, int c, int v_fast,
                                                           const uint64_t *__restrict__ goff,
                                                           const uint64_t *__restrict__ groff,
                                                           const uint32_t *__restrict__ gfinv) {
-    // shared memory: the tile, then the tables (offsets of register values
-    // and runs, f^-1), copied once per CTA
+    // shared memory: the tile, then the tables (register-value offsets as
+    // two 64-entry halves, run offsets, f^-1), copied once per CTA
     extern __shared__ unsigned char sm_raw[];
     Amp *buf = (Amp *)sm_raw;
     const unsigned T = 1u << (m + c), D = 1u << m, R = 1u << c;
-    uint64_t *off = (uint64_t *)(sm_raw + sizeof(Amp) * T);
-    uint64_t *roff = off + D;
+    uint64_t *olo = (uint64_t *)(sm_raw + sizeof(Amp) * T);
+    uint64_t *ohi = olo + 64;
+    uint64_t *roff = ohi + 64;
     uint32_t *finv = (uint32_t *)(roff + R);
-    for (unsigned i = threadIdx.x; i < D; i += kPermThreads) {
-        off[i] = goff[i];
-        finv[i] = gfinv[i];
-    }
+    for (unsigned i = threadIdx.x; i < 128; i += kPermThreads) olo[i] = goff[i];  // olo and ohi
+    for (unsigned i = threadIdx.x; i < D; i += kPermThreads) finv[i] = gfinv[i];
     for (unsigned i = threadIdx.x; i < R; i += kPermThreads) roff[i] = groff[i];
     __syncthreads();
-    constexpr int kL = sizeof(Amp) == 8 ? 16 : 8;  // loads in flight per thread per round
+    auto off = [&](unsigned v) { return olo[v & 63u] | ohi[v >> 6]; };
+    constexpr int kL = 8;  // loads in flight per thread per round
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint64_t base = insert_zeros(t, ins) | cmask;
         for (unsigned e0 = threadIdx.x; e0 < T; e0 += kL * kPermThreads) {
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(Amp *__restrict__ psi,
                 if (e < T) {
                     unsigned v, r;
                     split_e(e, m, c, v_fast, v, r);
-                    a[u] = psi[base + off[v] + roff[r]];
+                    a[u] = psi[base + off(v) + roff[r]];
                 }
             }
 #pragma unroll
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(Amp *__restrict__ psi,
             unsigned v, r;
             split_e(e, m, c, v_fast, v, r);
             const unsigned fv = finv[v];
-            psi[base + off[v] + roff[r]] = buf[v_fast ? ((r << m) | fv) : ((fv << c) | r)];
+            psi[base + off(v) + roff[r]] = buf[v_fast ? ((r << m) | fv) : ((fv << c) | r)];
         }
         __syncthreads();
     }
@@ -222,8 +225,15 @@ int permute(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qm
     // run qubits: the lowest outside the register and the controls
     const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
     const uint64_t free = all & ~(qmask | cmask);
-    const int cmin = sizeof(Amp) == 8 ? 2 : 1;  // runs of at least 32 bytes
-    int c = 13 - m < cmin ? cmin : 13 - m;      // tiles of 2^13 amplitudes
+    // the index holding the lowest address bit varies fastest: the register
+    // value when the register holds a lower qubit than any run qubit; then
+    // the loads and stores are coalesced over v and tiles of 2^11 amplitudes
+    // suffice (small tiles: many CTAs per SM); else runs of at least one
+    // 32-byte sector in tiles of 2^13
+    const bool v_fast = free == 0 || (qmask & (0ull - qmask)) < (free & (0ull - free));
+    const int cmin = v_fast ? 0 : (sizeof(Amp) == 8 ? 2 : 1);
+    const int tile_bits = v_fast ? 11 : 13;
+    int c = tile_bits - m < cmin ? cmin : tile_bits - m;
     while (c > 0 && ((size_t)sizeof(Amp) << (m + c)) > kPermSmemMax) --c;
     if (c > __builtin_popcountll(free)) c = __builtin_popcountll(free);
     int rbit[64], nr = 0;
@@ -232,26 +242,30 @@ int permute(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qm
     uint64_t rmask = 0;
     for (int j = 0; j < c; ++j) rmask |= 1ull << rbit[j];
     const int R = 1 << c;
-    std::vector<unsigned char> rec(sizeof(uint64_t) * (D + R) + sizeof(uint32_t) * D);
-    uint64_t *off = (uint64_t *)rec.data();
-    uint64_t *roff = off + D;
-    uint32_t *finv = (uint32_t *)(rec.data() + sizeof(uint64_t) * (D + R));
-    for (int v = 0; v < D; ++v) {
+    // record: olo[64], ohi[64] (register-value offsets of bits 0..5 and
+    // 6..11 of v), roff[R], finv[D]
+    std::vector<unsigned char> rec(sizeof(uint64_t) * (128 + R) + sizeof(uint32_t) * D);
+    uint64_t *olo = (uint64_t *)rec.data();
+    uint64_t *ohi = olo + 64;
+    uint64_t *roff = ohi + 64;
+    uint32_t *finv = (uint32_t *)(rec.data() + sizeof(uint64_t) * (128 + R));
+    auto reg_off = [&](int v) {
         uint64_t a = 0;
         for (int j = 0; j < m; ++j)
             if ((v >> j) & 1) a |= 1ull << qubits[j];
-        off[v] = a;
-        finv[perm[v]] = (uint32_t)v;
+        return a;
+    };
+    for (int v = 0; v < 64; ++v) {
+        olo[v] = reg_off(v & (D - 1));
+        ohi[v] = (v << 6) < D ? reg_off(v << 6) : 0;
     }
+    for (int v = 0; v < D; ++v) finv[perm[v]] = (uint32_t)v;
     for (int r = 0; r < R; ++r) {
         uint64_t a = 0;
         for (int j = 0; j < c; ++j)
             if ((r >> j) & 1) a |= 1ull << rbit[j];
         roff[r] = a;
     }
-    // the index holding the lowest address bit varies fastest
-    const uint64_t low = (qmask | rmask) & (0ull - (qmask | rmask));
-    const int v_fast = (low & qmask) ? 1 : 0;
     unsigned char *dev = nullptr;
     int rc = stage_operand(s, rec.data(), rec.size(), &dev);
     if (rc) return rc;
@@ -261,19 +275,19 @@ int permute(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qm
     for (int b = 0; b < 64; ++b)
         if ((fixed >> b) & 1ull) ins.pos[ins.m++] = b;
     const uint64_t ntiles = 1ull << (n - ins.m);
-    const size_t smem = (sizeof(Amp) << (m + c)) + sizeof(uint64_t) * (D + R) + sizeof(uint32_t) * D;
+    const size_t smem = (sizeof(Amp) << (m + c)) + sizeof(uint64_t) * (128 + R) + sizeof(uint32_t) * D;
     static bool attr[2][64] = {{false}};
     const int which = sizeof(Amp) == 8 ? 0 : 1;
     if (s->device >= 0 && s->device < 64 && !attr[which][s->device]) {
         cudaError_t e = cudaFuncSetAttribute(k_permute<Amp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kPermSmemMax + (size_t)12 * 4096 + 8 * 4096));
+                                             (int)(kPermSmemMax + sizeof(uint64_t) * (128 + 4096) + 4 * 4096));
         if (e != cudaSuccess) return cuda_err(s, e, "permutation kernel attribute");
         attr[which][s->device] = true;
     }
     const uint64_t grid = ntiles < (uint64_t)kSMs * 8 ? ntiles : (uint64_t)kSMs * 8;
     k_permute<Amp><<<(unsigned)grid, kPermThreads, smem, s->stream>>>(
-        (Amp *)s->state, ntiles, ins, cmask, m, c, v_fast, (const uint64_t *)dev, (const uint64_t *)dev + D,
-        (const uint32_t *)(dev + sizeof(uint64_t) * (D + R)));
+        (Amp *)s->state, ntiles, ins, cmask, m, c, v_fast ? 1 : 0, (const uint64_t *)dev,
+        (const uint64_t *)dev + 128, (const uint32_t *)(dev + sizeof(uint64_t) * (128 + R)));
     s->stats.launches++;
     return cuda_err(s, cudaGetLastError(), "permutation launch");
 }
