@@ -340,6 +340,17 @@ const char *sim_batch_last_error(const qsim_batch *b);
  * it before any stream capture. */
 int qsim_probs_all_noalloc(const void *state, int n, int precision, double *out, void *stream);
 
+/* Self-test of the device-side bounded wait.  Every kernel that waits on an
+ * mbarrier (bulk copies, tensor-core commits) polls it at most a fixed
+ * number of times; on time-out it raises a flag that the host reports as
+ * QSIM_ETIMEOUT, and the context stays usable.  This call runs that wait on
+ * a barrier that nothing arrives on, with at most `limit` polls (1..2^20),
+ * on `stream` (cudaStream_t, NULL = legacy default).  Returns QSIM_ETIMEOUT
+ * (the expected outcome) and the kernel's event-timed duration in *ms (may
+ * be NULL); QSIM_EINVAL for a limit outside the range, QSIM_ENOMEM or
+ * QSIM_ECUDA if the 4-byte flag cannot be allocated or a call fails. */
+int qsim_selftest_wait_timeout(unsigned int limit, void *stream, double *ms);
+
 /* One-line description of the last failure on this handle ("" if none). */
 const char *sim_last_error(const qsim *s);
 

@@ -16,8 +16,11 @@ namespace qsim_tc {
 
 // Upper bound on the polls of one mbarrier wait.  Every wait in the block
 // kernels gives up after it, raises an error flag and lets the kernel free
-// its tensor memory and return.
-constexpr uint32_t kWaitLimit = 1u << 24;
+// its tensor memory and return.  A poll of a barrier that never completes
+// took 3.9 us on GB300 (qsim_selftest_wait_timeout), so 2^18 polls give up
+// after about one second; the copies and tensor-core commits waited for
+// take microseconds.
+constexpr uint32_t kWaitLimit = 1u << 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -37,9 +40,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; returns false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+// Bounded wait (at most `limit` polls); returns false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

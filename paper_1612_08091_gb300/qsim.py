@@ -107,8 +107,19 @@ def load():
     lib.sim_last_error.restype = ctypes.c_char_p
     lib.qsim_build_info.argtypes = []
     lib.qsim_build_info.restype = ctypes.c_char_p
+    lib.qsim_selftest_wait_timeout.argtypes = [ctypes.c_uint, P, DP]
+    lib.qsim_selftest_wait_timeout.restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def selftest_wait_timeout(limit, stream=None):
+    """Run the device's bounded mbarrier wait on a barrier nothing arrives
+    on (qsim_selftest_wait_timeout); returns (status name, kernel ms)."""
+    lib = load()
+    ms = ctypes.c_double()
+    code = lib.qsim_selftest_wait_timeout(int(limit), ctypes.c_void_p(stream), ctypes.byref(ms))
+    return STATUS.get(code, str(code)), ms.value
 
 
 def _ints(seq):
