@@ -26,20 +26,40 @@ namespace {
 template <typename Amp> struct Mat1 { Amp m[4]; };
 template <typename Amp, int K> struct MatK { Amp m[(1 << K) * (1 << K)]; uint64_t off[1 << K]; };
 
+// One-qubit, phase and X kernels: each thread takes kGroups groups, g =
+// block * 256 kGroups + u * 256 + thread (u < kGroups), and issues all their
+// loads before any arithmetic, so that 4 to 8 amplitudes per thread are in
+// flight (one group per thread left too few bytes in flight for HBM).
+constexpr int kGroups = 4;
+constexpr int kPhaseGroups = 8;  // the phase kernel loads one amplitude per group
+
+inline unsigned blocks_for(uint64_t work, int threads) {
+    return (unsigned)((work + (uint64_t)threads - 1) / (uint64_t)threads);
+}
+
 template <typename Amp>
 __global__ void __launch_bounds__(256) k_dense1(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
                                                 uint64_t cmask, uint64_t tbit, const Mat1<Amp> M) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t i0 = insert_zeros(g, ins) | cmask;
-    const uint64_t i1 = i0 | tbit;
-    const Amp a = psi[i0], b = psi[i1];
-    Amp na = cmul(M.m[0], a);
-    na = cfma(M.m[1], b, na);
-    Amp nb = cmul(M.m[2], a);
-    nb = cfma(M.m[3], b, nb);
-    psi[i0] = na;
-    psi[i1] = nb;
+    const uint64_t g0 = blockIdx.x * (uint64_t)(256 * kGroups) + threadIdx.x;
+    uint64_t i0[kGroups];
+    Amp a[kGroups], b[kGroups];
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            i0[u] = insert_zeros(g0 + u * 256, ins) | cmask;
+            a[u] = psi[i0[u]];
+            b[u] = psi[i0[u] | tbit];
+        }
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            Amp na = cmul(M.m[0], a[u]);
+            na = cfma(M.m[1], b[u], na);
+            Amp nb = cmul(M.m[2], a[u]);
+            nb = cfma(M.m[3], b[u], nb);
+            psi[i0[u]] = na;
+            psi[i0[u] | tbit] = nb;
+        }
 }
 
 template <typename Amp, int K>
@@ -64,68 +84,123 @@ __global__ void __launch_bounds__(128) k_denseK(Amp *__restrict__ psi, uint64_t 
 template <typename Amp>
 __global__ void __launch_bounds__(256) k_phase(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
                                                uint64_t mask, Amp z) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t i = insert_zeros(g, ins) | mask;
-    psi[i] = cmul(z, psi[i]);
+    const uint64_t g0 = blockIdx.x * (uint64_t)(256 * kPhaseGroups) + threadIdx.x;
+    uint64_t i[kPhaseGroups];
+    Amp v[kPhaseGroups];
+#pragma unroll
+    for (int u = 0; u < kPhaseGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            i[u] = insert_zeros(g0 + u * 256, ins) | mask;
+            v[u] = psi[i[u]];
+        }
+#pragma unroll
+    for (int u = 0; u < kPhaseGroups; ++u)
+        if (g0 + u * 256 < ngroups) psi[i[u]] = cmul(z, v[u]);
 }
 
 template <typename Amp>
 __global__ void __launch_bounds__(256) k_diag1(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
                                                uint64_t cmask, uint64_t tbit, Amp d0, Amp d1) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t i0 = insert_zeros(g, ins) | cmask;
-    const uint64_t i1 = i0 | tbit;
-    psi[i0] = cmul(d0, psi[i0]);
-    psi[i1] = cmul(d1, psi[i1]);
+    const uint64_t g0 = blockIdx.x * (uint64_t)(256 * kGroups) + threadIdx.x;
+    uint64_t i0[kGroups];
+    Amp a[kGroups], b[kGroups];
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            i0[u] = insert_zeros(g0 + u * 256, ins) | cmask;
+            a[u] = psi[i0[u]];
+            b[u] = psi[i0[u] | tbit];
+        }
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            psi[i0[u]] = cmul(d0, a[u]);
+            psi[i0[u] | tbit] = cmul(d1, b[u]);
+        }
 }
 
 template <typename Amp>
 __global__ void __launch_bounds__(256) k_x(Amp *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
                                            uint64_t cmask, uint64_t tbit) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t i0 = insert_zeros(g, ins) | cmask;
-    const uint64_t i1 = i0 | tbit;
-    const Amp a = psi[i0], b = psi[i1];
-    psi[i0] = b;
-    psi[i1] = a;
+    const uint64_t g0 = blockIdx.x * (uint64_t)(256 * kGroups) + threadIdx.x;
+    uint64_t i0[kGroups];
+    Amp a[kGroups], b[kGroups];
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            i0[u] = insert_zeros(g0 + u * 256, ins) | cmask;
+            a[u] = psi[i0[u]];
+            b[u] = psi[i0[u] | tbit];
+        }
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            psi[i0[u]] = b[u];
+            psi[i0[u] | tbit] = a[u];
+        }
 }
 
 // complex128 with double-float arithmetic (df128.cuh): one-qubit dense,
-// diagonal and phase gates
+// diagonal and phase gates, kGroups (kPhaseGroups) groups per thread
 struct MatDF {
     qsim_df::C2 m[4];
 };
 
 __global__ void __launch_bounds__(256) k_dense1_df(double2 *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
                                                    uint64_t cmask, uint64_t tbit, const MatDF M) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t i0 = insert_zeros(g, ins) | cmask;
-    const uint64_t i1 = i0 | tbit;
-    const qsim_df::C2 a = qsim_df::split(psi[i0]), b = qsim_df::split(psi[i1]);
-    psi[i0] = qsim_df::to_double(qsim_df::cdot2(M.m[0], a, M.m[1], b));
-    psi[i1] = qsim_df::to_double(qsim_df::cdot2(M.m[2], a, M.m[3], b));
+    const uint64_t g0 = blockIdx.x * (uint64_t)(256 * kGroups) + threadIdx.x;
+    uint64_t i0[kGroups];
+    double2 a[kGroups], b[kGroups];
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            i0[u] = insert_zeros(g0 + u * 256, ins) | cmask;
+            a[u] = psi[i0[u]];
+            b[u] = psi[i0[u] | tbit];
+        }
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            const qsim_df::C2 x = qsim_df::split(a[u]), y = qsim_df::split(b[u]);
+            psi[i0[u]] = qsim_df::to_double(qsim_df::cdot2(M.m[0], x, M.m[1], y));
+            psi[i0[u] | tbit] = qsim_df::to_double(qsim_df::cdot2(M.m[2], x, M.m[3], y));
+        }
 }
 
 __global__ void __launch_bounds__(256) k_diag1_df(double2 *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
                                                   uint64_t cmask, uint64_t tbit, const MatDF M) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t i0 = insert_zeros(g, ins) | cmask;
-    const uint64_t i1 = i0 | tbit;
-    psi[i0] = qsim_df::to_double(qsim_df::cmul(M.m[0], qsim_df::split(psi[i0])));
-    psi[i1] = qsim_df::to_double(qsim_df::cmul(M.m[3], qsim_df::split(psi[i1])));
+    const uint64_t g0 = blockIdx.x * (uint64_t)(256 * kGroups) + threadIdx.x;
+    uint64_t i0[kGroups];
+    double2 a[kGroups], b[kGroups];
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            i0[u] = insert_zeros(g0 + u * 256, ins) | cmask;
+            a[u] = psi[i0[u]];
+            b[u] = psi[i0[u] | tbit];
+        }
+#pragma unroll
+    for (int u = 0; u < kGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            psi[i0[u]] = qsim_df::to_double(qsim_df::cmul(M.m[0], qsim_df::split(a[u])));
+            psi[i0[u] | tbit] = qsim_df::to_double(qsim_df::cmul(M.m[3], qsim_df::split(b[u])));
+        }
 }
 
 __global__ void __launch_bounds__(256) k_phase_df(double2 *__restrict__ psi, uint64_t ngroups, const InsertSpec ins,
                                                   uint64_t mask, const MatDF M) {
-    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t i = insert_zeros(g, ins) | mask;
-    psi[i] = qsim_df::to_double(qsim_df::cmul(M.m[3], qsim_df::split(psi[i])));
+    const uint64_t g0 = blockIdx.x * (uint64_t)(256 * kPhaseGroups) + threadIdx.x;
+    uint64_t i[kPhaseGroups];
+    double2 v[kPhaseGroups];
+#pragma unroll
+    for (int u = 0; u < kPhaseGroups; ++u)
+        if (g0 + u * 256 < ngroups) {
+            i[u] = insert_zeros(g0 + u * 256, ins) | mask;
+            v[u] = psi[i[u]];
+        }
+#pragma unroll
+    for (int u = 0; u < kPhaseGroups; ++u)
+        if (g0 + u * 256 < ngroups) psi[i[u]] = qsim_df::to_double(qsim_df::cmul(M.m[3], qsim_df::split(v[u])));
 }
 
 // complex128 k-qubit dense gate or fused block in double-float arithmetic:
@@ -183,20 +258,20 @@ bool gate_df(qsim *s, const GateRec &g) {
     case GK_DENSE: {
         spec(g.tmask | g.cmask);
         const uint64_t ng = 1ull << (s->n - ins.m);
-        k_dense1_df<<<(unsigned)((ng + 255) / 256), 256, 0, s->stream>>>(psi, ng, ins, g.cmask, tbit, M);
+        k_dense1_df<<<blocks_for(ng, 256 * kGroups), 256, 0, s->stream>>>(psi, ng, ins, g.cmask, tbit, M);
         return true;
     }
     case GK_DIAG1: {
         spec(g.tmask | g.cmask);
         const uint64_t ng = 1ull << (s->n - ins.m);
-        k_diag1_df<<<(unsigned)((ng + 255) / 256), 256, 0, s->stream>>>(psi, ng, ins, g.cmask, tbit, M);
+        k_diag1_df<<<blocks_for(ng, 256 * kGroups), 256, 0, s->stream>>>(psi, ng, ins, g.cmask, tbit, M);
         return true;
     }
     case GK_PHASE: {
         const uint64_t mask = g.tmask | g.cmask;
         spec(mask);
         const uint64_t ng = 1ull << (s->n - ins.m);
-        k_phase_df<<<(unsigned)((ng + 255) / 256), 256, 0, s->stream>>>(psi, ng, ins, mask, M);
+        k_phase_df<<<blocks_for(ng, 256 * kPhaseGroups), 256, 0, s->stream>>>(psi, ng, ins, mask, M);
         return true;
     }
     default:
@@ -215,10 +290,6 @@ InsertSpec make_spec(uint64_t mask) {
 inline double2 to_amp(cd z, double2 *) { return make_double2(z.real(), z.imag()); }
 inline float2 to_amp(cd z, float2 *) { return make_float2((float)z.real(), (float)z.imag()); }
 template <typename Amp> Amp amp(cd z) { return to_amp(z, (Amp *)nullptr); }
-
-inline unsigned blocks_for(uint64_t work, int threads) {
-    return (unsigned)((work + (uint64_t)threads - 1) / (uint64_t)threads);
-}
 
 template <int K>
 int dense_k_df(qsim *s, const int *targets, uint64_t cmask, const cd *m) {
@@ -272,20 +343,20 @@ int gate_plain(qsim *s, const GateRec &g) {
         const uint64_t mask = g.tmask | g.cmask;
         const InsertSpec ins = make_spec(mask);
         const uint64_t ngroups = 1ull << (s->n - ins.m);
-        k_phase<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, mask, amp<Amp>(g.m[3]));
+        k_phase<Amp><<<blocks_for(ngroups, 256 * kPhaseGroups), 256, 0, s->stream>>>(psi, ngroups, ins, mask, amp<Amp>(g.m[3]));
         break;
     }
     case GK_DIAG1: {
         const InsertSpec ins = make_spec(g.tmask | g.cmask);
         const uint64_t ngroups = 1ull << (s->n - ins.m);
-        k_diag1<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit,
+        k_diag1<Amp><<<blocks_for(ngroups, 256 * kGroups), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit,
                                                                         amp<Amp>(g.m[0]), amp<Amp>(g.m[3]));
         break;
     }
     case GK_X: {
         const InsertSpec ins = make_spec(g.tmask | g.cmask);
         const uint64_t ngroups = 1ull << (s->n - ins.m);
-        k_x<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit);
+        k_x<Amp><<<blocks_for(ngroups, 256 * kGroups), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit);
         break;
     }
     default: {
@@ -295,7 +366,7 @@ int gate_plain(qsim *s, const GateRec &g) {
             for (int i = 0; i < 4; ++i) M.m[i] = amp<Amp>(g.m[i]);
             const InsertSpec ins = make_spec(g.tmask | g.cmask);
             const uint64_t ngroups = 1ull << (s->n - ins.m);
-            k_dense1<Amp><<<blocks_for(ngroups, 256), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit, M);
+            k_dense1<Amp><<<blocks_for(ngroups, 256 * kGroups), 256, 0, s->stream>>>(psi, ngroups, ins, g.cmask, tbit, M);
             break;
         }
         case 2: return dense_k<Amp, 2>(s, g.targets, g.cmask, g.m.data());

@@ -121,18 +121,28 @@ constexpr int kCycDepth = 8;  // loads in flight per thread along a cycle
 
 // coff: the cycles' elements as register offsets in 16-byte units, cycle
 // by cycle, f(e_i) = e_{i+1}; cstart[j]: first element of cycle j (ncyc + 1
-// entries); a task is (cycle, slice) with the slice fastest.
+// entries); a task is (cycle, slice) with the slice fastest.  The current
+// cycle's offsets are copied to shared memory (dynamic, 8 bytes times the
+// longest cycle), so the address of each step is one shared-memory read.
 __global__ void __launch_bounds__(kCycThreads) k_permute_cycles(float4 *__restrict__ psi16, const InsertSpec ins,
                                                                 uint64_t cmask16, const uint64_t *__restrict__ coff,
                                                                 const uint32_t *__restrict__ cstart, uint32_t ncyc,
                                                                 uint64_t nslices, int amp_shift) {
+    extern __shared__ uint64_t s_e[];
     const uint64_t ntasks = (uint64_t)ncyc * nslices;
+    uint32_t loaded = 0xffffffffu;  // the cycle whose offsets are in s_e
     for (uint64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
         const uint32_t cyc = (uint32_t)(task / nslices);
         const uint64_t sl = task - (uint64_t)cyc * nslices;
         const uint32_t b0 = cstart[cyc];
         const int L = (int)(cstart[cyc + 1] - b0);
-        const uint64_t *e = coff + b0;
+        if (cyc != loaded) {  // uniform over the CTA
+            __syncthreads();
+            for (int i = threadIdx.x; i < L; i += kCycThreads) s_e[i] = coff[b0 + i];
+            __syncthreads();
+            loaded = cyc;
+        }
+        const uint64_t *e = s_e;
         // this thread's 16 bytes of the slice at register value 0
         float4 *p = psi16 + (((insert_zeros(sl << (8 + amp_shift), ins) >> amp_shift) | cmask16) + threadIdx.x);
         const float4 first = p[e[L - 1]];
@@ -211,7 +221,8 @@ int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint
     const uint64_t ntasks = (uint64_t)ncyc * nslices;
     // 64 registers a thread: four CTAs of 256 threads resident per SM
     const uint64_t grid = ntasks < (uint64_t)kSMs * 4 ? ntasks : (uint64_t)kSMs * 4;
-    k_permute_cycles<<<(unsigned)grid, kCycThreads, 0, s->stream>>>(
+    const size_t smem = sizeof(uint64_t) * cycles[0].size();  // the longest cycle (<= 2^12 entries)
+    k_permute_cycles<<<(unsigned)grid, kCycThreads, smem, s->stream>>>(
         (float4 *)s->state, ins, cmask >> amp_shift, (const uint64_t *)dev,
         (const uint32_t *)(dev + sizeof(uint64_t) * total), (uint32_t)ncyc, nslices, amp_shift);
     s->stats.launches++;
