@@ -483,7 +483,14 @@ def run_ours(args):
                 pst = ps.stats()
             ps_s = a.elapsed_time(b) / 1e3
             torch.cuda.empty_cache()
-            return {"value": amp_updates(sample, n) / ps_s, "unit": UNIT, "precision": "c128",
+            rate = amp_updates(sample, n) / ps_s
+            # every logical amplitude update of a plain complex128 gate reads
+            # and writes 16 bytes: roofline = HBM bandwidth / 32 bytes
+            roof = None
+            if fusion == "none":
+                roof = {"value": peak * 1e9 / 32.0, "unit": UNIT, "frac": rate * 32.0 / (peak * 1e9),
+                        "what": "measured HBM bandwidth / 32 bytes per logical amplitude update"}
+            return {"value": rate, "unit": UNIT, "precision": "c128", "hbm_roofline": roof,
                     "arithmetic": "double-float (fp32 pairs, ~2^-45 relative)" if df else "fp64",
                     "fusion": fusion if fusion == "none" else "%s, kmax %d" % (fusion, kmax),
                     "sample": "first %d gates of the same %d-qubit circuit, %s"

@@ -59,7 +59,7 @@ enum qsim_status {
     QSIM_ENONFINITE = 6,  /* matrix entry or amplitude is NaN or infinite */
     QSIM_ECUDA = 7,       /* a CUDA call failed; see sim_last_error */
     QSIM_ETIMEOUT = 8,    /* a bounded device wait gave up */
-    QSIM_ENOTSUP = 9      /* combination not supported by this build */
+    QSIM_ENOTSUP = 9      /* combination not supported by the library */
 };
 
 enum qsim_precision {

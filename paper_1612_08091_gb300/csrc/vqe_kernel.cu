@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
             __syncthreads();
             bool permuted = false;  // src holds the state before a pending ladder permutation
             bool failed = false;
-            // wait for the current copy phase; uniform verdict over the CTA
+            // wait for the current copy phase; the result is uniform over the CTA
             auto wait_copies = [&]() {
                 bool ok = mbar_wait(s_bar, s_phase);
                 if (!ok) ok = mbar_wait(s_bar, s_phase);  // give copies in flight a second bound
