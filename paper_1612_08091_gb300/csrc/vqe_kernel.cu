@@ -247,6 +247,23 @@ __device__ void build_phase_table(float2 *t, int kb, const float2 *ph, float2 ex
 // CTAs per SM so that one CTA's loads, arithmetic and stores overlap the
 // other's (measured faster than one CTA of 512 threads per SM with
 // double-buffered copies: 44.9 against 41.0 ms for the 4096-circuit batch).
+// The global-memory kernel's chunk size (2^12 amplitudes; a pair of chunks
+// is 64 KB of shared memory) and block size.
+constexpr int kGlobalThreads = 256;
+constexpr int kGlobalBits = 12;
+
+// Position in a pair buffer (source order, after a ladder permutation) of
+// logical element e: bits 0..g-1 are gl = (e ^ e << 1) mod 2^g, bit g is
+// parity(gl) ^ (e >> g).  The map is linear over GF(2), so for the store's
+// elements e = tid ^ (j << 8) it is pair_perm(tid) ^ pair_perm(j << 8), the
+// second term a compile-time constant.
+__host__ __device__ constexpr unsigned pair_perm(unsigned e) {
+    const unsigned gl = (e ^ (e << 1)) & ((1u << kGlobalBits) - 1u);
+    unsigned par = 0;
+    for (int b = 0; b < kGlobalBits; ++b) par ^= (gl >> b) & 1u;
+    return ((par ^ (e >> kGlobalBits)) << kGlobalBits) | gl;
+}
+
 // Order of the pair pass's 12 rotations, taken four at a time.  A group's
 // pivot bits are the same in all lanes' addresses at each access, so a group
 // holding qubits 0..3 (the bank bits of 8-byte elements) would be a 16-way
@@ -367,7 +384,8 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
             // each destination element at its source position.  Every wait
             // is bounded; on time-out the CTA raises the error flag and
             // stops.
-            const int g = A.g, h = n - g, lowrun = g - h;  // h >= 1 and lowrun >= 0 (n <= 2g)
+            constexpr int g = kGlobalBits;
+            const int h = n - g, lowrun = g - h;  // h >= 1 and lowrun >= 0 (n <= 2g)
             float2 *src = A.gbuf + (size_t)blockIdx.x * 2 * A.gstride;
             float2 *dst = src + A.gstride;
             const unsigned G = 1u << g, nchunks = 1u << h, hmask = nchunks - 1u, gmask = G - 1u;
@@ -416,14 +434,26 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                 const unsigned gl = ((e ^ (e << 1)) & gmask);
                 return ((((unsigned)__popc(gl) & 1u) ^ (e >> g)) << g) | gl;
             };
-            // phased: the layer's phases and flips of qubits 0..g-1 (flo)
+            // Destination chunks pr (logical elements e < G) and pr ^ hmask,
+            // written whole: this thread's elements are e = tid + j T, each
+            // read at pair_pos(e ^ flo) (linear: a per-thread part and a
+            // compile-time part); phased: the layer's phases of qubits
+            // 0..g-1 and flips (flo), the low seven phase bits constant per
+            // thread.
             auto store_pair = [&](float2 *to, unsigned pr, bool phased, unsigned flo) {
-                const unsigned hb = pr ^ hmask;
-                for (unsigned e = threadIdx.x; e < 2 * G; e += T) {
-                    const unsigned o = e & gmask, of = o ^ flo;
-                    float2 v = sm[pair_pos(e ^ flo)];
-                    if (phased) v = cmul(v, cmul(s_tlo[of & 127u], s_thi[of >> 7]));
-                    to[((size_t)(e < G ? pr : hb) << g) | o] = v;
+                static_assert(T == 256 && (2 << g) % T == 0, "store_pair assumes 256 threads");
+                const unsigned tf = threadIdx.x ^ flo;
+                const unsigned pt = permuted ? pair_perm(tf) : tf;
+                float2 *dst0 = to + ((size_t)pr << g) + threadIdx.x;
+                float2 *dst1 = to + ((size_t)(pr ^ hmask) << g) + threadIdx.x;
+                const float2 tlo = s_tlo[tf & 127u];
+                const unsigned thi0 = (tf >> 7) & 31u;
+#pragma unroll
+                for (int j = 0; j < (2 << g) / T; ++j) {
+                    const unsigned cj = (unsigned)j << 8;  // e = tid | j << 8
+                    float2 v = sm[pt ^ (permuted ? pair_perm(cj) : cj)];
+                    if (phased) v = cmul(v, cmul(tlo, s_thi[thi0 ^ ((cj >> 7) & 31u)]));
+                    ((j < G / T) ? dst0 : dst1)[cj & gmask] = v;
                 }
                 __syncthreads();
             };
@@ -592,8 +622,6 @@ VqeKernel kernel_for(int threads) {
 // n - 12 qubits, 2 KB for n = 20, 32 KB for n = 24), two CTAs per SM
 // (measured faster than three, which force the registers down to 80 and
 // spill).
-constexpr int kGlobalThreads = 256;
-constexpr int kGlobalBits = 12;
 static_assert(kGlobalBits == 12, "kPairOrder lists the 12 chunk qubits");
 constexpr int kMaxBatchQubits = 2 * kGlobalBits;  // n <= 2 g: a tile's runs are whole amplitudes
 size_t global_smem(int nmax) {
