@@ -271,6 +271,56 @@ __host__ __device__ constexpr unsigned pair_perm(unsigned e) {
 // 2-, 2- and 4-way.
 __constant__ int kPairOrder[12] = {0, 4, 5, 6, 1, 7, 8, 9, 2, 3, 10, 11};
 
+// One group of the pair pass with compile-time qubits Q0 < Q1 < Q2 < Q3 (a
+// group of kPairOrder): the 2^13-element pair buffer x holds 512 groups of
+// 16 elements, base (zeros at the pivots Q0..Q3) XOR any subset of the masks
+// (PERM ? 3 : 1) << Qj; rotation j uses r[j].t, negated where the base's
+// bits 0..Qj have odd parity (PERM: source order, see gates_blocked).
+template <bool PERM, int Q0, int Q1, int Q2, int Q3>
+__device__ __forceinline__ void pair_group(float2 *x, const Rot *r) {
+    static_assert(Q0 < Q1 && Q1 < Q2 && Q2 < Q3, "pivots in ascending order");
+    constexpr unsigned W = PERM ? 3u : 1u;
+    constexpr unsigned M0 = W << Q0, M1 = W << Q1, M2 = W << Q2, M3 = W << Q3;
+    const float t0 = r[0].t, t1 = r[1].t, t2 = r[2].t, t3 = r[3].t;
+    for (unsigned gi = threadIdx.x; gi < (1u << (kGlobalBits + 1 - 4)); gi += kGlobalThreads) {
+        unsigned base = gi;
+        base = ((base >> Q0) << (Q0 + 1)) | (base & ((1u << Q0) - 1u));
+        base = ((base >> Q1) << (Q1 + 1)) | (base & ((1u << Q1) - 1u));
+        base = ((base >> Q2) << (Q2 + 1)) | (base & ((1u << Q2) - 1u));
+        base = ((base >> Q3) << (Q3 + 1)) | (base & ((1u << Q3) - 1u));
+        float2 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            v[k] = x[base ^ ((k & 1) ? M0 : 0u) ^ ((k & 2) ? M1 : 0u) ^ ((k & 4) ? M2 : 0u) ^ ((k & 8) ? M3 : 0u)];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = j == 0 ? Q0 : j == 1 ? Q1 : j == 2 ? Q2 : Q3;
+            float t = j == 0 ? t0 : j == 1 ? t1 : j == 2 ? t2 : t3;
+            if (PERM && (__popc(base & ((2u << q) - 1u)) & 1)) t = -t;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if ((k >> j) & 1) continue;
+                const int k1 = k | (1 << j);
+                const float2 a = v[k], b = v[k1];
+                v[k] = make_float2(fmaf(-t, b.x, a.x), fmaf(-t, b.y, a.y));
+                v[k1] = make_float2(fmaf(t, a.x, b.x), fmaf(t, a.y, b.y));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            x[base ^ ((k & 1) ? M0 : 0u) ^ ((k & 2) ? M1 : 0u) ^ ((k & 4) ? M2 : 0u) ^ ((k & 8) ? M3 : 0u)] = v[k];
+    }
+    __syncthreads();
+}
+
+// The pair pass's 12 rotations (r in kPairOrder) on a pair buffer.
+template <bool PERM>
+__device__ __forceinline__ void pair_gates(float2 *x, const Rot *r) {
+    pair_group<PERM, 0, 4, 5, 6>(x, r);
+    pair_group<PERM, 1, 7, 8, 9>(x, r + 4);
+    pair_group<PERM, 2, 3, 10, 11>(x, r + 8);
+}
+
 template <int T, bool GLOBAL>
 __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A) {
     constexpr int kRegAmps = RegAmps<T>::value;
@@ -484,13 +534,9 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                 build_phase_table(s_tlo, 7, s_ph, s_gph);
                 build_phase_table(s_thi, g - 7, s_ph + 7, make_float2(1.f, 0.f));
                 build_phase_table(s_ttop, h, s_ph + g, make_float2(1.f, 0.f));
-                // rotation masks of the pair pass (in the pair buffer's order),
-                // grouped as kPairOrder
-                if (threadIdx.x < (unsigned)g) {
-                    const int q = kPairOrder[threadIdx.x];
-                    s_mask[threadIdx.x] = (permuted ? 3u : 1u) << q;
-                    s_rotp[threadIdx.x] = s_rot[q];
-                }
+                // the pair pass's rotations in kPairOrder; the top-qubit
+                // pass's masks (tile bits lowrun..g-1)
+                if (threadIdx.x < (unsigned)g) s_rotp[threadIdx.x] = s_rot[kPairOrder[threadIdx.x]];
                 if (threadIdx.x < (unsigned)h) s_mask[g + threadIdx.x] = 1u << (lowrun + threadIdx.x);
                 __syncthreads();
                 // pair pass: src (through the pending permutation) -> dst, RY
@@ -501,7 +547,10 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                         failed = true;
                         break;
                     }
-                    gates_blocked(sm, g + 1, s_mask, s_rotp, g, permuted);
+                    if (permuted)
+                        pair_gates<true>(sm, s_rotp);
+                    else
+                        pair_gates<false>(sm, s_rotp);
                     store_pair(dst, pr, true, s_flip & gmask);
                 }
                 // high pass on dst, in place: RY on the top qubits, then
