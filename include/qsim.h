@@ -206,8 +206,9 @@ int sim_reset_stats(qsim *s);
  * "gate_dense", "gate_phase", "gate_diag", "gate_x" (plain gates),
  * "block_tc" (4- and 5-qubit blocks on the tensor cores), "block_tc6"
  * (6-qubit blocks), "block_dense" (blocks on CUDA cores), "block_diag"
- * (diagonal blocks), "permute" and "permute_cycles" (sim_apply_permutation:
- * tiled through shared memory, or along the cycles of f). */
+ * (diagonal blocks), "permute", "permute_cycles" and "permute_cycles_bulk"
+ * (sim_apply_permutation: tiled through shared memory, or along the cycles
+ * of f through registers or through the bulk-copy engine). */
 typedef struct qsim_kernel_time {
     char name[24];
     uint64_t launches;

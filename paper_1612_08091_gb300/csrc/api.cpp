@@ -66,7 +66,8 @@ double gate_bytes(const qsim *s, const GateRec &g) {
 }
 
 const char *kClassName[KC_COUNT] = {"gate_dense", "gate_phase", "gate_diag",  "gate_x",  "block_tc",
-                                    "block_dense", "block_diag", "block_tc6", "permute", "permute_cycles"};
+                                    "block_dense", "block_diag", "block_tc6", "permute", "permute_cycles",
+                                    "permute_cycles_bulk"};
 
 int harvest(qsim *s) {
     if (s->pending.empty()) return QSIM_OK;
@@ -428,13 +429,14 @@ int sim_apply_permutation(qsim *s, const uint64_t *perm, const int *qubits, int 
     if ((rc = flush(s))) return rc;
     size_t ev0 = 0, ev1 = 0;
     if (s->profiling && (rc = record_event(s, &ev0))) return rc;
-    bool cycles = false;
-    rc = launch_permutation(s, perm, qubits, m, qmask, cmask, &cycles);
+    int kind = 0;
+    rc = launch_permutation(s, perm, qubits, m, qmask, cmask, &kind);
     if (rc) return rc;
     const double bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n - c);
     if (s->profiling) {
         if ((rc = record_event(s, &ev1))) return rc;
-        s->pending.push_back({cycles ? KC_PERMUTE_CYCLES : KC_PERMUTE, ev0, bytes, -1, 0.f});
+        s->pending.push_back({kind == 2 ? KC_PERMUTE_BULK : kind == 1 ? KC_PERMUTE_CYCLES : KC_PERMUTE, ev0, bytes,
+                              -1, 0.f});
     }
     s->stats.passes++;
     s->stats.amp_updates += std::ldexp(1.0, s->n - c);

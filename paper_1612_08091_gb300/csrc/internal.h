@@ -104,7 +104,7 @@ struct qsim {
 
 enum KernelClass {
     KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_BLOCK_DIAG, KC_BLOCK_TC6, KC_PERMUTE,
-    KC_PERMUTE_CYCLES, KC_COUNT
+    KC_PERMUTE_CYCLES, KC_PERMUTE_BULK, KC_COUNT
 };
 static_assert(KC_COUNT <= 16, "class_time holds 16 kernel classes");
 constexpr int kMaxDiagQubits = 12;
@@ -138,9 +138,10 @@ int cuda_err(qsim *s, cudaError_t e, const char *where);
 int launch_gate_plain(qsim *s, const GateRec &g);
 int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m);
 // Emulated classical bijection on a register (perm_kernels.cu).
-// *cycles: whether the cycle walk ran (else the tiled kernel)
+// *kind: which kernel ran: 0 tiled, 1 cycle walk through registers, 2 cycle
+// walk through the bulk-copy engine
 int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask,
-                       bool *cycles);
+                       int *kind);
 
 // Diagonal block: psi_i *= d[bits of i on dmask] (diag_kernels.cu).
 int launch_block_diag(qsim *s, uint64_t dmask, const cd *d);

@@ -35,7 +35,8 @@
 // walked from e_{L-1} down to e_0 with the loads of the next eight elements
 // in flight (a load of e_j always precedes the store to e_j).  Every access
 // of a CTA is 4 KB contiguous, fixed points of f are not touched, and the
-// work is (cycle, slice) tasks, longest cycles first.
+// work is (cycle, slice) tasks, longest cycles first.  Above the lowest 16 KB
+// the same walk runs through the bulk-copy engine (k_permute_cycles_bulk).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +45,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 using namespace qsim_dev;
 
@@ -166,13 +168,117 @@ __global__ void __launch_bounds__(kCycThreads) k_permute_cycles(float4 *__restri
     }
 }
 
+// Cycle walk through the bulk-copy engine, for registers above the lowest
+// 16 KB of amplitudes: one thread per CTA moves 16 KB slices with
+// cp.async.bulk, global -> shared stage (completing on the stage's
+// mbarrier) -> global, kBulkStages loads ahead, so the bytes in flight are
+// bounded by shared memory rather than registers.  For a cycle x_j =
+// e_{L-1-j}: x_0 goes to its own buffer; at step j >= 1 the thread waits for
+// x_j's stage, stores it to x_{j-1} (whose load completed at step j - 1),
+// and refills the stage the store of step j - 1 has finished reading with
+// x_{j+S-1}; last, x_0's data goes to x_{L-1} = e_0.  Each element is read
+// before it is written and every wait is bounded (time-out: error flag,
+// bounded waits for the copies in flight, return).
+constexpr int kBulkStages = 4;
+constexpr uint32_t kBulkSlice = 16384;  // bytes per slice (one bulk copy)
+
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(qsim_tc::smem_u32(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// coff32: the cycles' register offsets in slice units, cycle by cycle;
+// dynamic shared memory: (kBulkStages + 1) slices, then the current cycle's
+// offsets (uint32, the longest cycle).
+__global__ void __launch_bounds__(32) k_permute_cycles_bulk(unsigned char *__restrict__ psi, const InsertSpec ins,
+                                                           uint64_t cmask, int amp_bytes, int slice_bits,
+                                                           const uint32_t *__restrict__ coff32,
+                                                           const uint32_t *__restrict__ cstart, uint32_t ncyc,
+                                                           uint64_t nslices, unsigned int *err) {
+    extern __shared__ __align__(128) unsigned char sm_bulk[];
+    __shared__ __align__(8) uint64_t bar[kBulkStages + 1];  // [kBulkStages]: x_0's buffer
+    unsigned char *stage = sm_bulk;                           // kBulkStages + 1 slices
+    uint32_t *s_off = (uint32_t *)(sm_bulk + (size_t)(kBulkStages + 1) * kBulkSlice);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i <= kBulkStages; ++i) qsim_tc::mbar_init(&bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    uint32_t parity = 0;  // bit i: the phase barrier i waits for next (thread 0)
+    const uint64_t ntasks = (uint64_t)ncyc * nslices;
+    uint32_t loaded = 0xffffffffu;
+    for (uint64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const uint32_t cyc = (uint32_t)(task / nslices);
+        const uint64_t sl = task - (uint64_t)cyc * nslices;
+        const uint32_t b0 = cstart[cyc];
+        const int L = (int)(cstart[cyc + 1] - b0);
+        if (cyc != loaded) {
+            for (int i = threadIdx.x; i < L; i += 32) s_off[i] = coff32[b0 + i];
+            loaded = cyc;
+        }
+        __syncwarp();
+        bool ok = true;
+        if (threadIdx.x == 0) {
+            unsigned char *base = psi + (insert_zeros(sl << slice_bits, ins) | cmask) * (uint64_t)amp_bytes;
+            auto addr = [&](int j) { return base + (uint64_t)s_off[L - 1 - j] * kBulkSlice; };  // x_j
+            auto load = [&](int b, int j) {
+                qsim_tc::mbar_expect_tx(&bar[b], kBulkSlice);
+                qsim_tc::bulk_copy(stage + (size_t)b * kBulkSlice, addr(j), kBulkSlice, &bar[b]);
+            };
+            auto wait = [&](int b) {
+                const bool r = qsim_tc::mbar_wait(&bar[b], (parity >> b) & 1u);
+                parity ^= 1u << b;
+                return r;
+            };
+            uint32_t pending = 1u << kBulkStages;  // barriers with a load in flight
+            load(kBulkStages, 0);
+            for (int j = 1; j < kBulkStages && j < L; ++j) {
+                load(j % kBulkStages, j);
+                pending |= 1u << (j % kBulkStages);
+            }
+            ok = wait(kBulkStages);
+            pending &= ~(1u << kBulkStages);
+            for (int j = 1; ok && j < L; ++j) {
+                const int b = j % kBulkStages;
+                ok = wait(b);
+                pending &= ~(1u << b);
+                if (!ok) break;
+                qsim_tc::fence_proxy_async_smem();
+                bulk_store(addr(j - 1), stage + (size_t)b * kBulkSlice, kBulkSlice);
+                const int nx = j + kBulkStages - 1;
+                if (nx < L) {
+                    bulk_wait_read_1();  // the previous store has read its stage
+                    load(nx % kBulkStages, nx);
+                    pending |= 1u << (nx % kBulkStages);
+                }
+            }
+            if (ok) bulk_store(addr(L - 1), stage + (size_t)kBulkStages * kBulkSlice, kBulkSlice);
+            bulk_wait_all();
+            if (!ok) {
+                atomicOr(err, 1u);
+                for (int b = 0; b <= kBulkStages; ++b)
+                    if ((pending >> b) & 1u) wait(b);  // the loads still in flight, bounded
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) return;
+    }
+}
+
 // The cycle walk when the register and the controls leave the lowest 4 KB
 // of amplitudes contiguous and there are enough tasks to fill the GPU;
 // returns QSIM_ENOTSUP otherwise (the tiled kernel then runs).
 template <typename Amp>
-int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask) {
+int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask,
+                   bool *bulk) {
+    *bulk = false;
     const int amp_shift = sizeof(Amp) == 8 ? 1 : 0;  // amplitudes per 16 bytes: 2 or 1
     const int slice_bits = 8 + amp_shift;  // 4 KB slices: 512 c64 or 256 c128 amplitudes
+    const int bulk_bits = slice_bits + 2;  // 16 KB slices for the bulk-copy walk
     const uint64_t fixed = qmask | cmask;
     if ((fixed & ((1ull << slice_bits) - 1ull)) != 0) return QSIM_ENOTSUP;
     const int D = 1 << m;
@@ -194,9 +300,53 @@ int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint
     const int nfree = s->n - m - __builtin_popcountll(cmask);
     const uint64_t nslices = 1ull << (nfree - slice_bits);
     if ((uint64_t)cycles.size() * nslices < (uint64_t)kSMs) return QSIM_ENOTSUP;
+    // the bulk-copy walk: 16 KB slices, at least two tasks per SM
+    const bool use_bulk = (fixed & ((1ull << bulk_bits) - 1ull)) == 0 && nfree >= bulk_bits &&
+                          (uint64_t)cycles.size() * (1ull << (nfree - bulk_bits)) >= 2ull * kSMs;
     std::stable_sort(cycles.begin(), cycles.end(),
                      [](const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) { return a.size() > b.size(); });
     const size_t ncyc = cycles.size();
+    InsertSpec ins{};
+    ins.m = 0;
+    for (int b = 0; b < 64; ++b)
+        if ((fixed >> b) & 1ull) ins.pos[ins.m++] = b;
+    if (use_bulk) {
+        // record: offsets in 16 KB slice units (uint32), then cycle starts
+        const size_t bslice_amps = (size_t)kBulkSlice / sizeof(Amp);
+        std::vector<uint32_t> rb(total + ncyc + 1);
+        size_t k = 0;
+        for (size_t j = 0; j < ncyc; ++j) {
+            rb[total + j] = (uint32_t)k;
+            for (uint32_t v : cycles[j]) {
+                uint64_t a = 0;
+                for (int b = 0; b < m; ++b)
+                    if ((v >> b) & 1u) a |= 1ull << qubits[b];
+                rb[k++] = (uint32_t)(a / bslice_amps);
+            }
+        }
+        rb[total + ncyc] = (uint32_t)k;
+        unsigned char *dev = nullptr;
+        int rc = stage_operand(s, rb.data(), rb.size() * sizeof(uint32_t), &dev);
+        if (rc) return rc;
+        const uint64_t bslices = 1ull << (nfree - bulk_bits);
+        const uint64_t ntasks = (uint64_t)ncyc * bslices;
+        const size_t smem = (size_t)(kBulkStages + 1) * kBulkSlice + sizeof(uint32_t) * cycles[0].size();
+        static bool attr[64] = {false};
+        if (s->device >= 0 && s->device < 64 && !attr[s->device]) {
+            cudaError_t e = cudaFuncSetAttribute(k_permute_cycles_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)((kBulkStages + 1) * kBulkSlice + sizeof(uint32_t) * 4096));
+            if (e != cudaSuccess) return cuda_err(s, e, "permutation kernel attribute");
+            attr[s->device] = true;
+        }
+        // two CTAs (one pipeline each) per SM
+        const uint64_t grid = ntasks < (uint64_t)kSMs * 2 ? ntasks : (uint64_t)kSMs * 2;
+        k_permute_cycles_bulk<<<(unsigned)grid, 32, smem, s->stream>>>(
+            (unsigned char *)s->state, ins, cmask, (int)sizeof(Amp), bulk_bits, (const uint32_t *)dev,
+            (const uint32_t *)dev + total, (uint32_t)ncyc, bslices, (unsigned int *)((char *)s->ws + kWsErr));
+        s->stats.launches++;
+        *bulk = true;
+        return cuda_err(s, cudaGetLastError(), "permutation launch");
+    }
     std::vector<unsigned char> rec(sizeof(uint64_t) * total + sizeof(uint32_t) * (ncyc + 1));
     uint64_t *coff = (uint64_t *)rec.data();
     uint32_t *cstart = (uint32_t *)(rec.data() + sizeof(uint64_t) * total);
@@ -214,10 +364,6 @@ int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint
     unsigned char *dev = nullptr;
     int rc = stage_operand(s, rec.data(), rec.size(), &dev);
     if (rc) return rc;
-    InsertSpec ins{};
-    ins.m = 0;
-    for (int b = 0; b < 64; ++b)
-        if ((fixed >> b) & 1ull) ins.pos[ins.m++] = b;
     const uint64_t ntasks = (uint64_t)ncyc * nslices;
     // 64 registers a thread: four CTAs of 256 threads resident per SM
     const uint64_t grid = ntasks < (uint64_t)kSMs * 4 ? ntasks : (uint64_t)kSMs * 4;
@@ -306,11 +452,12 @@ int permute(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qm
 }  // namespace
 
 int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask,
-                       bool *cycles) {
+                       int *kind) {
     const bool c128 = s->prec == QSIM_C128;
-    int rc = c128 ? permute_cycles<double2>(s, perm, qubits, m, qmask, cmask)
-                  : permute_cycles<float2>(s, perm, qubits, m, qmask, cmask);
-    *cycles = rc != QSIM_ENOTSUP;
+    bool bulk = false;
+    int rc = c128 ? permute_cycles<double2>(s, perm, qubits, m, qmask, cmask, &bulk)
+                  : permute_cycles<float2>(s, perm, qubits, m, qmask, cmask, &bulk);
+    *kind = rc == QSIM_ENOTSUP ? 0 : bulk ? 2 : 1;
     if (rc != QSIM_ENOTSUP) return rc;
     return c128 ? permute<double2>(s, perm, qubits, m, qmask, cmask) : permute<float2>(s, perm, qubits, m, qmask, cmask);
 }

@@ -71,9 +71,41 @@ def test_permutation_cycle_walk(qs, oracle_mod, prec, kind):
         got = sim.get_amplitudes()
         kt = sim.kernel_times()
     if kind != "identity":
-        assert kt.get("permute_cycles", {}).get("launches", 0) == 1, kt
+        walks = sum(kt.get(c, {}).get("launches", 0) for c in ("permute_cycles", "permute_cycles_bulk"))
+        assert walks == 1, kt
     tol = 0 if prec == "c128" else 1e-7
     np.testing.assert_allclose(got, ref.psi, atol=tol)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("kind", ["random", "add", "fixed_points"])
+def test_permutation_bulk_copy_walk(qs, oracle_mod, prec, kind):
+    """A register above the lowest 16 KB of amplitudes with enough 16 KB
+    slices (qubits 16..21 of 27, one control on qubit 25: 2^20 amplitudes per
+    register value) goes through the bulk-copy cycle walk."""
+    n, qubits, controls = 27, (18, 16, 21, 17, 20, 19), (25,)
+    rng = np.random.default_rng(13)
+    D = 1 << len(qubits)
+    if kind == "random":
+        perm = rng.permutation(D)
+    elif kind == "add":
+        perm = (np.arange(D) + 11) % D
+    else:
+        perm = np.arange(D)
+        moved = rng.choice(D, 9, replace=False)
+        perm[moved] = moved[np.roll(np.arange(9), 1)]
+    psi = cg.random_state(n, seed=10)
+    ref = oracle_mod.OracleSim(n, psi=psi)
+    ref.apply_permutation(perm, qubits, controls)
+    with qs.Simulator(n, precision=prec) as sim:
+        sim.set_amplitudes(psi)
+        sim.set_profiling(True)
+        sim.apply_permutation(perm, qubits, controls)
+        got = sim.get_amplitudes()
+        kt = sim.kernel_times()
+    assert kt.get("permute_cycles_bulk", {}).get("launches", 0) == 1, kt
+    tol = 0 if prec == "c128" else 1e-7
+    assert np.max(np.abs(got - ref.psi)) <= tol
 
 
 def test_permutation_tiled_when_register_is_low(qs):
