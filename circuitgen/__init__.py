@@ -96,6 +96,42 @@ def basis_prep_ops(x, n):
     return [op("X", (q,)) for q in range(n) if (int(x) >> q) & 1]
 
 
+def ripple_adder_ops(m, reps=1):
+    """A ripple-carry adder of two m-bit registers made of CNOT and Toffoli
+    gates only (the MAJ / UMA construction): qubit 0 is the incoming carry
+    (left at 0), a_i = qubit 2i+1, b_i = qubit 2i+2, and qubit 2m+1 receives
+    the outgoing carry.  One application maps |a, b, z> to |a, (a + b) mod
+    2^m, z ^ carry>; the sequence is repeated reps times."""
+    A = lambda i: 2 * i + 1
+    B = lambda i: 2 * i + 2
+    ops = []
+
+    def maj(c, b, a):
+        ops.extend([op("X", (b,), (a,)), op("X", (c,), (a,)), op("X", (a,), (c, b))])
+
+    def uma(c, b, a):
+        ops.extend([op("X", (a,), (c, b)), op("X", (c,), (a,)), op("X", (b,), (c,))])
+
+    for _ in range(reps):
+        maj(0, B(0), A(0))
+        for i in range(1, m):
+            maj(A(i - 1), B(i), A(i))
+        ops.append(op("X", (2 * m + 1,), (A(m - 1),)))
+        for i in range(m - 1, 0, -1):
+            uma(A(i - 1), B(i), A(i))
+        uma(0, B(0), A(0))
+    return ops
+
+
+def adder_basis_index(m, a, b, z=0):
+    """Register index of |a, b, z> in the layout of ripple_adder_ops."""
+    x = 0
+    for i in range(m):
+        x |= ((a >> i) & 1) << (2 * i + 1)
+        x |= ((b >> i) & 1) << (2 * i + 2)
+    return x | (z << (2 * m + 1))
+
+
 def random_basis_state(n, seed):
     rng = np.random.default_rng(seed)
     return int(rng.integers(0, 1 << n, dtype=np.uint64))

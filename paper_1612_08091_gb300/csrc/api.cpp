@@ -145,6 +145,13 @@ int execute_item(qsim *s, const PlanItem &it) {
         cls = KC_BLOCK_DIAG;
         rc = launch_block_diag(s, it.dmask, it.dtab.data());
         bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
+    } else if (it.perm_block) {
+        int qubits[64], m = 0, kind = 0;
+        for (int b = 0; b < s->n; ++b)
+            if ((it.pmask >> b) & 1ull) qubits[m++] = b;
+        rc = launch_permutation(s, it.ptab.data(), qubits, m, it.pmask, 0, &kind);
+        cls = kind == 2 ? KC_PERMUTE_BULK : kind == 1 ? KC_PERMUTE_CYCLES : KC_PERMUTE;
+        bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
     } else {
         rc = QSIM_ENOTSUP;
         cls = KC_BLOCK_TC;
@@ -215,11 +222,13 @@ int flush(qsim *s) {
                     if (const int r = execute_item(s, single_item(q, s->n, gi))) return r;
                 return 0;
             },
-            kMaxDiagQubits, false);
+            kMaxDiagQubits, false, perm_min_width(s->prec, ch.kmax));
     } else {
         // greedy: each block is launched as soon as it is formed, so the
         // host's planning of the next blocks overlaps the device's work
-        rc = plan_greedy_each(s->queue, s->n, block_kmax(s), [s](PlanItem &it) { return execute_item(s, it); });
+        rc = plan_greedy_each(
+            s->queue, s->n, block_kmax(s), [s](PlanItem &it) { return execute_item(s, it); }, kMaxDiagQubits, true,
+            perm_min_width(s->prec, block_kmax(s)));
     }
     s->queue.clear();
     return rc;
@@ -395,6 +404,7 @@ int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const in
     g.m.resize((size_t)D * D);
     for (int i = 0; i < D * D; ++i) g.m[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
     g.kind = classify(g);
+    g.perm = perm_map(g, g.pmap);
     g.diag = true;
     for (int r = 0; r < D && g.diag; ++r)
         for (int c = 0; c < D; ++c)

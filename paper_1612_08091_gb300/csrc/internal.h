@@ -30,6 +30,8 @@ struct GateRec {
     std::vector<cd> m;  // 4^t entries, row-major, index bit j = targets[j]
     int kind = GK_DENSE;
     bool diag = false;  // the matrix is diagonal (the gate only multiplies amplitudes by phases)
+    bool perm = false;  // the matrix is a 0/1 permutation matrix (X, CNOT, Toffoli, SWAP ...)
+    std::vector<uint8_t> pmap;  // perm: target value c -> the row r with m[r][c] = 1
 };
 
 // One unit of device work produced by the planner.
@@ -38,6 +40,9 @@ struct PlanItem {
     bool diag_block = false;  // fused block of diagonal gates: one multiply per amplitude
     uint64_t dmask = 0;       // qubits of a diagonal block (up to kMaxDiagQubits)
     std::vector<cd> dtab;     // its 2^popc(dmask) factors, index bit j = j-th qubit of dmask
+    bool perm_block = false;  // fused block of permutation gates: amplitudes only move
+    uint64_t pmask = 0;       // qubits of a permutation block (up to kMaxPermQubits)
+    std::vector<uint64_t> ptab;  // f over the 2^popc(pmask) register values (bit j = j-th qubit of pmask)
     int gate = -1;
     int k = 0;              // fused block width
     int qubits[6] = {0, 0, 0, 0, 0, 0};  // sorted ascending; bit j of the block index
@@ -108,6 +113,7 @@ enum KernelClass {
 };
 static_assert(KC_COUNT <= 16, "class_time holds 16 kernel classes");
 constexpr int kMaxDiagQubits = 12;
+constexpr int kMaxPermQubits = 12;
 
 // Bytes of one amplitude.
 inline size_t amp_bytes(const qsim *s) { return s->prec == QSIM_C128 ? 16 : 8; }
@@ -172,13 +178,23 @@ int run_measure_all(qsim *s, double u, uint64_t *outcome);
 void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out);
 // diag_k: widest diagonal block (0 disables diagonal blocks); matrices:
 // build each fused block's matrix or diagonal table (false: members and
-// qubits only, for comparing plans)
+// qubits only, for comparing plans); perm_min: narrowest permutation block
+// worth a pass of its own (0 disables permutation blocks; see perm_min_width)
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out,
-                 int diag_k = kMaxDiagQubits, bool matrices = true);
+                 int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0);
 // The same plan handed to emit item by item as it is formed (so execution
 // overlaps planning); a non-zero return of emit stops planning and is returned.
 int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
-                     int diag_k = kMaxDiagQubits, bool matrices = true);
+                     int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0);
+// The narrowest permutation block the executor runs as its own pass:
+// complex128 dense blocks are bound by arithmetic, so any permutation block
+// of two or more gates is cheaper; complex64 dense blocks are HBM-bound like
+// a permutation pass, so only a permutation block wider than any dense block
+// (more than kmax qubits) saves passes.
+int perm_min_width(int prec, int kmax);
+// The permutation matrix of a gate as a map of its target values (perm and
+// pmap of GateRec); false if the matrix is not a 0/1 permutation.
+bool perm_map(const GateRec &g, std::vector<uint8_t> &pmap);
 // Fill it.m, the product of the member gates embedded in it.qubits (a dense
 // block), or it.dtab (a diagonal block).
 void block_matrix(const std::vector<GateRec> &q, PlanItem &it);

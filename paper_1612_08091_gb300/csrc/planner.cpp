@@ -145,10 +145,37 @@ std::vector<cd> diag_table(const std::vector<GateRec> &q, const std::vector<int>
     return d;
 }
 
+// f of a permutation block over qubit set pmask: each register value v
+// (bit j = j-th lowest qubit of pmask) taken through the member gates in
+// order (a gate whose controls are all 1 maps its target value c to
+// pmap[c]).
+std::vector<uint64_t> perm_table(const std::vector<GateRec> &q, const std::vector<int> &members, uint64_t pmask) {
+    int pos[64], k = 0;
+    for (int b = 0; b < 64; ++b) pos[b] = ((pmask >> b) & 1ull) ? k++ : -1;
+    std::vector<uint64_t> f((size_t)1 << k);
+    for (size_t v = 0; v < f.size(); ++v) {
+        uint64_t x = v;
+        for (int gi : members) {
+            const GateRec &g = q[gi];
+            bool on = true;
+            for (int c : g.controls) on = on && ((x >> pos[c]) & 1u);
+            if (!on) continue;
+            unsigned c = 0;
+            for (int j = 0; j < g.t; ++j) c |= (unsigned)((x >> pos[g.targets[j]]) & 1u) << j;
+            const unsigned r = g.pmap[c];
+            for (int j = 0; j < g.t; ++j) x = (x & ~(1ull << pos[g.targets[j]])) | ((uint64_t)((r >> j) & 1u) << pos[g.targets[j]]);
+        }
+        f[v] = x;
+    }
+    return f;
+}
+
 void block_matrix(const std::vector<GateRec> &q, PlanItem &it) {
     const auto t0 = std::chrono::steady_clock::now();
     if (it.diag_block) {
         it.dtab = diag_table(q, it.members, it.dmask);
+    } else if (it.perm_block) {
+        it.ptab = perm_table(q, it.members, it.pmask);
     } else {
         const int D = 1 << it.k;
         it.m.assign((size_t)D * D, cd(0.0, 0.0));
@@ -158,8 +185,35 @@ void block_matrix(const std::vector<GateRec> &q, PlanItem &it) {
     it.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+int perm_min_width(int prec, int kmax) { return prec == QSIM_C128 ? 1 : kmax + 1; }
+
+bool perm_map(const GateRec &g, std::vector<uint8_t> &pmap) {
+    const int T = 1 << g.t;
+    pmap.assign(T, 0);
+    for (int c = 0; c < T; ++c) {
+        int row = -1;
+        for (int r = 0; r < T; ++r) {
+            const cd z = g.m[(size_t)r * T + c];
+            if (z == cd(1.0, 0.0)) {
+                if (row >= 0) return false;
+                row = r;
+            } else if (z != cd(0.0, 0.0)) {
+                return false;
+            }
+        }
+        if (row < 0) return false;
+        pmap[c] = (uint8_t)row;
+    }
+    std::vector<char> seen(T, 0);  // a column map onto distinct rows
+    for (int c = 0; c < T; ++c) {
+        if (seen[pmap[c]]) return false;
+        seen[pmap[c]] = 1;
+    }
+    return true;
+}
+
 int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
-                     int diag_k, bool matrices) {
+                     int diag_k, bool matrices, int perm_min) {
     const size_t G = q.size();
     if (G == 0) return 0;
     // per-wire gate lists in program order
@@ -198,6 +252,59 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
     while (remaining) {
         while (next_seed < G && done[next_seed]) ++next_seed;
         const int seed = (int)next_seed;  // earliest undone gate is always ready
+        if (perm_min > 0 && q[seed].perm && popc(qmask(q[seed])) <= kMaxPermQubits) {
+            // a permutation block: grow through the ready permutation gates
+            // (fewest new qubits first, program order kept on every wire) up
+            // to kMaxPermQubits qubits
+            std::vector<int> pm;
+            uint64_t Sp = qmask(q[seed]);
+            double frac = touched_fraction(q[seed]);
+            take(seed);
+            pm.push_back(seed);
+            for (;;) {
+                int best = -1, best_add = 1 << 30;
+                for (int b = 0; b < n; ++b) {
+                    if (front[b] >= wire[b].size()) continue;
+                    const int gi = wire[b][front[b]];
+                    if (!q[gi].perm) continue;
+                    const uint64_t m = qmask(q[gi]);
+                    const int add = popc(m & ~Sp);
+                    if (popc(Sp | m) > kMaxPermQubits || !is_ready(gi)) continue;
+                    if (add < best_add || (add == best_add && gi < best)) {
+                        best = gi;
+                        best_add = add;
+                    }
+                }
+                if (best < 0) break;
+                take(best);
+                pm.push_back(best);
+                Sp |= qmask(q[best]);
+                frac += touched_fraction(q[best]);
+            }
+            // its own pass only if wide enough (perm_min), cheaper than the
+            // separate launches, and at least two gate incidences per qubit:
+            // a single layer of permutation gates (the CNOTs of a brickwork
+            // layer) rides along in the dense blocks that hold its
+            // neighbours at no cost, and taking it out splits them (69 ->
+            // 181 passes for a 32-qubit depth-40 brickwork); chains of
+            // dependent permutation gates (adders, comparators) do not
+            int incid = 0;
+            for (int gi : pm) incid += popc(qmask(q[gi]));
+            if (pm.size() >= 2 && frac >= 1.0 && popc(Sp) >= perm_min && incid >= 2 * popc(Sp)) {
+                PlanItem it;
+                it.fused = true;
+                it.perm_block = true;
+                it.pmask = Sp;
+                it.k = popc(Sp);
+                it.ngates = (int)pm.size();
+                it.members = pm;
+                for (int gi : pm) it.amp_updates += (double)(1ull << (n - (int)q[gi].controls.size()));
+                if (matrices) block_matrix(q, it);
+                if (const int rc = emit(it)) return rc;
+                continue;
+            }
+            for (auto r = pm.rbegin(); r != pm.rend(); ++r) untake(*r);
+        }
         if (diag_k > 0 && q[seed].diag && popc(qmask(q[seed])) <= diag_k) {
             // a diagonal block: ready diagonal gates commute with each other,
             // so absorb them (fewest new qubits first) up to diag_k qubits
@@ -315,7 +422,7 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
 }
 
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out, int diag_k,
-                 bool matrices) {
+                 bool matrices, int perm_min) {
     out.clear();
     plan_greedy_each(
         q, n, kmax,
@@ -323,16 +430,17 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
             out.push_back(std::move(it));
             return 0;
         },
-        diag_k, matrices);
+        diag_k, matrices, perm_min);
 }
 
 // ---------------------------------------------------------------------------
 // learned planner
 // ---------------------------------------------------------------------------
 // Features (all scaled to O(1)):
-//  0 n/32            1 bytes per amplitude/16   2 fused block        3 runs on tensor cores
+//  0 n/32            1 bytes per amplitude/16   2 fused block        3 tensor cores (1), c128 double-float (0.5)
 //  4 width/5         5 gates in item/32         6 plain dense gate   7 plain phase gate
-//  8 plain diagonal  9 plain X permutation     10 controls/8        11 log2(fraction touched)/8
+//  8 diagonal gate or block                     9 X gate or permutation block
+// 10 controls/8      11 log2(fraction touched)/8
 // 12 lowest qubit/32 13 highest qubit/32       14 qubits below 5 /5  15 constant 1
 void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df,
                    float *f) {
@@ -350,6 +458,12 @@ void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int
         f[5] = it.ngates / 32.f;
         f[8] = 1.f;
         mask = it.dmask;
+    } else if (it.fused && it.perm_block) {
+        f[2] = 1.f;
+        f[4] = it.k / 5.f;
+        f[5] = it.ngates / 32.f;
+        f[9] = 1.f;
+        mask = it.pmask;
     } else if (it.fused) {
         f[2] = 1.f;
         if (prec == QSIM_C64 && it.k >= 4 && n >= 12 && tc_enabled) f[3] = 1.f;
@@ -428,7 +542,7 @@ void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, b
     choice.predicted_ms = total_single;
     for (int kmax = 2; kmax <= kmax_limit; ++kmax) {
         std::vector<PlanItem> blocks;
-        plan_greedy(q, n, kmax, blocks, kMaxDiagQubits, false);
+        plan_greedy(q, n, kmax, blocks, kMaxDiagQubits, false, perm_min_width(prec, kmax));
         std::vector<char> fuse(blocks.size(), 0);
         double total = 0.0;
         for (size_t i = 0; i < blocks.size(); ++i) {

@@ -65,7 +65,6 @@ struct VqeArgs {
     unsigned int *err;      // error flag (a bounded wait gave up)
     int begin, end;   // its circuits: order[begin..end)
     int m;            // qubits held in shared memory
-    int g;            // chunk bits of the global-memory path (two chunks fit in shared memory)
     float2 *gbuf;     // per-CTA global buffers (two of gstride amplitudes each)
     size_t gstride;
     double h;
@@ -114,27 +113,19 @@ __device__ __forceinline__ unsigned ladder_src(unsigned y, unsigned mask) { retu
 // at a time in registers: each thread loads the 16 amplitudes of a group,
 // applies the four rotations there and stores them back, so a layer of k
 // one-qubit rotations costs ceil(k/4) passes over shared memory instead of k.
-// Rotation j pairs the elements i and i ^ mask[j]: a single bit for an array
-// in index order, two adjacent bits for the source-ordered buffers of the
-// global-memory path.  The lowest bit of each mask (its pivot) must differ
-// between the masks; a group is a base with zeros at its pivots XOR any
-// subset of its masks.  A group of fewer than four rotations is padded with
-// identity rotations on other bits.
-//
-// logical_pairs: the array is a pair buffer of the global-memory path in
-// source order, and mask[j] = 3 << k_j stands for logical qubit k_j.  The
-// element of a pair whose logical bit k_j is 0 is the one whose bits 0..k_j
-// have even parity; within a group that parity is the base's, so the
-// rotation is applied with t -> -t where the base's parity is odd.  This
-// needs groups without identity padding (nb a multiple of 4).
+// Rotation j pairs the elements i and i ^ mask[j] (single bits here; the
+// pair pass of the global-memory path, whose buffers are in source order,
+// has its own compile-time version, pair_group).  The masks' bits must
+// differ; a group is a base with zeros at its bits XOR any subset of its
+// masks.  A group of fewer than four rotations is padded with identity
+// rotations on other bits.
 __device__ __forceinline__ void cswap(int &a, int &b) {
     const int lo = a < b ? a : b, hi = a < b ? b : a;
     a = lo;
     b = hi;
 }
 
-__device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot *g, int nb,
-                              bool logical_pairs = false) {
+__device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot *g, int nb) {
     if (k < 4) {
         // fewer than four bits in the array: one pass per gate
         for (int j = 0; j < nb; ++j) gate_smem(x, k, mask[j], g[j]);
@@ -171,9 +162,7 @@ __device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot 
                 v[r] = x[base ^ ((r & 1) ? m0 : 0u) ^ ((r & 2) ? m1 : 0u) ^ ((r & 4) ? m2 : 0u) ^ ((r & 8) ? m3 : 0u)];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const unsigned mj = j == 0 ? m0 : j == 1 ? m1 : j == 2 ? m2 : m3;
-                float t = j == 0 ? t0 : j == 1 ? t1 : j == 2 ? t2 : t3;
-                if (logical_pairs && (__popc(base & ((mj & (0u - mj)) * 2u - 1u)) & 1)) t = -t;
+                const float t = j == 0 ? t0 : j == 1 ? t1 : j == 2 ? t2 : t3;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     if ((r >> j) & 1) continue;
@@ -274,8 +263,11 @@ __constant__ int kPairOrder[12] = {0, 4, 5, 6, 1, 7, 8, 9, 2, 3, 10, 11};
 // One group of the pair pass with compile-time qubits Q0 < Q1 < Q2 < Q3 (a
 // group of kPairOrder): the 2^13-element pair buffer x holds 512 groups of
 // 16 elements, base (zeros at the pivots Q0..Q3) XOR any subset of the masks
-// (PERM ? 3 : 1) << Qj; rotation j uses r[j].t, negated where the base's
-// bits 0..Qj have odd parity (PERM: source order, see gates_blocked).
+// (PERM ? 3 : 1) << Qj; rotation j uses r[j].t.  PERM: the buffer is in
+// source order after a ladder permutation, where logical qubit k pairs the
+// elements p and p ^ (3 << k); the element whose logical bit k is 0 is the
+// one whose bits 0..k have even parity, which within a group is the base's,
+// so the rotation is applied with t -> -t where the base's parity is odd.
 template <bool PERM, int Q0, int Q1, int Q2, int Q3>
 __device__ __forceinline__ void pair_group(float2 *x, const Rot *r) {
     static_assert(Q0 < Q1 && Q1 < Q2 && Q2 < Q3, "pivots in ascending order");
@@ -733,7 +725,6 @@ int launch(qsim_batch *b, int threads, int m, int grid) {
     a.energies = b->d_energies;
     a.err = b->d_counter + 2;
     a.m = m;
-    a.g = kGlobalBits;
     a.gbuf = b->d_gbuf;
     a.gstride = b->gstride;
     a.h = b->h;

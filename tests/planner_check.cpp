@@ -9,6 +9,11 @@
 //     most kmax qubits and contains its members' qubits; a diagonal block
 //     holds only diagonal gates and its table is the diagonal of the product;
 //     plan_greedy_each hands out the same items as plan_greedy.
+//  3. permutation blocks on permutation-heavy random circuits (X with 0-2
+//     controls, SWAP, some dense and diagonal gates): every gate once, in
+//     program order on every qubit; a permutation block holds only
+//     permutation gates on at most 12 qubits, is at least perm_min wide, and
+//     its table is the permutation of the embedded matrix product.
 #include <algorithm>
 #include <cstdio>
 #include <random>
@@ -49,6 +54,23 @@ GateRec random_gate(const std::vector<int> &pool, int kind) {
         g.kind = GK_DENSE;
         for (auto &z : g.m) z = cd(unif(rng), unif(rng));
     }
+    g.perm = perm_map(g, g.pmap);
+    return g;
+}
+
+// SWAP of two qubits of the pool as a 2-target permutation matrix
+GateRec swap_gate(const std::vector<int> &pool) {
+    std::vector<int> perm = pool;
+    std::shuffle(perm.begin(), perm.end(), rng);
+    GateRec g;
+    g.t = 2;
+    g.targets[0] = perm[0];
+    g.targets[1] = perm[1];
+    g.tmask = (1ull << perm[0]) | (1ull << perm[1]);
+    g.m.assign(16, cd(0.0, 0.0));
+    g.m[0 * 4 + 0] = g.m[1 * 4 + 2] = g.m[2 * 4 + 1] = g.m[3 * 4 + 3] = 1.0;
+    g.kind = GK_DENSE;
+    g.perm = perm_map(g, g.pmap);
     return g;
 }
 
@@ -206,10 +228,94 @@ int check_plans() {
     return bad == 0 ? 0 : 1;
 }
 
+int check_perm_plans() {
+    int bad = 0, blocks = 0;
+    for (int trial = 0; trial < 60; ++trial) {
+        // n <= 10 keeps the embedded-matrix check below (2^n x 2^n) quick
+        const int n = 6 + trial % 5, kmax = 2 + trial % 4, G = 60 + (int)(rng() % 80);
+        const int perm_min = trial % 2 ? 1 : kmax + 1;
+        std::vector<int> all(n);
+        for (int i = 0; i < n; ++i) all[i] = i;
+        std::vector<GateRec> q;
+        for (int i = 0; i < G; ++i) {
+            std::shuffle(all.begin(), all.end(), rng);
+            const int width = 2 + (int)(rng() % 2);
+            std::vector<int> pool(all.begin(), all.begin() + width);
+            const int r = (int)(rng() % 10);
+            q.push_back(r < 6 ? random_gate(pool, 1) : r < 8 ? swap_gate(pool) : random_gate(pool, r == 8 ? 0 : 2));
+        }
+        std::vector<PlanItem> plan;
+        plan_greedy(q, n, kmax, plan, kMaxDiagQubits, true, perm_min);
+        std::vector<int> order, seen(G, 0);
+        for (const PlanItem &it : plan) {
+            for (int gi : it.members) {
+                order.push_back(gi);
+                seen[gi]++;
+            }
+            if (!it.perm_block) continue;
+            ++blocks;
+            std::vector<int> Sv;
+            for (int b = 0; b < 64; ++b)
+                if ((it.pmask >> b) & 1ull) Sv.push_back(b);
+            if ((int)Sv.size() > kMaxPermQubits || (int)Sv.size() < perm_min) ++bad;
+            for (int gi : it.members)
+                if (!q[gi].perm || ((q[gi].tmask | q[gi].cmask) & ~it.pmask)) ++bad;
+            // follow every basis state through the embedded member matrices:
+            // each column must hold a single 1, and the last row reached is
+            // the table's image
+            const int D = 1 << (int)Sv.size();
+            std::vector<int> x(D);
+            for (int v = 0; v < D; ++v) x[v] = v;
+            for (int gi : it.members) {
+                const std::vector<cd> E = embed(q[gi], Sv);
+                for (int v = 0; v < D; ++v) {
+                    int row = -1, ones = 0;
+                    for (int r = 0; r < D; ++r) {
+                        const cd z = E[(size_t)r * D + x[v]];
+                        if (z == cd(1.0, 0.0)) {
+                            row = r;
+                            ++ones;
+                        } else if (z != cd(0.0, 0.0)) {
+                            ones = 2;
+                        }
+                    }
+                    if (ones != 1) {
+                        ++bad;
+                        break;
+                    }
+                    x[v] = row;
+                }
+            }
+            for (int v = 0; v < D; ++v)
+                if ((uint64_t)x[v] != it.ptab[v]) {
+                    ++bad;
+                    break;
+                }
+        }
+        for (int gi = 0; gi < G; ++gi)
+            if (seen[gi] != 1) ++bad;
+        std::vector<int> at(G);
+        for (size_t i = 0; i < order.size(); ++i) at[order[i]] = (int)i;
+        for (int a = 0; a < G; ++a)
+            for (int b = a + 1; b < G; ++b)
+                if (((q[a].tmask | q[a].cmask) & (q[b].tmask | q[b].cmask)) && at[a] > at[b]) {
+                    bool both_diag_same_block = false;
+                    for (const PlanItem &it : plan)
+                        if (it.diag_block && std::count(it.members.begin(), it.members.end(), a) &&
+                            std::count(it.members.begin(), it.members.end(), b))
+                            both_diag_same_block = true;
+                    if (!both_diag_same_block) ++bad;
+                }
+    }
+    printf("permutation blocks: %d blocks, %d violations over 60 random circuits\n", blocks, bad);
+    return bad == 0 && blocks > 0 ? 0 : 1;
+}
+
 }  // namespace
 
 int main() {
     const int a = check_block_matrix();
     const int b = check_plans();
-    return a | b;
+    const int c = check_perm_plans();
+    return a | b | c;
 }

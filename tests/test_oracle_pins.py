@@ -367,3 +367,21 @@ def test_permutation_emulation_pins(oracle_mod):
         b = _sim(oracle_mod, n, psi=psi)
         b.apply(P, qubits, controls)
         np.testing.assert_allclose(a.psi, b.psi, atol=1e-15)
+
+
+@pytest.mark.parametrize("m", [3, 5])
+def test_ripple_adder_adds(oracle_mod, m):
+    """The CNOT / Toffoli ripple-carry adder on basis states: |a, b, 0> goes
+    to |a, (a + b) mod 2^m, carry> with amplitude 1 (classical arithmetic
+    fixes the result, independent of the oracle's gate code)."""
+    n = 2 * m + 2
+    rng = np.random.default_rng(m)
+    for _ in range(6):
+        a, b = (int(v) for v in rng.integers(0, 1 << m, 2))
+        s = _sim(oracle_mod, n)
+        s.psi[:] = 0
+        s.psi[cg.adder_basis_index(m, a, b)] = 1.0
+        oracle_mod.run_ops(s, cg.ripple_adder_ops(m))
+        want = cg.adder_basis_index(m, a, (a + b) % (1 << m), (a + b) >> m)
+        assert abs(s.psi[want] - 1.0) < 1e-15
+        assert np.sum(np.abs(s.psi) ** 2) - abs(s.psi[want]) ** 2 < 1e-15
