@@ -60,7 +60,8 @@ def parse():
                          "instead of the 4096-circuit mix")
     ap.add_argument("--vqe-config", default=None, metavar="THREADS,M",
                     help="vqe workload: fixed launch configuration instead of the autotuner's")
-    ap.add_argument("--workload", default="random", choices=["random", "vqe", "planner", "qft", "grover", "fig6"],
+    ap.add_argument("--workload", default="random",
+                    choices=["random", "vqe", "planner", "qft", "grover", "fig6", "adder"],
                     help="random: the headline line; vqe / planner: secondary measurements")
     return ap.parse_args()
 
@@ -759,6 +760,17 @@ def run_circuit(args):
         ops = cg.grover_ops(n, marked, iterations=iters)
         what = ("Grover search on %d qubits, marked item %d (seed 2017): %d of the r = %d iterations timed"
                 % (n, marked, iters, full_iters))
+    elif w == "adder":
+        m = 15
+        n = 2 * m + 2
+        rng = np.random.default_rng(SEED)
+        a_in, b_in = (int(v) for v in rng.integers(0, 1 << m, 2))
+        reps = 4
+        ops = cg.ripple_adder_ops(m, reps=reps)
+        basis = cg.adder_basis_index(m, a_in, b_in)
+        what = ("ripple-carry adder (CNOT / Toffoli) of two %d-bit registers on %d qubits, %d times, basis input "
+                "a = %d, b = %d (seed %d)" % (m, n, reps, a_in, b_in, SEED))
+        full_iters = None
     else:
         n = 30
         ops = cg.hadamard_crz_chain(n, SEED)
@@ -804,10 +816,30 @@ def run_circuit(args):
             want = (-1) ** iters * math.sin((2 * iters + 1) * theta)
             check = {"marked_amplitude": [float(a.real), float(a.imag)], "closed_form": want,
                      "abs_error": float(abs(a - want))}
+        elif w == "adder":
+            bb, z = b_in, 0
+            for _ in range(reps):
+                z ^= (a_in + bb) >> m
+                bb = (a_in + bb) % (1 << m)
+            want_idx = cg.adder_basis_index(m, a_in, bb, z)
+            amp = sim.get_amplitudes(want_idx, 1)[0]
+            check = {"result_index": want_idx, "amplitude": [float(amp.real), float(amp.imag)]}
         else:
             _, nrm = sim.probs_all()
             check = {"norm2": nrm}
     torch.cuda.empty_cache()
+    no_perm = None
+    if w == "adder":
+        # the same circuit with dense blocks only (no permutation blocks)
+        with q.Simulator(n, precision="c64", fusion="greedy", stream=stream, perm_blocks=False) as sim:
+            t_np = timed(sim, ops, args.steps)
+            sim.reset_stats()
+            sim.reset(basis)
+            sim.run(ops)
+            sim.flush()
+            no_perm = {"ms": 1e3 * t_np, "passes": sim.stats()["passes"], "value": upd / t_np,
+                       "what": "greedy dense blocks only (perm_blocks=False)"}
+        torch.cuda.empty_cache()
 
     # plain complex128 on a sample of the first gates
     sample = ops[: min(len(ops), 64)]
@@ -823,6 +855,8 @@ def run_circuit(args):
                           % len(sample), "extrapolated_ms": 1e3 * upd / rate_plain,
                           "speedup_of_fused": (upd / t_fused) / rate_plain},
            "check": check}
+    if no_perm is not None:
+        out["dense_blocks_only"] = no_perm
     if full_iters:
         out["config"]["extrapolated_full_search_s"] = t_fused * full_iters / iters
     print(json.dumps(out), flush=True)
@@ -837,7 +871,7 @@ def main():
         return run_vqe(args)
     if args.workload == "planner":
         return run_planner(args)
-    if args.workload in ("qft", "grover", "fig6"):
+    if args.workload in ("qft", "grover", "fig6", "adder"):
         return run_circuit(args)
     return run_ours(args)
 

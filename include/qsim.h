@@ -95,6 +95,9 @@ typedef struct qsim_opts {
                                phase gates, multi-target dense gates) and fused blocks
                                (dense and diagonal) compute in FP32 pairs (about 2^-45
                                relative error per product) instead of FP64 arithmetic */
+    int no_permutation_blocks; /* non-zero: the greedy and learned planners form no
+                               permutation blocks (runs of X / CNOT / Toffoli / SWAP
+                               executed as one emulated-permutation pass) */
 } qsim_opts;
 
 /* A Pauli-sum term c * P.  Qubit q of P is X if bit q is set in xmask only,

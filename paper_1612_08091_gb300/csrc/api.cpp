@@ -198,7 +198,7 @@ int flush(qsim *s) {
     const std::vector<GateRec> &q = s->queue;
     MlpChoice ch;
     if (s->fusion == QSIM_FUSE_MLP && s->cost.loaded()) {
-        plan_mlp(q, s->n, s->prec, s->tc_enabled, s->c128_df, block_kmax(s), s->cost, ch);
+        plan_mlp(q, s->n, s->prec, s->tc_enabled, s->c128_df, s->perm_blocks, block_kmax(s), s->cost, ch);
         s->last_plan_predicted_ms = ch.predicted_ms;
     }
     if (s->fusion == QSIM_FUSE_NONE || (s->fusion == QSIM_FUSE_MLP && s->cost.loaded() && ch.kmax == 1)) {
@@ -222,13 +222,13 @@ int flush(qsim *s) {
                     if (const int r = execute_item(s, single_item(q, s->n, gi))) return r;
                 return 0;
             },
-            kMaxDiagQubits, false, perm_min_width(s->prec, ch.kmax));
+            kMaxDiagQubits, false, s->perm_blocks ? perm_min_width(s->prec, ch.kmax) : 0);
     } else {
         // greedy: each block is launched as soon as it is formed, so the
         // host's planning of the next blocks overlaps the device's work
         rc = plan_greedy_each(
             s->queue, s->n, block_kmax(s), [s](PlanItem &it) { return execute_item(s, it); }, kMaxDiagQubits, true,
-            perm_min_width(s->prec, block_kmax(s)));
+            s->perm_blocks ? perm_min_width(s->prec, block_kmax(s)) : 0);
     }
     s->queue.clear();
     return rc;
@@ -310,6 +310,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->tc_enabled = o.no_tensor_cores == 0;
     s->norm_tracking = o.no_norm_tracking == 0;
     s->c128_df = o.c128_double_float != 0;
+    s->perm_blocks = o.no_permutation_blocks == 0;
     if (const char *v = getenv("QSIM_TC_KERNEL"))
         s->tc_variant = (v[0] == 'w') ? 1 : (v[0] == 'd') ? 0 : (v[0] == 's') ? 2 : 3;
     if (const char *v = getenv("QSIM_TC_STREAMING")) s->tc_streaming = atoi(v);

@@ -84,6 +84,7 @@ struct qsim {
     int tc_terms = 3;
     bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
     bool c128_df = false;       // complex128 gates and blocks in double-float arithmetic
+    bool perm_blocks = true;    // the planners may form permutation blocks
     int tc_variant = 3;         // 4-5-qubit blocks: 3 k_block_tmem<5> (state operand in tensor memory);
                                 // 0 k_block_tc<2>, 1 k_block_tc_ws, 2 k_block_tc<1> (state operand in shared memory)
     int tc_streaming = 0;       // streaming (evict-first) cache hints on the block kernel's loads and stores
@@ -213,7 +214,8 @@ struct MlpChoice {
     std::vector<char> fuse;
     double predicted_ms = 0;
 };
-void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df, int kmax_limit, const CostModel &cm,
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df, bool perm_blocks,
+              int kmax_limit, const CostModel &cm,
               MlpChoice &choice);
 // Gate gi as a plan item of its own.
 PlanItem single_item(const std::vector<GateRec> &q, int n, int gi);

@@ -523,7 +523,8 @@ PlanItem single_item(const std::vector<GateRec> &q, int n, int gi) {
     return it;
 }
 
-void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df, int kmax_limit, const CostModel &cm,
+void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, bool df, bool perm_blocks,
+              int kmax_limit, const CostModel &cm,
               MlpChoice &choice) {
     auto cost = [&](const PlanItem &it) {
         float f[kFeatures];
@@ -542,7 +543,7 @@ void plan_mlp(const std::vector<GateRec> &q, int n, int prec, bool tc_enabled, b
     choice.predicted_ms = total_single;
     for (int kmax = 2; kmax <= kmax_limit; ++kmax) {
         std::vector<PlanItem> blocks;
-        plan_greedy(q, n, kmax, blocks, kMaxDiagQubits, false, perm_min_width(prec, kmax));
+        plan_greedy(q, n, kmax, blocks, kMaxDiagQubits, false, perm_blocks ? perm_min_width(prec, kmax) : 0);
         std::vector<char> fuse(blocks.size(), 0);
         double total = 0.0;
         for (size_t i = 0; i < blocks.size(); ++i) {

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("fusion", ctypes.c_int), ("kmax", ctypes.c_int),
                 ("device", ctypes.c_int), ("tc_terms", ctypes.c_int), ("no_tensor_cores", ctypes.c_int),
-                ("no_norm_tracking", ctypes.c_int), ("c128_double_float", ctypes.c_int)]
+                ("no_norm_tracking", ctypes.c_int), ("c128_double_float", ctypes.c_int),
+                ("no_permutation_blocks", ctypes.c_int)]
 
 
 class Pauli(ctypes.Structure):
@@ -131,7 +132,7 @@ class Simulator:
     """An n-qubit register on the GPU behind the libqsim C ABI."""
 
     def __init__(self, n, precision="c128", fusion="none", kmax=6, device=None, stream=None, torch_memory=True,
-                 tc_terms=3, tensor_cores=True, norm_tracking=True, c128_df=False):
+                 tc_terms=3, tensor_cores=True, norm_tracking=True, c128_df=False, perm_blocks=True):
         import torch
 
         if not torch.cuda.is_available():
@@ -150,6 +151,7 @@ class Simulator:
         opts.no_tensor_cores = 0 if tensor_cores else 1
         opts.no_norm_tracking = 0 if norm_tracking else 1
         opts.c128_double_float = 1 if c128_df else 0
+        opts.no_permutation_blocks = 0 if perm_blocks else 1
         self._keep = []
         if torch_memory:
             ws = ctypes.c_size_t()

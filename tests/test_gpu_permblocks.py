@@ -92,3 +92,19 @@ def test_mixed_permutation_heavy_circuits(qs, oracle_mod, prec, p_dense):
         assert np.max(np.abs(got - ref.psi)) <= 1e-11
     else:
         assert infidelity(ref.psi, got) <= TOL64_INFID
+
+
+def test_permutation_blocks_can_be_switched_off(qs):
+    m = 6
+    n = 2 * m + 2
+    ops = cg.ripple_adder_ops(m, reps=3)
+    out = {}
+    for on in (True, False):
+        with qs.Simulator(n, precision="c128", fusion="greedy", perm_blocks=on) as sim:
+            sim.reset(cg.adder_basis_index(m, 21, 42))
+            sim.set_profiling(True)
+            sim.run(ops)
+            out[on] = (sim.get_amplitudes(), perm_launches(sim.kernel_times()), sim.stats()["passes"])
+    assert out[True][1] > 0 and out[False][1] == 0
+    assert out[True][2] < out[False][2]
+    np.testing.assert_array_equal(out[True][0], out[False][0])
