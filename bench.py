@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--fusion", default="greedy")
     ap.add_argument("--kmax", type=int, default=6)
     ap.add_argument("--plain-layers", type=int, default=2, help="layers of the plain c128 comparison sample")
+    ap.add_argument("--grover-iterations", type=int, default=20,
+                    help="Grover iterations timed (0: the full r = floor(pi/4 sqrt(2^n)) search)")
     ap.add_argument("--cpu-gates", type=int, default=6, help="gates of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -755,8 +757,8 @@ def run_circuit(args):
     elif w == "grover":
         n = 28
         marked = int(cg.grover_marked(n, 2017))
-        iters = 20
         full_iters = cg.grover_iterations(n)
+        iters = args.grover_iterations if args.grover_iterations > 0 else full_iters
         ops = cg.grover_ops(n, marked, iterations=iters)
         what = ("Grover search on %d qubits, marked item %d (seed 2017): %d of the r = %d iterations timed"
                 % (n, marked, iters, full_iters))
@@ -794,11 +796,8 @@ def run_circuit(args):
 
     with q.Simulator(n, precision="c64", fusion="greedy", stream=stream) as sim:
         t_fused = timed(sim, ops, args.steps)
-        sim.reset_stats()
-        sim.reset(basis)
-        sim.run(ops)
-        sim.flush()
-        passes = sim.stats()["passes"]
+        # the register holds the last timed run's result; passes per run
+        passes = sim.stats()["passes"] / (args.warmup + args.steps)
         check = {}
         if w == "qft":
             rng = np.random.default_rng(SEED + 1)
@@ -814,8 +813,11 @@ def run_circuit(args):
             theta = math.asin(2.0 ** (-n / 2))
             a = sim.get_amplitudes(marked, 1)[0]
             want = (-1) ** iters * math.sin((2 * iters + 1) * theta)
+            p1, nrm = sim.probs_all()
             check = {"marked_amplitude": [float(a.real), float(a.imag)], "closed_form": want,
-                     "abs_error": float(abs(a - want))}
+                     "abs_error": float(abs(a - want)),
+                     "success_probability": float(abs(a) ** 2 / nrm),
+                     "success_closed_form": math.sin((2 * iters + 1) * theta) ** 2, "norm2": nrm}
         elif w == "adder":
             bb, z = b_in, 0
             for _ in range(reps):
