@@ -120,3 +120,27 @@ def test_learned_planner_end_to_end(qs, oracle_mod):
               % (name, n, 1e3 * t_greedy, 1e3 * t_mlp, pred, t_greedy / t_mlp))
         # the learned plan must not be clearly worse than greedy fusion
         assert t_mlp <= 1.25 * t_greedy + 2e-3
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_learned_planner_with_permutation_blocks(qs, oracle_mod, prec):
+    """fusion "mlp" on a circuit whose greedy plan has permutation blocks
+    (a ripple-carry adder plus a layer of U3): the learned plan regenerates
+    the same items (same permutation-block rule) and matches the oracle."""
+    from paper_1612_08091_gb300 import costmodel
+
+    X, ms = costmodel.collect(sizes=(18, 19), precisions=(prec,), kmaxes=(1, 3, 5), seed=9)
+    params, _ = costmodel.train(X, ms, hidden=32, epochs=100)
+    m = 8
+    n = 2 * m + 2
+    ops = cg.random_u3_brickwork(n, 1, seed=3) + cg.ripple_adder_ops(m, reps=2)
+    ref = oracle_mod.OracleSim(n)
+    oracle_mod.run_ops(ref, ops)
+    with qs.Simulator(n, precision=prec, fusion="mlp") as sim:
+        sim.set_cost_model(params, 32)
+        sim.run(ops)
+        got = sim.get_amplitudes()
+    if prec == "c128":
+        assert np.max(np.abs(got - ref.psi)) <= 1e-11
+    else:
+        assert infidelity(ref.psi, got) <= TOL64_INFID
