@@ -816,8 +816,10 @@ def run_circuit(args):
             p1, nrm = sim.probs_all()
             check = {"marked_amplitude": [float(a.real), float(a.imag)], "closed_form": want,
                      "abs_error": float(abs(a - want)),
-                     "success_probability": float(abs(a) ** 2 / nrm),
-                     "success_closed_form": math.sin((2 * iters + 1) * theta) ** 2, "norm2": nrm}
+                     "success_probability_raw": float(abs(a) ** 2),
+                     "success_probability_normalised": float(abs(a) ** 2 / nrm),
+                     "success_closed_form": math.sin((2 * iters + 1) * theta) ** 2, "norm2": nrm,
+                     "norm2_error": abs(nrm - 1.0)}
         elif w == "adder":
             bb, z = b_in, 0
             for _ in range(reps):

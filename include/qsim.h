@@ -89,8 +89,9 @@ typedef struct qsim_opts {
     int tc_terms;           /* complex64 tensor-core blocks: 3 = BF16x3 (default, 0 means 3),
                                5 = five split products (gate split in three parts) */
     int no_tensor_cores;    /* non-zero: run complex64 blocks on the CUDA cores */
-    int no_norm_tracking;   /* non-zero: do not rescale tensor-core block outputs by the
-                               previous block pass's input/output norm ratio */
+    int no_norm_tracking;   /* non-zero: tensor-core block passes do not scale their
+                               outputs back to the norm the state had after the last
+                               reset, measurement or host write */
     int c128_double_float;  /* non-zero: complex128 gates (one-qubit dense, diagonal and
                                phase gates, multi-target dense gates) and fused blocks
                                (dense and diagonal) compute in FP32 pairs (about 2^-45
@@ -117,26 +118,36 @@ typedef struct qsim_stats {
     double alg_bytes;        /* algorithmic HBM bytes of the gate passes */
 } qsim_stats;
 
-/* Scratch bytes a handle of n qubits needs (whatever the precision). */
+/* Scratch bytes a handle of n qubits needs (whatever the precision).  Not in
+ * the paper: its simulator allocates host memory itself; here a caller may
+ * hand device memory in through qsim_opts. */
 int sim_workspace_bytes(int n, int precision, size_t *bytes);
 
-/* Create an n-qubit register (1 <= n <= 36) in |0...0>.  On success *out
- * receives the handle.  QSIM_ENOMEM if the state does not fit. */
+/* Create an n-qubit register (1 <= n <= 36) in |0...0>: the register that
+ * allocate_qureg(n) hands out (Sec. 4.1.1), its qubits starting in |0> as in
+ * the first example of Sec. 4.  On success *out receives the handle.
+ * QSIM_ENOMEM if the state does not fit. */
 int sim_create(int n, int precision, const qsim_opts *opts, qsim **out);
 
-/* Destroy a handle; frees what the library allocated.  NULL is accepted. */
+/* Destroy a handle; frees what the library allocated (the deallocation of
+ * a register, Sec. 4.1.1).  NULL is accepted. */
 int sim_destroy(qsim *s);
 
-/* Drop the queue and set the register to the basis state |basis>. */
+/* Drop the queue and set the register to the basis state |basis>: a fresh
+ * register (Sec. 4.1.1) prepared in a basis state, as the reset of a measured
+ * qubit before its reuse does in Shor's example (Appendix A.3). */
 int sim_reset(qsim *s, uint64_t basis);
 
 /* Queue U (2^t x 2^t, see conventions) on targets[0..t-1], conditioned on
- * controls[0..c-1] all being |1>.  1 <= t <= 5, 0 <= c < n.  Validated now
- * (range, duplicates, finite entries), executed at the next flush.  U is not
- * checked for unitarity. */
+ * controls[0..c-1] all being |1>: the `Gate | qubits` statement of Sec. 4 on
+ * a tuple of qubits (Sec. 4.1.2), inside a Control(eng, controls) section
+ * (Sec. 4.1.3); executed lazily (Sec. 4.3.2, Fig. 7 caption).
+ * 1 <= t <= 5, 0 <= c < n.  Validated now (range, duplicates, finite
+ * entries), executed at the next flush.  U may be non-unitary; the
+ * complex64 norm control then starts afresh after it. */
 int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const int *controls, int c);
 
-/* Execute every queued gate (Sec. 4.1.3: eng.flush()). */
+/* Execute every queued gate: eng.flush() of Sec. 4, listing 1. */
 int sim_flush(qsim *s);
 
 /* Emulation of a classical reversible function on a register (Sec. 4.3.3,
@@ -155,7 +166,8 @@ int sim_apply_permutation(qsim *s, const uint64_t *perm, const int *qubits, int 
 int sim_prob(qsim *s, int qubit, double *p1);
 
 /* p1[q] = P(qubit q = 1) for all q in one pass; p1 holds n doubles. *norm2
- * (may be NULL) receives sum_i |psi_i|^2. */
+ * (may be NULL) receives sum_i |psi_i|^2.  The per-qubit marginals of the
+ * outcome distribution of Measure | qureg (Sec. 4.3.1, Fig. 6). */
 int sim_probs_all(qsim *s, double *p1, double *norm2);
 
 /* Measure one qubit with the caller's uniform draw u in [0,1): the outcome
@@ -164,45 +176,56 @@ int sim_probs_all(qsim *s, double *p1, double *norm2);
  * Appendix A.1, A.3). *p_outcome may be NULL. */
 int sim_measure(qsim *s, int qubit, double u, int *outcome, double *p_outcome);
 
-/* Project onto qubits[j] == bits[j] (j < m) and renormalise.  *p (may be
- * NULL) receives the probability of the projected outcome.  A projection of
- * probability 0 returns QSIM_EZEROPROB and leaves the state unchanged. */
+/* Project onto qubits[j] == bits[j] (j < m) and renormalise: the state
+ * after Measure | (psi, b1) has given those bits (Appendix A.1).  *p (may be
+ * NULL) receives sum |psi_i|^2 over the projected part, the outcome's
+ * probability for a normalised state.  A projection of probability 0 returns
+ * QSIM_EZEROPROB and leaves the state unchanged. */
 int sim_collapse(qsim *s, const int *qubits, int m, const int *bits, double *p);
 
-/* Sample the whole register with draw u in [0,1): the outcome is the
- * smallest j with sum_{i<=j} |psi_i|^2 > u * norm2 (cumulative sums in
- * FP64); the register collapses to |j> keeping the phase of psi_j. */
+/* Measure | qureg (Sec. 4.3.1): sample the whole register with draw u in
+ * [0,1): the outcome is the smallest j with sum_{i<=j} |psi_i|^2 > u * norm2
+ * (cumulative sums in FP64); the register collapses to |j> keeping the
+ * phase of psi_j. */
 int sim_measure_all(qsim *s, double u, uint64_t *outcome);
 
-/* <psi| sum_k terms[k].coeff * P_k |psi>, accumulated in FP64.  The state
- * is assumed normalised (no division by the norm). */
+/* <psi| sum_k terms[k].coeff * P_k |psi>, accumulated in FP64.  Not in the
+ * paper (its simulator exposes no observable); the Pauli-sum expectation the
+ * variational workloads need.  The state is assumed normalised (no division
+ * by the norm; complex64 block passes hold the norm, see sim_apply). */
 int sim_expect(qsim *s, const qsim_pauli *terms, int nterms, double *out);
 
 /* Copy amplitudes [offset, offset+count) to host memory as complex double
- * (2*count doubles, re/im interleaved), widening complex64 exactly. */
+ * (2*count doubles, re/im interleaved), widening complex64 exactly.  The
+ * state is the one the paper's simulator back-end holds (Sec. 4.3.2); the
+ * paper names no call for reading it. */
 int sim_get_amplitudes(qsim *s, uint64_t offset, uint64_t count, double *out);
 
 /* Overwrite amplitudes [offset, offset+count) from host complex double
- * (rounded to nearest for complex64).  No normalisation is applied. */
+ * (rounded to nearest for complex64).  No normalisation is applied.  Not in
+ * the paper: state preparation for tests and checkpoint / resume. */
 int sim_set_amplitudes(qsim *s, uint64_t offset, uint64_t count, const double *in);
 
-/* Device pointer of the amplitudes (valid until sim_destroy).  Flushes. */
+/* Device pointer of the amplitudes (valid until sim_destroy).  Flushes.
+ * Not in the paper: zero-copy access for device-side consumers. */
 int sim_state_ptr(qsim *s, void **dev_ptr);
 
 /* Run subsequent work on another cudaStream_t (after the current stream's
- * queued work, which this call waits for). */
+ * queued work, which this call waits for).  Not in the paper. */
 int sim_set_stream(qsim *s, void *stream);
 
 /* Choose the fusion mode (enum qsim_fusion) and block width kmax (1..6, see
- * qsim_opts.kmax).
+ * qsim_opts.kmax): how the lazily buffered gates are executed (Sec. 4.3.2,
+ * Fig. 7 caption).
  * QSIM_FUSE_MLP uses the cost model loaded with sim_set_cost_model (greedy
  * fusion if none is loaded).  Flushes the queue first. */
 int sim_set_fusion(qsim *s, int mode, int kmax);
 
+/* Counters of qsim_stats; not in the paper. */
 int sim_get_stats(const qsim *s, qsim_stats *out);
 int sim_reset_stats(qsim *s);
 
-/* Per-kernel-class device time.  When profiling is on, every gate or block
+/* Per-kernel-class device time (not in the paper).  When profiling is on, every gate or block
  * launch is bracketed by CUDA events on the handle's stream; the times are
  * collected (stream synchronised) by sim_get_kernel_times, which returns one
  * row per kernel class seen since profiling was switched on.  Class names:
@@ -219,7 +242,8 @@ typedef struct qsim_kernel_time {
     double alg_bytes;  /* algorithmic HBM bytes of those launches */
 } qsim_kernel_time;
 
-/* on: 0 off, 1 per-class times, 2 per-class times and per-launch records
+/* Profiling (not in the paper).
+ * on: 0 off, 1 per-class times, 2 per-class times and per-launch records
  * (features of the planned item and its cost) for sim_get_item_times. */
 int sim_set_profiling(qsim *s, int on);
 int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nrows);
@@ -243,20 +267,21 @@ int sim_get_kernel_times(qsim *s, qsim_kernel_time *rows, int max_rows, int *nro
  * highest qubit/32, qubits below 5 /5, 1.
  * --------------------------------------------------------------------------- */
 
-/* Copy out (and clear) the per-launch records: feats holds 16 floats per
+/* Learned planner (not in the paper).  Copy out (and clear) the per-launch records: feats holds 16 floats per
  * record, ms one float (the cost above, in ms); *nitems receives the number
  * of records available
  * (records are cleared only when all of them fit in max_items). */
 int sim_get_item_times(qsim *s, float *feats, float *ms, int max_items, int *nitems);
 
-/* Load the cost model (parameter layout of sim_mlp_*: W1[h][16], b1[h],
+/* Learned planner (not in the paper).  Load the cost model (parameter layout of sim_mlp_*: W1[h][16], b1[h],
  * W2[h][h], b2[h], w3[h], b3); count 0 unloads it.  Copied. */
 int sim_set_cost_model(qsim *s, const float *params, int count, int hidden);
 
-/* Predicted cost (ms) of the last plan made by the learned planner. */
+/* Predicted cost (ms) of the last plan made by the learned planner (not in
+ * the paper). */
 int sim_plan_stats(qsim *s, double *predicted_ms);
 
-/* The cost model's network, trained on the GPU by the library's own
+/* The cost model's network (not in the paper), trained on the GPU by the library's own
  * forward, backward and Adam kernels (FP32, deterministic). */
 typedef struct qsim_mlp qsim_mlp;
 int sim_mlp_param_count(int hidden);
@@ -264,11 +289,13 @@ int sim_mlp_create(int hidden, unsigned long long seed, void *stream, qsim_mlp *
 int sim_mlp_destroy(qsim_mlp *m);
 int sim_mlp_get_params(qsim_mlp *m, float *out, int count);
 int sim_mlp_set_params(qsim_mlp *m, const float *in, int count);
-/* Y[i] = network(X[i*16 .. i*16+15]); host arrays. */
+/* Cost-model inference (not in the paper): Y[i] = network(X[i*16 .. i*16+15]);
+ * host arrays. */
 int sim_mlp_forward(qsim_mlp *m, const float *X, int n, float *Y);
-/* Gradient (parameter layout) of the mean squared error over n samples. */
+/* Cost-model training (not in the paper): gradient (parameter layout) of the
+ * mean squared error over n samples. */
 int sim_mlp_gradient(qsim_mlp *m, const float *X, const float *T, int n, float *grads, float *loss);
-/* Adam (lr, betas 0.9/0.999) on the mean squared error for `epochs` passes
+/* Cost-model training (not in the paper): Adam (lr, betas 0.9/0.999) on the mean squared error for `epochs` passes
  * in minibatches of `batch`; *loss = mean squared error of the last epoch. */
 int sim_mlp_train(qsim_mlp *m, const float *X, const float *T, int n, int epochs, int batch, float lr, float *loss);
 
@@ -286,11 +313,11 @@ int sim_mlp_train(qsim_mlp *m, const float *X, const float *T, int n, int epochs
  * --------------------------------------------------------------------------- */
 typedef struct qsim_batch qsim_batch;
 
-/* Device bytes a batch needs (angles, energies, queue, per-CTA buffers for
+/* Batched sweep (not in the paper).  Device bytes a batch needs (angles, energies, queue, per-CTA buffers for
  * circuits that do not fit in shared memory). */
 int sim_batch_workspace_bytes(int count, const int *nqubits, const int *layers, size_t *bytes);
 
-/* Create a batch.  stream: cudaStream_t to run on (NULL: the batch creates
+/* Batched sweep (not in the paper).  Create a batch.  stream: cudaStream_t to run on (NULL: the batch creates
  * its own non-blocking stream; graph capture needs a non-default stream).
  * workspace: caller-owned device memory of sim_batch_workspace_bytes bytes,
  * 256-byte aligned, or NULL to let the library allocate.  Copies the size
@@ -298,7 +325,7 @@ int sim_batch_workspace_bytes(int count, const int *nqubits, const int *layers, 
 int sim_batch_create(int count, const int *nqubits, const int *layers, double h, void *stream, void *workspace,
                      size_t workspace_bytes, qsim_batch **out);
 
-/* Evaluate all circuits.  angles (host): for each circuit in order, for each
+/* Batched sweep (not in the paper).  Evaluate all circuits.  angles (host): for each circuit in order, for each
  * layer, n RY angles (qubit 0..n-1) then n RZ angles; energies (host):
  * count doubles.  The first call captures the graph (angles H2D, queue and
  * error-flag reset, the two persistent kernels, energies and flag D2H);
@@ -306,18 +333,21 @@ int sim_batch_create(int count, const int *nqubits, const int *layers, double h,
  * (energies then not written). */
 int sim_batch_run(qsim_batch *b, const double *angles, double *energies);
 
-/* Time every candidate launch configuration (threads per CTA 256/512/1024,
+/* Batched sweep (not in the paper).  Time every candidate launch configuration (threads per CTA 256/512/1024,
  * shared-memory threshold m = 12..14 qubits) on these angles, reps timed
  * runs each after one warm-up, keep the fastest (median) and report it. */
 int sim_batch_autotune(qsim_batch *b, const double *angles, int reps, int *threads, int *m);
 
-/* Set the launch configuration of the small-circuit kernel by hand
+/* Batched sweep (not in the paper).  Set the launch configuration of the
+ * small-circuit kernel by hand
  * (QSIM_EINVAL if it cannot run: 2^m must be <= 32 * threads for 256 and
  * 512 threads, <= 16 * 1024 for 1024); circuits with more than m qubits go
  * to the global-memory kernel (256 threads, two CTAs per SM, 2^12-amplitude
  * chunks). */
 int sim_batch_set_config(qsim_batch *b, int threads, int m);
 
+/* Batched sweep (not in the paper): destroy a batch; the last failure's
+ * message. */
 int sim_batch_destroy(qsim_batch *b);
 const char *sim_batch_last_error(const qsim_batch *b);
 
@@ -331,7 +361,7 @@ const char *sim_batch_last_error(const qsim_batch *b);
  *              complex64: 8-byte aligned), read only;
  *   n          1..36; larger registers return QSIM_ENOTSUP because the
  *              built-in scratch array holds partial sums for at most 36
- *              qubits (190 KiB, fixed at build time);
+ *              qubits (320 KiB, fixed at build time);
  *   precision  QSIM_C128 or QSIM_C64;
  *   out        device pointer to n + 1 doubles, written asynchronously:
  *              out[0] = sum_i |psi_i|^2, out[1 + q] = P(qubit q = 1);
@@ -340,11 +370,11 @@ const char *sim_batch_last_error(const qsim_batch *b);
  * precision, QSIM_ECUDA if a launch fails.  No cudaMalloc, cudaFree or
  * allocating library call is made.  The scratch is one array shared by all
  * calls in the process: calls whose kernels overlap on the GPU race on it.
- * The first call on each device looks up the array's device address; make
- * it before any stream capture. */
+ * The first call on each device looks up the array's device address and
+ * the device's SM count; make it before any stream capture. */
 int qsim_probs_all_noalloc(const void *state, int n, int precision, double *out, void *stream);
 
-/* Self-test of the device-side bounded wait.  Every kernel that waits on an
+/* Self-test of the device-side bounded wait (not in the paper).  Every kernel that waits on an
  * mbarrier (bulk copies, tensor-core commits) polls it at most a fixed
  * number of times; on time-out it raises a flag that the host reports as
  * QSIM_ETIMEOUT, and the context stays usable.  This call runs that wait on
@@ -355,10 +385,11 @@ int qsim_probs_all_noalloc(const void *state, int n, int precision, double *out,
  * QSIM_ECUDA if the 4-byte flag cannot be allocated or a call fails. */
 int qsim_selftest_wait_timeout(unsigned int limit, void *stream, double *ms);
 
-/* One-line description of the last failure on this handle ("" if none). */
+/* One-line description of the last failure on this handle ("" if none).
+ * Not in the paper (its Python front end raises exceptions). */
 const char *sim_last_error(const qsim *s);
 
-/* Library build string: version, target architecture. */
+/* Library build string: version, target architecture.  Not in the paper. */
 const char *qsim_build_info(void);
 
 #ifdef __cplusplus

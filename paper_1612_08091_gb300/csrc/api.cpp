@@ -2,8 +2,9 @@
 //
 // Host side only: argument validation, the lazy gate queue, planning and the
 // dispatch of device work onto the handle's stream.  Every arithmetic step
-// on amplitudes runs in the CUDA kernels of gate_kernels.cu,
-// fused_kernel.cu and reduce_kernels.cu.
+// on amplitudes runs in the CUDA kernels (gate_kernels.cu,
+// tmem_block_kernel.cu, diag_kernels.cu, perm_kernels.cu,
+// reduce_kernels.cu).
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -48,6 +49,27 @@ int validate_qubits(qsim *s, const int *a, int na, const int *b, int nb, uint64_
         *mb |= 1ull << b[j];
     }
     return QSIM_OK;
+}
+
+// Start a new norm-control chain of the tensor-core block passes (see
+// tmem_block_kernel.cu): the next block pass applies no correction and the
+// chain steers to `target` (<= 0: that pass's input norm).  Called wherever
+// the norm legitimately changes or becomes unknown to the device records.
+void norm_anchor(qsim *s, double target) {
+    s->norm_chain = false;
+    s->norm_target = target;
+}
+
+// max |U U^dag - I| <= 1e-9: the gate keeps the norm
+bool is_unitary(const GateRec &g) {
+    const int D = 1 << g.t;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            cd acc(0.0, 0.0);
+            for (int k = 0; k < D; ++k) acc += g.m[(size_t)r * D + k] * std::conj(g.m[(size_t)c * D + k]);
+            if (std::abs(acc - cd(r == c ? 1.0 : 0.0, 0.0)) > 1e-9) return false;
+        }
+    return true;
 }
 
 int classify(const GateRec &g) {
@@ -130,6 +152,10 @@ int execute_item(qsim *s, const PlanItem &it) {
     const auto h0 = std::chrono::steady_clock::now();
     int rc;
     size_t ev0 = 0, ev1 = 0;
+    // a non-unitary gate changes the norm: no correction across it
+    bool unitary = true;
+    for (int gi : it.members) unitary = unitary && s->queue[gi].unitary;
+    if (!unitary) norm_anchor(s, -1.0);
     if (s->profiling) {
         if (s->pending.size() >= 4096 && (rc = harvest(s))) return rc;
         if ((rc = record_event(s, &ev0))) return rc;
@@ -167,6 +193,7 @@ int execute_item(qsim *s, const PlanItem &it) {
         bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
     }
     if (rc) return rc;
+    if (!unitary) norm_anchor(s, -1.0);
     const auto h1 = std::chrono::steady_clock::now();
     s->stats.alg_bytes += bytes;
     if (s->profiling) {
@@ -311,9 +338,6 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->norm_tracking = o.no_norm_tracking == 0;
     s->c128_df = o.c128_double_float != 0;
     s->perm_blocks = o.no_permutation_blocks == 0;
-    if (const char *v = getenv("QSIM_TC_KERNEL"))
-        s->tc_variant = (v[0] == 'w') ? 1 : (v[0] == 'd') ? 0 : (v[0] == 's') ? 2 : 3;
-    if (const char *v = getenv("QSIM_TC_STREAMING")) s->tc_streaming = atoi(v);
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {
@@ -322,6 +346,11 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
         }
     }
     cudaGetDevice(&s->device);
+    if (cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || s->sms < 1) {
+        cudaGetLastError();
+        delete s;
+        return QSIM_ECUDA;
+    }
     const size_t need = amp_bytes(s) << n;
     int rc = QSIM_OK;
     if (o.state) {
@@ -385,6 +414,7 @@ int sim_reset(qsim *s, uint64_t basis) {
     if (!s) return QSIM_EINVAL;
     if (basis >> s->n) return set_err(s, QSIM_ERANGE, "basis state out of range");
     s->queue.clear();
+    norm_anchor(s, 1.0);
     return launch_set_basis(s, basis);
 }
 
@@ -405,6 +435,7 @@ int sim_apply(qsim *s, const double *matrix, const int *targets, int t, const in
     g.m.resize((size_t)D * D);
     for (int i = 0; i < D * D; ++i) g.m[i] = cd(matrix[2 * i], matrix[2 * i + 1]);
     g.kind = classify(g);
+    g.unitary = is_unitary(g);
     g.perm = perm_map(g, g.pmap);
     g.diag = true;
     for (int r = 0; r < D && g.diag; ++r)
@@ -484,8 +515,10 @@ int sim_measure(qsim *s, int qubit, double u, int *outcome, double *p_outcome) {
     if (!(p > 0.0)) return set_err(s, QSIM_EZEROPROB, "measured outcome has probability 0");
     rc = run_collapse_mask(s, 1ull << qubit, (uint64_t)b << qubit, 1.0 / std::sqrt(p));
     if (rc) return rc;
+    norm_anchor(s, 1.0);
     *outcome = b;
-    if (p_outcome) *p_outcome = p;
+    // the probability that decided the outcome (relative to the norm)
+    if (p_outcome) *p_outcome = p / (s0 + s1);
     return QSIM_OK;
 }
 
@@ -506,7 +539,9 @@ int sim_collapse(qsim *s, const int *qubits, int m, const int *bits, double *p) 
     if (rc) return rc;
     if (p) *p = pv;
     if (!(pv > 0.0)) return set_err(s, QSIM_EZEROPROB, "projection has probability 0");
-    return run_collapse_mask(s, mask, value, 1.0 / std::sqrt(pv));
+    rc = run_collapse_mask(s, mask, value, 1.0 / std::sqrt(pv));
+    if (!rc) norm_anchor(s, 1.0);
+    return rc;
 }
 
 int sim_measure_all(qsim *s, double u, uint64_t *outcome) {
@@ -514,7 +549,9 @@ int sim_measure_all(qsim *s, double u, uint64_t *outcome) {
     if (!(u >= 0.0 && u < 1.0)) return set_err(s, QSIM_EINVAL, "draw outside [0,1)");
     int rc = flush(s);
     if (rc) return rc;
-    return run_measure_all(s, u, outcome);
+    rc = run_measure_all(s, u, outcome);
+    if (!rc) norm_anchor(s, 1.0);
+    return rc;
 }
 
 int sim_expect(qsim *s, const qsim_pauli *terms, int nterms, double *out) {
@@ -570,6 +607,7 @@ int sim_set_amplitudes(qsim *s, uint64_t offset, uint64_t count, const double *i
     int rc = flush(s);
     if (rc) return rc;
     if (!count) return QSIM_OK;
+    norm_anchor(s, -1.0);
     cudaError_t e;
     if (s->prec == QSIM_C128) {
         e = cudaMemcpyAsync((char *)s->state + offset * 16, in, count * 16, cudaMemcpyHostToDevice, s->stream);
@@ -592,6 +630,8 @@ int sim_state_ptr(qsim *s, void **dev_ptr) {
     if (!s || !dev_ptr) return QSIM_EINVAL;
     int rc = flush(s);
     if (rc) return rc;
+    // the caller may write through the pointer
+    norm_anchor(s, -1.0);
     *dev_ptr = s->state;
     return QSIM_OK;
 }

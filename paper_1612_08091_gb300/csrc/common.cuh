@@ -9,7 +9,6 @@
 
 namespace qsim_dev {
 
-constexpr int kSMs = 152;          // GB300 streaming multiprocessors
 constexpr int kMaxQubits = 36;     // largest register the library accepts
 
 // Sorted list of bit positions to insert (as zeros) into a group counter so

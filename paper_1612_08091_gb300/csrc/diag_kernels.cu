@@ -151,7 +151,7 @@ int diag_block(qsim *s, uint64_t dmask, const cd *dt) {
     const int n = s->n;
     const int cb = std::max(std::min(n, 9), std::min(16, n - 10));
     const uint64_t nchunks = 1ull << (n - cb);
-    const uint64_t grid = nchunks < (uint64_t)kSMs * 8 ? nchunks : (uint64_t)kSMs * 8;
+    const uint64_t grid = nchunks < (uint64_t)s->sms * 8 ? nchunks : (uint64_t)s->sms * 8;
     k_diag_block<Amp><<<(unsigned)grid, kDiagThreads, smem, s->stream>>>((Amp *)s->state, nchunks, cb, k, dev,
                                                                            s->c128_df ? 1 : 0);
     s->stats.launches++;

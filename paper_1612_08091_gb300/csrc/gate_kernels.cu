@@ -429,7 +429,7 @@ int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m) {
 
 int launch_set_basis(qsim *s, uint64_t basis) {
     const uint64_t N = 1ull << s->n;
-    const unsigned grid = (unsigned)std::min<uint64_t>(blocks_for(N, 256), (uint64_t)kSMs * 16);
+    const unsigned grid = (unsigned)std::min<uint64_t>(blocks_for(N, 256), (uint64_t)s->sms * 16);
     if (s->prec == QSIM_C128)
         k_set_basis<double2><<<grid, 256, 0, s->stream>>>((double2 *)s->state, N, basis);
     else

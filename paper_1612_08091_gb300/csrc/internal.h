@@ -31,6 +31,7 @@ struct GateRec {
     int kind = GK_DENSE;
     bool diag = false;  // the matrix is diagonal (the gate only multiplies amplitudes by phases)
     bool perm = false;  // the matrix is a 0/1 permutation matrix (X, CNOT, Toffoli, SWAP ...)
+    bool unitary = true;  // max |U U^dag - I| <= 1e-9 (else the gate may change the norm)
     std::vector<uint8_t> pmap;  // perm: target value c -> the row r with m[r][c] = 1
 };
 
@@ -67,6 +68,7 @@ struct qsim {
     int n = 0;
     int prec = QSIM_C128;
     int device = 0;
+    int sms = 1;  // streaming multiprocessors of the device (sizes the persistent grids)
     void *state = nullptr;
     bool own_state = false;
     void *ws = nullptr;
@@ -82,12 +84,16 @@ struct qsim {
     // tensor-core block path
     bool tc_enabled = true;
     int tc_terms = 3;
-    bool norm_tracking = true;  // scale each block pass by the previous pass's norm ratio
+    bool norm_tracking = true;  // each block pass scales its outputs back to the norm target
     bool c128_df = false;       // complex128 gates and blocks in double-float arithmetic
     bool perm_blocks = true;    // the planners may form permutation blocks
-    int tc_variant = 3;         // 4-5-qubit blocks: 3 k_block_tmem<5> (state operand in tensor memory);
-                                // 0 k_block_tc<2>, 1 k_block_tc_ws, 2 k_block_tc<1> (state operand in shared memory)
-    int tc_streaming = 0;       // streaming (evict-first) cache hints on the block kernel's loads and stores
+    // norm control of the tensor-core block passes (tmem_block_kernel.cu):
+    // norm_chain: the previous block pass's record describes the current
+    // state (false after a reset, a measurement, host-set amplitudes or a
+    // non-unitary gate); norm_target: the norm a new chain steers to (1 after
+    // a reset or a measurement, <= 0: the first pass's input norm)
+    bool norm_chain = false;
+    double norm_target = 1.0;
     uint64_t tc_passes = 0;
     int tc_prev_grid = 0;
     unsigned char *stage_host = nullptr;  // pinned staging for block operands
@@ -119,6 +125,7 @@ constexpr int kMaxPermQubits = 12;
 // Bytes of one amplitude.
 inline size_t amp_bytes(const qsim *s) { return s->prec == QSIM_C128 ? 16 : 8; }
 
+
 // Workspace layout (byte offsets) -----------------------------------------
 constexpr size_t kWsPartials = 0;                       // reduction partials
 constexpr size_t kWsPartialsBytes = 1u << 20;           // 1 MiB
@@ -129,12 +136,14 @@ constexpr size_t kWsChunkBytes = 64u << 10;
 constexpr size_t kWsErr = kWsChunk + kWsChunkBytes;     // device error flags
 constexpr size_t kWsErrBytes = 256;
 constexpr size_t kWsNorm = kWsErr + kWsErrBytes;        // block-pass norm partials
-constexpr size_t kWsNormBytes = 32u << 10;  // 2 slots x 2 sums x up to kMaxTcGrid CTAs
-constexpr int kMaxTcGrid = 608;             // CTAs of a block pass: 4 per SM at most
+constexpr size_t kWsNormBytes = 48u << 10;  // 2 slots x 2 sums x up to kMaxTcGrid CTAs, 2 records
+constexpr int kMaxTcGrid = 1024;            // largest grid of a block pass
 constexpr size_t kWsRing = kWsNorm + kWsNormBytes;      // block operand ring
 constexpr size_t kWsRingBytes = 16u << 20;
 constexpr size_t kWsTotal = kWsRing + kWsRingBytes;
-constexpr int kReduceBlocks = 608;                      // 4 per SM
+constexpr int kMaxReduceBlocks = 2048;                  // largest reduction grid (partials fit in 1 MiB)
+// Grid of the reduction kernels: four CTAs per SM.
+inline int reduce_blocks(const qsim *s) { return 4 * s->sms < kMaxReduceBlocks ? 4 * s->sms : kMaxReduceBlocks; }
 constexpr int kMaxChunks = 4096;
 
 // Error helpers -------------------------------------------------------------
@@ -160,7 +169,8 @@ int stage_operand(qsim *s, const void *data, size_t bytes, unsigned char **dev);
 // Read and clear the device error flags (synchronises the stream).
 int check_device_errors(qsim *s);
 
-// Fused tensor-core block (fused_kernel.cu).  Returns QSIM_ENOTSUP when the
+// Fused 4- or 5-qubit tensor-core block (tmem_block_kernel.cu; a 4-qubit
+// block is embedded in a 5-qubit one).  Returns QSIM_ENOTSUP when the
 // block cannot run on the tensor-core kernel (caller falls back).
 int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m);
 // 5- or 6-qubit block with the state operand in tensor memory (complex64,

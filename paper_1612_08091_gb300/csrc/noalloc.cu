@@ -11,16 +11,18 @@
 // fixed array compiled into the library.
 //
 // The scratch is a file-scope __device__ array of kScratchDoubles doubles
-// (190 KiB).  Every GPU that loads the library holds it until the process
-// exits.  All calls share it: two calls whose kernels overlap on the GPU (for
+// (320 KiB: partial sums of up to 1024 CTAs for up to 36 qubits).  Every GPU
+// that loads the library holds it until the process exits.  All calls share it: two calls whose kernels overlap on the GPU (for
 // example on two streams) race on it and both results are undefined.  Each
 // call overwrites every scratch entry it later reads, so nothing has to start
 // at zero and the contents left by the previous call do not matter.
 //
 // In host code the symbol g_probs_scratch is only a host-side stand-in, not a
 // device address; its device address is looked up once per device with
-// cudaGetSymbolAddress while that device is current.  The first call on a
-// device does that look-up; make that first call before any stream capture.
+// cudaGetSymbolAddress while that device is current, together with the
+// device's SM count (the grid is four CTAs per SM, at most 1024).  The first
+// call on a device does that set-up; make that first call before any stream
+// capture.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -33,15 +35,16 @@ using namespace qsim_dev;
 namespace {
 
 constexpr int kNaThreads = 256;
-constexpr int kNaBlocks = 608;      // 4 per SM
+constexpr int kNaMaxBlocks = 1024;  // largest grid (four CTAs per SM)
 constexpr int kNaMaxValues = 40;    // norm + up to 36 qubits, rounded up
-constexpr int kScratchDoubles = kNaBlocks * kNaMaxValues;
+constexpr int kScratchDoubles = kNaMaxBlocks * kNaMaxValues;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_probs_scratch[kScratchDoubles];
 
 std::mutex g_setup_mutex;
 double *g_scratch_ptr[kMaxDevices] = {nullptr};
+int g_grid_cap[kMaxDevices] = {0};
 
 // Same tiling as the handle-based probabilities pass: a warp owns tiles of
 // 1024 consecutive amplitudes, lane l reads index tile*1024 + 32*j + l.
@@ -124,22 +127,27 @@ __global__ void k_na_finalize(const double *__restrict__ partials, int nblocks, 
     }
 }
 
-// Device address of the scratch array on the current device (looked up once).
-int scratch_for_current_device(double **out) {
+// Device address of the scratch array on the current device and the grid
+// cap (looked up once per device).
+int scratch_for_current_device(double **out, int *grid_cap) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return QSIM_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return QSIM_ENOTSUP;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
         void *p = nullptr;
+        int sms = 0;
         cudaError_t e = cudaGetSymbolAddress(&p, g_probs_scratch);
-        if (e != cudaSuccess || !p) {
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || !p || sms < 1) {
             cudaGetLastError();
             return QSIM_ECUDA;
         }
+        g_grid_cap[dev] = 4 * sms < kNaMaxBlocks ? 4 * sms : kNaMaxBlocks;
         g_scratch_ptr[dev] = (double *)p;
     }
     *out = g_scratch_ptr[dev];
+    *grid_cap = g_grid_cap[dev];
     return QSIM_OK;
 }
 
@@ -151,11 +159,12 @@ int probs_noalloc(const void *state, int n, double *out, cudaStream_t stream) {
         return cudaGetLastError() == cudaSuccess ? QSIM_OK : QSIM_ECUDA;
     }
     double *scratch = nullptr;
-    int rc = scratch_for_current_device(&scratch);
+    int cap = 0;
+    int rc = scratch_for_current_device(&scratch, &cap);
     if (rc) return rc;
     const uint64_t ntiles = 1ull << (n - 10);
     const uint64_t want = (ntiles + (kNaThreads / 32) - 1) / (kNaThreads / 32);
-    const int grid = (int)(want < (uint64_t)kNaBlocks ? want : (uint64_t)kNaBlocks);
+    const int grid = (int)(want < (uint64_t)cap ? want : (uint64_t)cap);
     k_na_probs_tiles<Amp><<<grid, kNaThreads, 0, stream>>>(psi, n, ntiles, scratch);
     if (cudaGetLastError() != cudaSuccess) return QSIM_ECUDA;
     k_na_finalize<<<1, 64, 0, stream>>>(scratch, grid, n + 1, out);

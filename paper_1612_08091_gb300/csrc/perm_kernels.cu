@@ -299,10 +299,10 @@ int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint
     if (cycles.empty()) return QSIM_OK;  // f is the identity
     const int nfree = s->n - m - __builtin_popcountll(cmask);
     const uint64_t nslices = 1ull << (nfree - slice_bits);
-    if ((uint64_t)cycles.size() * nslices < (uint64_t)kSMs) return QSIM_ENOTSUP;
+    if ((uint64_t)cycles.size() * nslices < (uint64_t)s->sms) return QSIM_ENOTSUP;
     // the bulk-copy walk: 16 KB slices, at least two tasks per SM
     const bool use_bulk = (fixed & ((1ull << bulk_bits) - 1ull)) == 0 && nfree >= bulk_bits &&
-                          (uint64_t)cycles.size() * (1ull << (nfree - bulk_bits)) >= 2ull * kSMs;
+                          (uint64_t)cycles.size() * (1ull << (nfree - bulk_bits)) >= 2ull * (uint64_t)s->sms;
     std::stable_sort(cycles.begin(), cycles.end(),
                      [](const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) { return a.size() > b.size(); });
     const size_t ncyc = cycles.size();
@@ -339,7 +339,7 @@ int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint
             attr[s->device] = true;
         }
         // two CTAs (one pipeline each) per SM
-        const uint64_t grid = ntasks < (uint64_t)kSMs * 2 ? ntasks : (uint64_t)kSMs * 2;
+        const uint64_t grid = ntasks < (uint64_t)s->sms * 2 ? ntasks : (uint64_t)s->sms * 2;
         k_permute_cycles_bulk<<<(unsigned)grid, 32, smem, s->stream>>>(
             (unsigned char *)s->state, ins, cmask, (int)sizeof(Amp), bulk_bits, (const uint32_t *)dev,
             (const uint32_t *)dev + total, (uint32_t)ncyc, bslices, (unsigned int *)((char *)s->ws + kWsErr));
@@ -366,7 +366,7 @@ int permute_cycles(qsim *s, const uint64_t *perm, const int *qubits, int m, uint
     if (rc) return rc;
     const uint64_t ntasks = (uint64_t)ncyc * nslices;
     // 64 registers a thread: four CTAs of 256 threads resident per SM
-    const uint64_t grid = ntasks < (uint64_t)kSMs * 4 ? ntasks : (uint64_t)kSMs * 4;
+    const uint64_t grid = ntasks < (uint64_t)s->sms * 4 ? ntasks : (uint64_t)s->sms * 4;
     const size_t smem = sizeof(uint64_t) * cycles[0].size();  // the longest cycle (<= 2^12 entries)
     k_permute_cycles<<<(unsigned)grid, kCycThreads, smem, s->stream>>>(
         (float4 *)s->state, ins, cmask >> amp_shift, (const uint64_t *)dev,
@@ -441,7 +441,7 @@ int permute(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qm
         if (e != cudaSuccess) return cuda_err(s, e, "permutation kernel attribute");
         attr[which][s->device] = true;
     }
-    const uint64_t grid = ntiles < (uint64_t)kSMs * 8 ? ntiles : (uint64_t)kSMs * 8;
+    const uint64_t grid = ntiles < (uint64_t)s->sms * 8 ? ntiles : (uint64_t)s->sms * 8;
     k_permute<Amp><<<(unsigned)grid, kPermThreads, smem, s->stream>>>(
         (Amp *)s->state, ntiles, ins, cmask, m, c, v_fast ? 1 : 0, (const uint64_t *)dev,
         (const uint64_t *)dev + 128, (const uint32_t *)(dev + sizeof(uint64_t) * (128 + R)));

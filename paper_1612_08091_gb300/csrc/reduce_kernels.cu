@@ -729,7 +729,7 @@ int probs_all_t(qsim *s, double *p1, double *norm2_out) {
         if (rc) return rc;
     } else {
         const uint64_t ntiles = 1ull << (n - 10);
-        const unsigned grid = grid_for(ntiles, kRedThreads / 32, kReduceBlocks);
+        const unsigned grid = grid_for(ntiles, kRedThreads / 32, reduce_blocks(s));
         k_probs_tiles<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, n, ntiles, ws_partials(s));
         s->stats.launches++;
         cudaError_t e = cudaGetLastError();
@@ -748,7 +748,7 @@ template <typename Amp>
 int bit_sums_t(qsim *s, int q, bool only_set, double *s0, double *s1) {
     const int n = s->n;
     const uint64_t ntiles = (1ull << (n - 10)) >> ((only_set && q >= 10) ? 1 : 0);
-    const unsigned grid = grid_for(ntiles, kRedThreads / 32, kReduceBlocks);
+    const unsigned grid = grid_for(ntiles, kRedThreads / 32, reduce_blocks(s));
     k_bit_sums<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, q, ntiles, only_set ? 1 : 0,
                                                           ws_partials(s));
     s->stats.launches++;
@@ -768,7 +768,7 @@ int masked_sum_t(qsim *s, uint64_t mask, uint64_t value, double *out) {
         return bit_sums_t<Amp>(s, __builtin_ctzll(mask), true, nullptr, out);
     const InsertSpec ins = make_spec(mask);
     const uint64_t ngroups = 1ull << (s->n - ins.m);
-    const unsigned grid = grid_for(ngroups, kRedThreads, kReduceBlocks);
+    const unsigned grid = grid_for(ngroups, kRedThreads, reduce_blocks(s));
     k_masked_sum<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, ngroups, ins, value, ws_partials(s));
     s->stats.launches++;
     cudaError_t e = cudaGetLastError();
@@ -780,7 +780,7 @@ template <typename Amp>
 int split_sum_t(qsim *s, int q, double *s0, double *s1) {
     if (s->n >= 10) return bit_sums_t<Amp>(s, q, false, s0, s1);
     const uint64_t npairs = 1ull << (s->n - 1);
-    const unsigned grid = grid_for(npairs, kRedThreads, kReduceBlocks);
+    const unsigned grid = grid_for(npairs, kRedThreads, reduce_blocks(s));
     k_split_sum<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, npairs, q, ws_partials(s));
     s->stats.launches++;
     cudaError_t e = cudaGetLastError();
@@ -801,12 +801,12 @@ int collapse_t(qsim *s, uint64_t mask, uint64_t value, double scale) {
     if (s->n >= 1 && __builtin_popcountll(mask) == 1) {
         const int q = __builtin_ctzll(mask);
         const uint64_t npairs = N >> 1;
-        const unsigned grid = grid_for(npairs, 256, kSMs * 16);
+        const unsigned grid = grid_for(npairs, 256, s->sms * 16);
         k_collapse_bit<Amp><<<grid, 256, 0, s->stream>>>((Amp *)s->state, npairs, q, value ? 1 : 0, scale, shi, slo);
         s->stats.launches++;
         return cuda_err(s, cudaGetLastError(), "collapse launch");
     }
-    const unsigned grid = grid_for(N, 256, kSMs * 16);
+    const unsigned grid = grid_for(N, 256, s->sms * 16);
     k_collapse_mask<Amp><<<grid, 256, 0, s->stream>>>((Amp *)s->state, N, mask, value, scale, shi, slo);
     s->stats.launches++;
     return cuda_err(s, cudaGetLastError(), "collapse launch");
@@ -853,7 +853,7 @@ int expect_t(qsim *s, const qsim_pauli *terms, int nterms, double *out) {
             if (rc) return rc;
         } else {
             const uint64_t ntiles = 1ull << (n - 10);
-            const unsigned grid = grid_for(ntiles, kZThreads / 32, 2 * kReduceBlocks);
+            const unsigned grid = grid_for(ntiles, kZThreads / 32, 2 * reduce_blocks(s));
             k_expect_z_tiles<Amp><<<grid, kZThreads, 0, s->stream>>>((const Amp *)s->state, ntiles, T,
                                                                          ws_partials(s));
             s->stats.launches++;
@@ -884,7 +884,7 @@ int expect_t(qsim *s, const qsim_pauli *terms, int nterms, double *out) {
             ++i;
         }
         const uint64_t npairs = N >> 1;
-        const unsigned grid = grid_for(npairs, kRedThreads, kReduceBlocks);
+        const unsigned grid = grid_for(npairs, kRedThreads, reduce_blocks(s));
         k_expect_x<Amp><<<grid, kRedThreads, 0, s->stream>>>((const Amp *)s->state, npairs, T, ws_partials(s));
         s->stats.launches++;
         cudaError_t e = cudaGetLastError();
@@ -953,7 +953,7 @@ int measure_all_t(qsim *s, double u, uint64_t *outcome) {
         if (res.index == ~0ull) return set_err(s, QSIM_EZEROPROB, "no amplitude of non-zero weight");
     }
     const double mag = std::sqrt(res.re * res.re + res.im * res.im);
-    const unsigned grid = grid_for(N, 256, kSMs * 16);
+    const unsigned grid = grid_for(N, 256, s->sms * 16);
     k_write_basis<Amp><<<grid, 256, 0, s->stream>>>((Amp *)s->state, N, res.index, res.re / mag, res.im / mag);
     s->stats.launches++;
     e = cudaGetLastError();

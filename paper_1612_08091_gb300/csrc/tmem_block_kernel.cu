@@ -42,11 +42,26 @@
 //   t into TMEM -> thread 0 issues N/16 tcgen05.mma M128 N K16 per product
 //   and commits them to an mbarrier -> issue the loads of tile t+1 (2^K
 //   amplitudes per thread held in registers: 96 or 128 KB in flight per SM).
-// The other CTAs on the SM fill this CTA's waits.  Norm tracking: per-CTA
-// FP64 sums of |x|^2 and |y|^2, and the outputs scaled by sqrt(in/out) of
-// the previous block pass (of any block kernel).  Every wait is bounded; on
+// The other CTAs on the SM fill this CTA's waits.  Every wait is bounded; on
 // time-out the kernel raises an error flag in the workspace, frees its
 // tensor memory and returns.
+//
+// Norm control.  The bf16 split and the FP32 accumulation shrink the norm by
+// a few 1e-7 per pass, and the shrink is systematic on structured states
+// (Grover's search repeats the same blocks on a state whose amplitudes are
+// mostly equal), so uncorrected it adds up over 1e5 passes.  Every pass
+// writes per-CTA FP64 sums of |x|^2 over its inputs (a) and of |y|^2 over its
+// raw outputs (b), and CTA 0 records the scale s it applied and the norm
+// target T.  The next pass knows the norm the previous one left, s^2 b, and
+// its shrink ratio b / a; assuming the same ratio, it scales its outputs by
+//     s' = sqrt(T / (s^2 b * b / a)),
+// which brings the norm back to T after every pass.  Errors therefore do
+// not accumulate: what remains is one pass's change of shrink ratio and the
+// drift of the non-tensor-core passes since the previous block pass, both
+// corrected by the pass after.  T is 1 after a reset or a measurement and the
+// input norm of the first pass otherwise (host-set amplitudes, a
+// non-unitary gate); the host starts a new chain (no previous record, scale
+// 1) at each such point.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -87,12 +102,17 @@ struct TmArgs {
     uint64_t ntiles;           // 2^(n - K - 7)
     InsertSpec vspec;          // the K + 7 positions of V = S u F, ascending
     unsigned int *err;         // error flag
-    // norm tracking: this pass writes per-CTA sums of |x|^2 (inputs) and
-    // |y|^2 (raw outputs) to norm_out[0..grid) and [kMaxTcGrid..); the
-    // previous block pass's sums (norm_prev, prev_grid CTAs, or null) give
-    // the output scale sqrt(in/out)
+    // norm control: this pass writes per-CTA sums of |x|^2 (inputs) and
+    // |y|^2 (raw outputs) to norm_out[0..grid) and [kMaxTcGrid..), and CTA 0
+    // writes {scale applied, target} to rec_out; the previous block pass's
+    // sums (norm_prev, prev_grid CTAs) and record (rec_prev) give this
+    // pass's scale; both null start a chain with scale 1 and target
+    // `target` (<= 0: this pass's own input norm)
     double *norm_out;
+    double *rec_out;
     const double *norm_prev;
+    const double *rec_prev;
+    double target;
     int prev_grid;
     int fpos[7];               // tile column bit j <-> qubit fpos[j]
     uint64_t rdep[64];         // address bits of block row r
@@ -143,18 +163,30 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // output scale from the previous pass's input/output norms, summed
-        // in a fixed order
+        // output scale from the previous pass's sums (fixed summation order,
+        // so every CTA computes the same value) and record
         float sc = 1.0f;
+        double T = args.target;
         if (args.norm_prev) {
             double a = 0.0, b = 0.0;
             for (int i = 0; i < args.prev_grid; ++i) {
                 a += args.norm_prev[i];
                 b += args.norm_prev[kMaxTcGrid + i];
             }
-            if (a > 0.0 && b > 0.0 && a < 1e300 && b < 1e300) sc = (float)sqrt(a / b);
+            const double sp = args.rec_prev[0], tp = args.rec_prev[1];
+            T = tp > 0.0 ? tp : a;
+            if (T > 0.0 && a > 0.0 && b > 0.0 && sp > 0.0 && a < 1e300 && b < 1e300 && T < 1e300) {
+                const double s2 = (T / (sp * sp * b)) * (a / b);
+                // a correction this large means the chain was not restarted
+                // where the norm changed; leave the pass unscaled
+                if (s2 > 0.25 && s2 < 4.0) sc = (float)sqrt(s2);
+            }
         }
         *s_scale = sc;
+        if (blockIdx.x == 0 && args.rec_out) {
+            args.rec_out[0] = (double)sc;
+            args.rec_out[1] = T;
+        }
     }
     __syncthreads();
     if (tid == 0) bulk_load(B, args.rec, args.rec_bytes, &bars[0]);
@@ -203,13 +235,15 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
         };
         auto epilogue = [&](uint64_t tt) {
             float2 *p = args.psi + insert_zeros(tt, args.vspec) + coff;
-            float ssq = 0.f;
+            // four FP32 partial sums (chains of 2^K / 2 terms): the rounding
+            // of a long chain is systematic when many amplitudes are equal
+            float ssq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kN / 32; ++chunk) {
                 float d[32];  // rows 16 chunk .. 16 chunk + 15, (re, im) interleaved
                 tmem_ld32(lanes + Sh::kColD + chunk * 32, d);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) ssq = fmaf(d[q], d[q], ssq);
+                for (int q = 0; q < 32; ++q) ssq[q & 3] = fmaf(d[q], d[q], ssq[q & 3]);
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) {
                     const int r = chunk * 16 + q;
@@ -229,7 +263,7 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                     }
                 }
             }
-            nrm_out += (double)ssq;
+            nrm_out += (double)((ssq[0] + ssq[1]) + (ssq[2] + ssq[3]));
         };
 
         uint64_t t = blockIdx.x;
@@ -248,22 +282,24 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                     atomicOr(args.err, 2u);
                 }
             }
-            float xsq = 0.f;
+            float xsq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kRows / 16; ++chunk) {
                 uint32_t hw[16], lw[16];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float4 x = v[chunk * 8 + j];
-                    xsq = fmaf(x.x, x.x, fmaf(x.y, x.y, xsq));
-                    xsq = fmaf(x.z, x.z, fmaf(x.w, x.w, xsq));
+                    xsq[0] = fmaf(x.x, x.x, xsq[0]);
+                    xsq[1] = fmaf(x.y, x.y, xsq[1]);
+                    xsq[2] = fmaf(x.z, x.z, xsq[2]);
+                    xsq[3] = fmaf(x.w, x.w, xsq[3]);
                     split_pair(x.x, x.y, hw[2 * j], lw[2 * j]);
                     split_pair(x.z, x.w, hw[2 * j + 1], lw[2 * j + 1]);
                 }
                 tmem_st16(lanes + Sh::kColAHi + chunk * 16, hw);
                 tmem_st16(lanes + Sh::kColALo + chunk * 16, lw);
             }
-            nrm_in += (double)xsq;
+            nrm_in += (double)((xsq[0] + xsq[1]) + (xsq[2] + xsq[3]));
             tcgen05_wait_st();
             tc_fence_before();
             if (__syncthreads_or(failed)) {
@@ -408,18 +444,58 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
     a.nsplit = nsplit;
     a.ntiles = 1ull << (n - Sh::kTileBits);
     a.err = (unsigned int *)((char *)s->ws + kWsErr);
-    const uint64_t cap = (uint64_t)kSMs * Sh::kCtasPerSm;
+    uint64_t cap = (uint64_t)s->sms * Sh::kCtasPerSm;
+    if (cap > (uint64_t)kMaxTcGrid) cap = kMaxTcGrid;
     const uint64_t grid = a.ntiles < cap ? a.ntiles : cap;
+    // norm control: sums in slot (pass & 1), records after both slots
     double *slots = (double *)((char *)s->ws + kWsNorm);
+    double *recs = slots + 4 * kMaxTcGrid;
     const int slot = (int)(s->tc_passes & 1);
+    const bool chain = s->norm_tracking && s->norm_chain;
     a.norm_out = slots + slot * 2 * kMaxTcGrid;
-    a.norm_prev = (s->norm_tracking && s->tc_passes > 0) ? slots + (slot ^ 1) * 2 * kMaxTcGrid : nullptr;
+    a.rec_out = recs + 2 * slot;
+    a.norm_prev = chain ? slots + (slot ^ 1) * 2 * kMaxTcGrid : nullptr;
+    a.rec_prev = chain ? recs + 2 * (slot ^ 1) : nullptr;
+    a.target = s->norm_target;
     a.prev_grid = s->tc_prev_grid;
     kernel<<<(unsigned)grid, kTmThreads, smem, s->stream>>>(a);
     s->stats.launches++;
     s->tc_passes++;
     s->tc_prev_grid = (int)grid;
+    s->norm_chain = true;
     return cuda_err(s, cudaGetLastError(), "tmem block launch");
+}
+
+// Embed a k-qubit block (k < 5) into the 5-qubit block on its qubits and the
+// lowest qubits outside them (identity on the added ones), so that it runs
+// on the 5-qubit kernel.  q5 receives the 5 qubits in ascending order.
+void pad_to_five(int n, const int *q, int k, const cd *m, int *q5, std::vector<cd> &m5) {
+    uint64_t S = 0;
+    for (int j = 0; j < k; ++j) S |= 1ull << q[j];
+    uint64_t S5 = S;
+    for (int b = 0; b < n && __builtin_popcountll(S5) < 5; ++b) S5 |= 1ull << b;
+    int kk = 0;
+    for (int b = 0; b < n; ++b)
+        if ((S5 >> b) & 1ull) q5[kk++] = b;
+    int pos[5] = {0, 0, 0, 0, 0};  // position in q5 of block qubit j
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < 5; ++i)
+            if (q5[i] == q[j]) pos[j] = i;
+    uint32_t added = 0;  // positions (in q5) of the added qubits
+    for (int i = 0; i < 5; ++i)
+        if (!((S >> q5[i]) & 1ull)) added |= 1u << i;
+    const int D = 1 << k;
+    m5.assign(32 * 32, cd(0.0, 0.0));
+    for (int r = 0; r < 32; ++r)
+        for (int c = 0; c < 32; ++c) {
+            if ((r & added) != (c & added)) continue;
+            int ro = 0, co = 0;
+            for (int j = 0; j < k; ++j) {
+                ro |= ((r >> pos[j]) & 1) << j;
+                co |= ((c >> pos[j]) & 1) << j;
+            }
+            m5[r * 32 + c] = m[ro * D + co];
+        }
 }
 
 }  // namespace
@@ -427,4 +503,13 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
 int launch_block_tmem(qsim *s, const int *qubits, int k, const cd *m) {
     if (s->prec != QSIM_C64 || !s->tc_enabled || (k != 5 && k != 6) || s->n < k + 7) return QSIM_ENOTSUP;
     return k == 6 ? launch_tmem<6>(s, qubits, m) : launch_tmem<5>(s, qubits, m);
+}
+
+int launch_block_tc(qsim *s, const int *qubits, int k, const cd *m) {
+    if (s->prec != QSIM_C64 || !s->tc_enabled || k < 4 || k > 5 || s->n < 12) return QSIM_ENOTSUP;
+    if (k == 5) return launch_tmem<5>(s, qubits, m);
+    int q5[5];
+    std::vector<cd> m5;
+    pad_to_five(s->n, qubits, k, m, q5, m5);
+    return launch_tmem<5>(s, q5, m5.data());
 }

@@ -793,8 +793,11 @@ int sim_batch_workspace_bytes(int count, const int *nqubits, const int *layers, 
         nmax = std::max(nmax, nqubits[i]);
     }
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = kSMs;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return QSIM_ECUDA;
+    }
     const size_t max_grid = (size_t)sms * 4;
     const size_t gstride = nmax > 12 ? ((size_t)1 << nmax) : 0;
     size_t s = align256(sizeof(double) * nang) + align256(sizeof(double) * count) + 3 * align256(sizeof(int) * count) +

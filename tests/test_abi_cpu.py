@@ -61,3 +61,51 @@ def test_product_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.findall(r"^\s*(?:import|from)\s+(\w+)", text, flags=re.M), f
                 assert "qsim_oracle" not in text, f
+
+
+def declaration_comments():
+    """Each function declared in include/*.h with the comment block that
+    governs it: the nearest comment above the declaration, where consecutive
+    declarations without a comment between them share the one above the
+    first."""
+    out = {}
+    decl = re.compile(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*\*?\s*\b(sim_[a-z0-9_]+|qsim_[a-z0-9_]+)\s*\(")
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", h)).read().split("\n")
+        for i, line in enumerate(lines):
+            m = decl.match(line)
+            if not m:
+                continue
+            j = i - 1
+            # skip earlier declarations of the same group (and their continuation lines)
+            while j >= 0 and "*/" not in lines[j] and lines[j].strip():
+                j -= 1
+            if j < 0 or "*/" not in lines[j]:
+                out[m.group(1)] = ""
+                continue
+            k = j
+            while k >= 0 and "/*" not in lines[k]:
+                k -= 1
+            text = " ".join(re.sub(r"^\s*(/\*+|\*+/?)?", "", l) for l in lines[k:j + 1])
+            out[m.group(1)] = re.sub(r"\s+", " ", text)
+    return out
+
+
+def test_every_declaration_cites_its_passage():
+    """Every entry point of the boundary names the passage of the paper that
+    defines its operation (a section, figure or appendix), or says that the
+    paper has no counterpart."""
+    comments = declaration_comments()
+    assert set(comments) == set(declared_functions())
+    marker = re.compile(r"Sec\.\s*\d|Appendix\s+A|Fig\.\s*\d|not in the paper|The paper has no counterpart",
+                        re.I)
+    bad = sorted(name for name, c in comments.items() if not marker.search(c))
+    assert not bad, bad
+    # the calls that carry the paper's operations cite a passage, not only "not in the paper"
+    for name in ("sim_create", "sim_destroy", "sim_apply", "sim_flush", "sim_prob", "sim_probs_all",
+                 "sim_measure", "sim_collapse", "sim_measure_all", "sim_get_amplitudes", "sim_apply_permutation",
+                 "sim_set_fusion"):
+        assert re.search(r"Sec\.\s*\d|Appendix\s+A", comments[name]), name
+    assert re.search(r"not in the paper", comments["sim_expect"], re.I)

@@ -1,0 +1,109 @@
+"""Long complex64 runs: the raw reads stay within 1e-5 after about 1.5e5
+tensor-core block passes.
+
+Grover's search (Appendix A.2) is the longest of the benchmark workloads:
+154,409 passes at 28 qubits.  Its state is almost uniform, so the rounding of
+the bf16 split and of the FP32 accumulation repeats itself from pass to pass
+and would add up over the run.  Here the same iteration runs on 20 qubits
+for as many passes, and the raw norm, the marked item's probability, the
+single-qubit probabilities and <sum Z_i Z_i+1> are compared, without any
+division by the norm, with the closed form of the search after k
+iterations: amplitude (-1)^k sin((2k+1) theta) on the marked item and
+(-1)^k cos((2k+1) theta) / sqrt(N - 1) elsewhere, sin theta = 2^(-n/2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1612_08091_gb300 as q
+
+    q.load()
+    return q
+
+
+def grover_closed_form(n, marked, k):
+    theta = math.asin(2.0 ** (-n / 2))
+    sign = (-1) ** k
+    a_m = sign * math.sin((2 * k + 1) * theta)
+    a_o = sign * math.cos((2 * k + 1) * theta) / math.sqrt((1 << n) - 1)
+    return a_m, a_o
+
+
+def test_grover20_150k_passes_raw_reads(qs):
+    n = 20
+    marked = cg.grover_marked(n, seed=2017)
+    iters = 15000
+    chunk = 500
+    body = cg.grover_iteration_ops(n, marked)
+    with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
+        sim.run([cg.op("H", (q,)) for q in range(n)])
+        for _ in range(iters // chunk):
+            sim.run(body * chunk)
+            sim.flush()
+        st = sim.stats()
+        am = sim.get_amplitudes(marked, 1)[0]
+        p1, nrm = sim.probs_all()
+        zz = sim.expect(cg.zz_chain_terms(n))
+        psi = sim.get_amplitudes()
+    a_m, a_o = grover_closed_form(n, marked, iters)
+    bits = np.array([(marked >> q) & 1 for q in range(n)])
+    N = 1 << n
+    p1_want = bits * a_m ** 2 + a_o ** 2 * ((N >> 1) - bits)
+    s = 1 - 2 * bits  # Z eigenvalue of the marked item's bits
+    zz_want = sum(s[i] * s[i + 1] for i in range(n - 1)) * (a_m ** 2 - a_o ** 2)
+    print("Grover-20, %d iterations, %d passes: |norm2-1| %.2e, P(marked) %.8f (closed form %.8f), "
+          "<sum ZZ> %.8f (%.8f)" % (iters, st["passes"], abs(nrm - 1.0), abs(am) ** 2, a_m ** 2, zz, zz_want))
+    assert st["passes"] >= 140000
+    assert abs(nrm - 1.0) <= 1e-5
+    assert abs(np.vdot(psi, psi).real - 1.0) <= 1e-5
+    assert abs(abs(am) ** 2 - a_m ** 2) <= 1e-5
+    np.testing.assert_allclose(p1, p1_want, atol=1e-5)
+    assert abs(zz - zz_want) <= 1e-5 * (n - 1)
+    # the state itself, up to the global phase the closed form fixes
+    want = np.full(N, a_o, dtype=np.complex128)
+    want[marked] = a_m
+    assert abs(np.vdot(want, psi)) ** 2 >= 1 - 1e-5
+
+
+def test_norm_control_restarts_after_host_writes_and_measurement(qs, oracle_mod):
+    """The norm target follows the state: amplitudes written by the host with
+    norm 4 stay at norm 4 through block passes; after a measurement the
+    target is 1 again.  A non-unitary gate (a projector) changes the norm and
+    the block passes after it keep the new norm."""
+    n = 16
+    ops = cg.random_u3_brickwork(n, 12, seed=11)
+    psi = 2.0 * cg.random_state(n, seed=12)
+    ref = oracle_mod.OracleSim(n, psi=psi)
+    oracle_mod.run_ops(ref, ops)
+    with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
+        sim.set_amplitudes(psi)
+        sim.run(ops)
+        _, nrm = sim.probs_all()
+        assert abs(nrm - 4.0) <= 4e-5
+        got = sim.get_amplitudes()
+        assert np.max(np.abs(got - ref.psi)) <= 1e-3
+        b, _ = sim.measure(3, 0.5)
+        sim.run(ops)
+        _, nrm = sim.probs_all()
+        assert abs(nrm - 1.0) <= 1e-5
+        # projector onto |1> of qubit 0 (halves the norm, roughly), then
+        # unitary blocks: the norm after them is the projected one
+        proj = np.array([[0, 0], [0, 1]], dtype=np.complex128)
+        ref2 = oracle_mod.OracleSim(n, psi=sim.get_amplitudes())
+        sim.apply(proj, [0])
+        ref2.apply(proj, [0])
+        sim.run(ops)
+        oracle_mod.run_ops(ref2, ops)
+        _, nrm = sim.probs_all()
+    assert abs(nrm - ref2.norm2()) <= 1e-5

@@ -60,17 +60,19 @@ def test_fused_block_placements(qs, oracle_mod, n, S, terms):
     assert np.max(np.abs(got - ref.psi)) <= (2e-4 if terms == 3 else 2e-5)
 
 
-def test_tc_matches_cuda_core_blocks(qs):
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_tc_and_cuda_core_blocks_against_oracle(qs, oracle_mod, tensor_cores):
     n = 18
     ops = cg.random_u3_brickwork(n, 6, seed=5)
-    with qs.Simulator(n, precision="c64", fusion="greedy", kmax=5) as a, \
-            qs.Simulator(n, precision="c64", fusion="greedy", kmax=5, tensor_cores=False) as b:
+    ref = oracle_mod.OracleSim(n)
+    oracle_mod.run_ops(ref, ops)
+    with qs.Simulator(n, precision="c64", fusion="greedy", kmax=5, tensor_cores=tensor_cores) as a:
         a.set_profiling(True)
         a.run(ops)
-        b.run(ops)
-        ga, gb = a.get_amplitudes(), b.get_amplitudes()
-        assert a.kernel_times()["block_tc"]["launches"] > 0
-    assert infidelity(ga, gb) <= TOL64_INFID
+        got = a.get_amplitudes()
+        kt = a.kernel_times()
+    assert kt.get("block_tc" if tensor_cores else "block_dense", {}).get("launches", 0) > 0, kt
+    assert infidelity(ref.psi, got) <= TOL64_INFID
 
 
 def test_tc_long_circuit_accuracy(qs, oracle_mod):
@@ -96,6 +98,6 @@ def test_tc_long_circuit_accuracy(qs, oracle_mod):
     for terms, track, inf, drift, eerr in rows:
         assert inf <= TOL64_INFID
         if track:
-            # the correction lags one pass behind the drift it measures
-            assert drift <= 5e-6
+            # every block pass scales its output back to the norm target
+            assert drift <= 2e-6
             assert eerr <= 1e-5 * len(terms_zz)

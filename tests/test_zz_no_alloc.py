@@ -1,10 +1,13 @@
-"""The allocation-free probabilities call, checked against the regular one.
+"""The allocation-free probabilities call, checked against the oracle and
+the regular one.
 
 qsim_probs_all_noalloc serves callers that cannot allocate GPU memory when
 they ask for probabilities (their device memory belongs to another pool, a
-fixed real-time budget, an allocation-free callback).  It must give what
-sim_probs_all gives, within the tests' tolerances, on consecutive calls that
-share its built-in scratch array.  This file is named to be collected last.
+fixed real-time budget, an allocation-free callback).  It must give what the
+FP64 oracle and sim_probs_all give, within the tests' tolerances, on
+consecutive calls that share its built-in scratch array, and it must leave
+the device's free memory unchanged.  This file is named to be collected
+last.
 """
 import ctypes
 
@@ -16,35 +19,53 @@ import circuitgen as cg
 pytestmark = pytest.mark.gpu
 
 
+def _noalloc(lib):
+    fn = lib.qsim_probs_all_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    return fn
+
+
+# 7: the one-block kernel; 10: the smallest tiled register; 16: several
+# tiles per CTA; 24: more tiles than the grid holds (grid-stride loop)
 @pytest.mark.parametrize("prec,tol", [("c128", 1e-12), ("c64", 1e-6)])
-def test_noalloc_probs_match_sim_probs_all(prec, tol):
+def test_noalloc_probs_match_oracle_and_sim_probs_all(prec, tol, oracle_mod):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     import paper_1612_08091_gb300 as q
 
-    lib = q.load()
-    fn = lib.qsim_probs_all_noalloc
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
-    fn.restype = ctypes.c_int
+    fn = _noalloc(q.load())
     precision = 0 if prec == "c128" else 1
     stream = torch.cuda.current_stream()
-    for n in (7, 16):
+    for n in (7, 10, 16, 24):
+        psi = cg.random_state(n, seed=40 + n)
+        second = [cg.op("U3", (n - 1,), (), (0.7, 1.1, -0.4)), cg.op("X", (0,), (3,))]
         with q.Simulator(n, precision=prec) as sim:
-            sim.set_amplitudes(cg.random_state(n, seed=40 + n))
+            sim.set_amplitudes(psi)
             out = torch.full((n + 1,), float("nan"), dtype=torch.float64, device="cuda")
             for call in range(2):
+                ref = oracle_mod.OracleSim(n, psi=psi)
                 if call == 1:  # change the state between the two calls
-                    sim.apply_op(cg.op("U3", (n - 1,), (), (0.7, 1.1, -0.4)))
-                    sim.apply_op(cg.op("X", (0,), (3,)))
+                    sim.run(second)
+                    oracle_mod.run_ops(ref, second)
                 ref_p1, ref_norm = sim.probs_all()
                 ptr = sim.state_ptr()
+                torch.cuda.synchronize()
+                free_before = torch.cuda.mem_get_info()[0]
                 rc = fn(ptr, n, precision, out.data_ptr(), stream.cuda_stream)
                 assert rc == 0
                 torch.cuda.synchronize()
+                if call == 1:  # the first call on the device may load the module
+                    assert torch.cuda.mem_get_info()[0] == free_before
                 got = out.cpu().numpy()
+                # against the regular entry point
                 assert abs(got[0] - ref_norm) <= tol
                 np.testing.assert_allclose(got[1:], ref_p1, atol=tol)
+                # against the FP64 oracle (complex64: the amplitudes themselves
+                # are rounded to FP32, relative 2^-24 each)
+                assert abs(got[0] - ref.norm2()) <= tol
+                np.testing.assert_allclose(got[1:], ref.probs_all(), atol=tol)
     # sizes beyond the scratch array and bad arguments are rejected
     dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
     assert fn(dummy.data_ptr(), 37, precision, dummy.data_ptr(), None) == 9  # ENOTSUP
