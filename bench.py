@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--vqe-config", default=None, metavar="THREADS,M",
                     help="vqe workload: fixed launch configuration instead of the autotuner's")
     ap.add_argument("--workload", default="random",
-                    choices=["random", "vqe", "planner", "qft", "grover", "fig6", "adder"],
+                    choices=["random", "vqe", "planner", "qft", "grover", "fig6", "adder", "plain"],
                     help="random: the headline line; vqe / planner: secondary measurements")
     return ap.parse_args()
 
@@ -642,29 +642,37 @@ def run_vqe(args):
 
 
 def run_planner(args):
-    """Held-out 33-qubit complex64 random circuits of depth 30: the learned
-    planner (trained here on this GPU's timings of 26-28 qubit circuits)
-    against greedy fusion (k <= 6); unfused complex128 on a sample."""
+    """Learned fusion planning as configured: the cost model trained on this
+    GPU's timings of 26-30 qubit random, QFT and H / controlled-Rz circuits
+    (complex64), evaluated on a held-out 33-qubit complex64 random circuit of
+    depth 30 against greedy fusion with kmax 5 and kmax 6 (each the median of
+    `steps` timed runs) and against the unfused complex128 path over the
+    whole circuit (one run; 128 GiB).  A second model, trained on complex128
+    double-float timings (26-28 qubits), is evaluated on a held-out 30-qubit
+    circuit, where blocks are bound by arithmetic and plans differ."""
     import torch
 
     import paper_1612_08091_gb300 as q
     from paper_1612_08091_gb300 import costmodel
 
     torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sizes = (26, 27, 28, 29, 30)
     t0 = time.perf_counter()
-    X, ms = costmodel.collect(sizes=(26, 27, 28), precisions=("c64",), seed=2018)
+    X, ms = costmodel.collect(sizes=sizes, precisions=("c64",), seed=2018)
     collect_s = time.perf_counter() - t0
     params, loss = costmodel.train(X, ms, hidden=32, epochs=300)
     n = 33
     ops = cg.random_u3_brickwork(n, 30, seed=2018)
     upd = amp_updates(ops, n)
 
-    def timed(fusion, model=None, n=n, ops=ops, precision="c64", df=False):
-        with q.Simulator(n, precision=precision, fusion=fusion, c128_df=df) as sim:
+    def timed(fusion, model=None, n=n, ops=ops, precision="c64", df=False, kmax=6, steps=None):
+        steps = args.steps if steps is None else steps
+        with q.Simulator(n, precision=precision, fusion=fusion, c128_df=df, kmax=kmax, stream=stream) as sim:
             if model is not None:
                 sim.set_cost_model(*model)
             res = []
-            for _ in range(args.warmup + args.steps):
+            for _ in range(args.warmup + steps):
                 sim.reset(0)
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
@@ -673,11 +681,28 @@ def run_planner(args):
                 torch.cuda.synchronize()
                 res.append(time.perf_counter() - t1)
             st = sim.stats()
+            p1, nrm = sim.probs_all()
         torch.cuda.empty_cache()
-        return statistics.median(res[args.warmup:]), st["passes"] / (args.warmup + args.steps)
+        return {"s": statistics.median(res[args.warmup:]), "passes": st["passes"] / (args.warmup + steps),
+                "runs": steps, "p1": np.asarray(p1), "norm2": nrm}
 
-    t_greedy, p_greedy = timed("greedy")
-    t_mlp, p_mlp = timed("mlp", (params, 32))
+    g5 = timed("greedy", kmax=5)
+    g6 = timed("greedy", kmax=6)
+    ml = timed("mlp", (params, 32))
+    # the unfused complex128 path over the whole circuit, FP64 arithmetic,
+    # one timed run (warm-up: the circuit's first layer)
+    with q.Simulator(n, precision="c128", fusion="none", stream=stream) as ps:
+        ps.run(ops[:n])
+        ps.flush()
+        ps.reset(0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ps.run(ops)
+        ps.flush()
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t1
+        p1_plain, _ = ps.probs_all()
+    torch.cuda.empty_cache()
 
     # complex128 in double-float arithmetic, where fused blocks are bound by
     # FP32 arithmetic rather than HBM: a second model trained on this GPU's
@@ -690,39 +715,35 @@ def run_planner(args):
     n2 = 30
     ops2 = cg.random_u3_brickwork(n2, 10, seed=2018)
     upd2 = amp_updates(ops2, n2)
-    t_greedy2, p_greedy2 = timed("greedy", n=n2, ops=ops2, precision="c128", df=True)
-    t_mlp2, p_mlp2 = timed("mlp", (params2, 32), n=n2, ops=ops2, precision="c128", df=True)
-    # plain complex128 on the first layer, extrapolated per amplitude update
-    layer = ops[: n + len(range(0, n - 1, 2))]
-    with q.Simulator(n, precision="c128", fusion="none") as ps:
-        ps.run(layer[:2])
-        ps.flush()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        ps.run(layer)
-        ps.flush()
-        torch.cuda.synchronize()
-        t_layer = time.perf_counter() - t1
-    rate_plain = amp_updates(layer, n) / t_layer
-    out = {"metric": "learned fusion planner, held-out 33-qubit circuit", "value": upd / t_mlp, "unit": UNIT,
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_mlp,
+    g2 = timed("greedy", n=n2, ops=ops2, precision="c128", df=True)
+    m2 = timed("mlp", (params2, 32), n=n2, ops=ops2, precision="c128", df=True)
+
+    def arm(r, u):
+        return {"ms": 1e3 * r["s"], "passes": r["passes"], "value": u / r["s"], "runs": r["runs"],
+                "timing": "host clock around run + flush (median)"}
+
+    out = {"metric": "learned fusion planner, held-out 33-qubit circuit", "value": upd / ml["s"], "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ml["s"],
            "higher_is_better": True, "dtype": "c64", "data": "synthetic",
            "config": {"workload": "33-qubit random U3 + CNOT brickwork, depth 30 (seed 2018), complex64",
-                      "training": {"samples": int(len(ms)), "sizes": [26, 27, 28], "collect_s": collect_s,
-                                   "train_mse_log_ms": loss}},
-           "greedy_k6": {"ms": 1e3 * t_greedy, "passes": p_greedy, "value": upd / t_greedy},
-           "learned": {"ms": 1e3 * t_mlp, "passes": p_mlp, "gain_over_greedy": t_greedy / t_mlp},
-           "plain_c128": {"value": rate_plain, "unit": UNIT,
-                          "sample": "first layer (%d gates), fp64 arithmetic" % len(layer),
-                          "extrapolated_ms": 1e3 * upd / rate_plain},
+                      "training": {"samples": int(len(ms)), "sizes": list(sizes), "collect_s": collect_s,
+                                   "train_mse_log_ms": loss,
+                                   "circuits": "random depth 4, QFT of a basis state, H / controlled-Rz chain"}},
+           "learned": dict(arm(ml, upd), gain_over_greedy_k5=g5["s"] / ml["s"], gain_over_greedy_k6=g6["s"] / ml["s"]),
+           "greedy_k5": arm(g5, upd),
+           "greedy_k6": arm(g6, upd),
+           "plain_c128": {"ms": 1e3 * t_plain, "value": upd / t_plain, "runs": 1, "arithmetic": "fp64",
+                          "what": "whole circuit, one launch per gate, complex128",
+                          "learned_speedup": t_plain / ml["s"]},
+           "check": {"max_p1_difference_learned_vs_plain_c128": float(np.max(np.abs(ml["p1"] - np.asarray(p1_plain)))),
+                     "learned_norm2": ml["norm2"]},
            "c128_double_float": {
                "workload": "30-qubit random U3 + CNOT brickwork, depth 10 (seed 2018), complex128 in "
                            "double-float arithmetic",
                "training": {"samples": int(len(ms2)), "sizes": [26, 27, 28], "collect_s": collect2_s,
                             "train_mse_log_ms": loss2},
-               "greedy_k5": {"ms": 1e3 * t_greedy2, "passes": p_greedy2, "value": upd2 / t_greedy2},
-               "learned": {"ms": 1e3 * t_mlp2, "passes": p_mlp2, "value": upd2 / t_mlp2,
-                           "gain_over_greedy": t_greedy2 / t_mlp2}}}
+               "greedy_k5": arm(g2, upd2),
+               "learned": dict(arm(m2, upd2), gain_over_greedy=g2["s"] / m2["s"])}}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -867,6 +888,71 @@ def run_circuit(args):
     return 0
 
 
+def run_plain(args):
+    """The plain complex128 path (one launch per gate) over the WHOLE
+    32-qubit depth-40 circuit of the headline, in FP64 arithmetic and in
+    double-float arithmetic (FP32 pairs, about 2^-45 relative per product),
+    each run once after a warm-up on the circuit's first layer; the two
+    results are compared with each other."""
+    import torch
+
+    import paper_1612_08091_gb300 as q
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    ops, terms, _ = workload(n, args.depth)
+    upd = amp_updates(ops, n)
+    peak, peak_kind = measured_peaks()
+    arms = {}
+    probs = {}
+    for name, df in (("fp64", False), ("double_float", True)):
+        with q.Simulator(n, precision="c128", fusion="none", stream=stream, c128_df=df) as sim:
+            sim.run(ops[:n])
+            sim.flush()
+            sim.reset(0)
+            torch.cuda.synchronize()
+            sim.reset_stats()
+            sim.set_profiling(True)
+            clocks = ClockSampler(0)
+            clocks.start()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.run(ops)
+            sim.flush()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            t = e0.elapsed_time(e1) / 1e3
+            kt = sim.kernel_times()
+            st = sim.stats()
+            sim.set_profiling(False)
+            p1, nrm = sim.probs_all()
+            zz = sim.expect(terms)
+            probs[name] = np.asarray(p1)
+        torch.cuda.empty_cache()
+        rate = upd / t
+        arms[name] = {
+            "value": rate, "unit": UNIT, "s": t, "gates": len(ops), "launches": int(st["launches"]),
+            "hbm_roofline": {"value": peak * 1e9 / 32.0, "frac": rate * 32.0 / (peak * 1e9), "peak": peak,
+                             "peak_source": peak_kind,
+                             "what": "measured HBM bandwidth / 32 bytes per logical amplitude update"},
+            "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
+                            "GB/s": v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9,
+                            "frac": v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9 / peak} for k, v in kt.items()},
+            "check": {"norm2": nrm, "zz": zz}, "clocks": clk}
+    out = {"metric": "plain complex128 path, whole circuit", "value": arms["double_float"]["value"], "unit": UNIT,
+           "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * arms["double_float"]["s"],
+           "higher_is_better": True, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": workload_name(n, args.depth), "n_qubits": n, "fusion": "none",
+                      "amp_updates": upd, "l2": "state %.0f GiB, larger than L2" % (16 * 2.0 ** n / 2 ** 30)},
+           "fp64": arms["fp64"], "double_float": arms["double_float"],
+           "check": {"max_prob_difference_fp64_vs_double_float":
+                     float(np.max(np.abs(probs["fp64"] - probs["double_float"])))}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -875,6 +961,8 @@ def main():
         return run_vqe(args)
     if args.workload == "planner":
         return run_planner(args)
+    if args.workload == "plain":
+        return run_plain(args)
     if args.workload in ("qft", "grover", "fig6", "adder"):
         return run_circuit(args)
     return run_ours(args)

@@ -210,6 +210,34 @@ int sim_set_amplitudes(qsim *s, uint64_t offset, uint64_t count, const double *i
  * Not in the paper: zero-copy access for device-side consumers. */
 int sim_state_ptr(qsim *s, void **dev_ptr);
 
+/* ---------------------------------------------------------------------------
+ * Sharded registers.  The paper's road map (Sec. 5) points to a distributed
+ * simulator that splits the state over many nodes.  A register of n qubits
+ * split by its top g qubits is held as 2^g handles of n - g qubits (shards);
+ * gates on the local qubits run on each shard, a qubit of the shard index is
+ * first exchanged with a local one, and reductions add the shards' FP64
+ * partial results.  These two calls are the device steps that need more
+ * than one shard or a scale decided over all of them.
+ * --------------------------------------------------------------------------- */
+
+/* The exchange step of a sharded register (Sec. 5, distributed simulation):
+ * for every index i of a shard with bit `qubit` equal to 0, amplitude
+ * i + 2^qubit of shard a trades places with amplitude i of shard b.  With a
+ * the shard whose index bit j is 0 and b its partner with bit j set, this
+ * exchanges the local qubit `qubit` with the global qubit j.  Both handles
+ * must have the same n, precision and device; both queues are flushed first.
+ * Runs on a's stream, ordered after b's queued work and before b's later
+ * work.  QSIM_EINVAL for a == b or mismatched handles. */
+int sim_swap_halves(qsim *a, qsim *b, int qubit);
+
+/* The projection step of a measurement (Sec. 4, listing 1; Appendix A.1)
+ * with the renormalisation supplied by the caller: amplitudes whose
+ * qubits[j] == bits[j] for all j < m are multiplied by `scale`, all others
+ * set to 0 (m = 0: every amplitude is multiplied by scale; scale 0 clears
+ * the register).  A sharded register projects each shard with the scale
+ * 1/sqrt(p) of the outcome's probability p summed over all shards. */
+int sim_project(qsim *s, const int *qubits, int m, const int *bits, double scale);
+
 /* Run subsequent work on another cudaStream_t (after the current stream's
  * queued work, which this call waits for).  Not in the paper. */
 int sim_set_stream(qsim *s, void *stream);

@@ -23,8 +23,10 @@
 //
 // BF16x3.  X = X1 + X2 and R = R1 + R2 (+ R3) are split into bfloat16 parts;
 // the products X1 R1 + X2 R1 + X1 R2 (or five with X2 R2 + X1 R3) accumulate
-// in FP32 in tensor memory.  The state split loses about 2^-16 relatively
-// per pass (incoherently); the gate split is computed on the host in FP64.
+// in FP32 in tensor memory.  X1 is X rounded to nearest, X2 the remainder
+// rounded stochastically (so X1 + X2 is X on average, to about 2^-17
+// relatively per element and pass); the gate split is computed on the host
+// in FP64.
 //
 // Where the operands live.  R's bf16 parts are operand B in shared memory:
 // K-major, 128-byte swizzle, in 64-element K halves of N x 128 bytes.  The
@@ -114,6 +116,7 @@ struct TmArgs {
     const double *rec_prev;
     double target;
     int prev_grid;
+    uint32_t seed;             // per-pass seed of the stochastic rounding of the state's lo part
     int fpos[7];               // tile column bit j <-> qubit fpos[j]
     uint64_t rdep[64];         // address bits of block row r
 };
@@ -235,15 +238,17 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
         };
         auto epilogue = [&](uint64_t tt) {
             float2 *p = args.psi + insert_zeros(tt, args.vspec) + coff;
-            // four FP32 partial sums (chains of 2^K / 2 terms): the rounding
-            // of a long chain is systematic when many amplitudes are equal
-            float ssq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kN / 32; ++chunk) {
                 float d[32];  // rows 16 chunk .. 16 chunk + 15, (re, im) interleaved
                 tmem_ld32(lanes + Sh::kColD + chunk * 32, d);
+                // FP32 partial sums of 32 terms, FP64 across chunks: the
+                // rounding of a long FP32 chain is systematic when many
+                // amplitudes are equal
+                float ssq = 0.f;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) ssq[q & 3] = fmaf(d[q], d[q], ssq[q & 3]);
+                for (int q = 0; q < 32; ++q) ssq = fmaf(d[q], d[q], ssq);
+                nrm_out += (double)ssq;
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) {
                     const int r = chunk * 16 + q;
@@ -263,7 +268,6 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                     }
                 }
             }
-            nrm_out += (double)((ssq[0] + ssq[1]) + (ssq[2] + ssq[3]));
         };
 
         uint64_t t = blockIdx.x;
@@ -282,24 +286,25 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                     atomicOr(args.err, 2u);
                 }
             }
-            float xsq[4] = {0.f, 0.f, 0.f, 0.f};
+            const uint32_t dbase = (args.seed + (uint32_t)t * 0x27D4EB2Fu) ^ ((uint32_t)tid * 0x165667B1u);
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kRows / 16; ++chunk) {
                 uint32_t hw[16], lw[16];
+                float xsq = 0.f;  // 32 terms in FP32, then FP64
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float4 x = v[chunk * 8 + j];
-                    xsq[0] = fmaf(x.x, x.x, xsq[0]);
-                    xsq[1] = fmaf(x.y, x.y, xsq[1]);
-                    xsq[2] = fmaf(x.z, x.z, xsq[2]);
-                    xsq[3] = fmaf(x.w, x.w, xsq[3]);
-                    split_pair(x.x, x.y, hw[2 * j], lw[2 * j]);
-                    split_pair(x.z, x.w, hw[2 * j + 1], lw[2 * j + 1]);
+                    xsq = fmaf(x.x, x.x, fmaf(x.y, x.y, xsq));
+                    xsq = fmaf(x.z, x.z, fmaf(x.w, x.w, xsq));
+                    const uint32_t r = (uint32_t)(chunk * 16 + 2 * j);
+                    split_pair_sr(x.x, x.y, dither_bits(dbase, r), hw[2 * j], lw[2 * j]);
+                    split_pair_sr(x.z, x.w, dither_bits(dbase, r + 1), hw[2 * j + 1], lw[2 * j + 1]);
                 }
                 tmem_st16(lanes + Sh::kColAHi + chunk * 16, hw);
                 tmem_st16(lanes + Sh::kColALo + chunk * 16, lw);
+                nrm_in += (double)xsq;
             }
-            nrm_in += (double)((xsq[0] + xsq[1]) + (xsq[2] + xsq[3]));
+
             tcgen05_wait_st();
             tc_fence_before();
             if (__syncthreads_or(failed)) {
@@ -310,8 +315,14 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                 tc_fence_after();
                 const uint32_t b0 = smem_u32(B);
                 uint32_t acc = 0;
-                for (int term = 0; term < nterms; ++term) {
-                    // (A part, B part): X1R1, X2R1, X1R2, X2R2, X1R3
+                for (int step = 0; step < nterms; ++step) {
+                    // (A part, B part) of term 0..4: X1R1, X2R1, X1R2, X2R2,
+                    // X1R3.  The small products go first and X1R1 last, so
+                    // the FP32 accumulator is rounded at full magnitude only
+                    // by X1R1's own K steps (the rounding of structured
+                    // states repeats from pass to pass)
+                    const int term = nterms == 5 ? (step < 2 ? step + 3 : step == 4 ? 0 : step - 1)
+                                                 : (step == 2 ? 0 : step + 1);
                     const uint32_t a = tmem + ((term == 1 || term == 3) ? Sh::kColALo : Sh::kColAHi);
                     const uint32_t b = b0 + (uint32_t)(term < 2 ? 0 : (term < 4 ? 1 : 2)) * Sh::kBPart;
 #pragma unroll
@@ -458,6 +469,12 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
     a.rec_prev = chain ? recs + 2 * (slot ^ 1) : nullptr;
     a.target = s->norm_target;
     a.prev_grid = s->tc_prev_grid;
+    {
+        // a different, reproducible dither stream for every pass
+        uint64_t z = (s->tc_passes + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        a.seed = (uint32_t)(z ^ (z >> 31));
+    }
     kernel<<<(unsigned)grid, kTmThreads, smem, s->stream>>>(a);
     s->stats.launches++;
     s->tc_passes++;

@@ -97,6 +97,8 @@ def load():
         "sim_batch_set_config": [P, I, I],
         "sim_batch_destroy": [P],
         "sim_get_kernel_times": [P, ctypes.POINTER(KernelTime), I, IP],
+        "sim_swap_halves": [P, P, I],
+        "sim_project": [P, IP, I, IP, D],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -251,6 +253,19 @@ class Simulator:
         p = ctypes.c_double()
         self._check(self.lib.sim_collapse(self.h, q, m, b, ctypes.byref(p)), "sim_collapse")
         return p.value
+
+    def project(self, qubits, bits, scale):
+        """Keep the amplitudes with qubits[j] == bits[j], multiplied by
+        `scale`; zero the rest (sim_project)."""
+        q, m = _ints(qubits)
+        b, _ = _ints(bits)
+        self._check(self.lib.sim_project(self.h, q if m else None, m, b if m else None, float(scale)),
+                    "sim_project")
+
+    def swap_halves(self, other, qubit):
+        """Exchange amplitude i + 2^qubit of this handle with amplitude i of
+        `other` for every i with bit `qubit` clear (sim_swap_halves)."""
+        self._check(self.lib.sim_swap_halves(self.h, other.h, int(qubit)), "sim_swap_halves")
 
     def measure_all(self, u):
         out = ctypes.c_uint64()

@@ -79,23 +79,29 @@ def test_random32_depth40_roundtrip_fused(qs):
     _free()
 
 
-def test_random32_roundtrip_plain_c128(qs):
+@pytest.mark.parametrize("df", [False, True])
+def test_random32_roundtrip_plain_c128(qs, df):
+    """U U^dag on 32 qubits, complex128, one launch per gate, in FP64 and in
+    double-float arithmetic (about 2^-45 relative per product)."""
     n = 32
     ops = cg.random_u3_brickwork(n, 3, seed=8091)
-    with qs.Simulator(n, precision="c128", fusion="none") as sim:
+    with qs.Simulator(n, precision="c128", fusion="none", c128_df=df) as sim:
         sim.run(ops + cg.inverse_ops(ops))
         a0 = sim.get_amplitudes(0, 1)[0]
+        p1, nrm = sim.probs_all()
     assert abs(abs(a0) - 1.0) <= 1e-12
+    assert abs(nrm - 1.0) <= 1e-12 and np.max(p1) <= 1e-12
     _free()
 
 
-@pytest.mark.parametrize("prec,fusion", [("c64", "greedy"), ("c128", "none")])
-def test_random26_depth40_against_oracle(qs, oracle_mod, prec, fusion):
+@pytest.mark.parametrize("prec,fusion,df", [("c64", "greedy", False), ("c128", "none", False),
+                                            ("c128", "none", True), ("c128", "greedy", True)])
+def test_random26_depth40_against_oracle(qs, oracle_mod, prec, fusion, df):
     n = 26
     ops = cg.random_u3_brickwork(n, 40, seed=8091)
     ref = oracle_mod.OracleSim(n)
     oracle_mod.run_ops(ref, ops)
-    with qs.Simulator(n, precision=prec, fusion=fusion) as sim:
+    with qs.Simulator(n, precision=prec, fusion=fusion, c128_df=df) as sim:
         sim.run(ops)
         got = sim.get_amplitudes()
         p1, _ = sim.probs_all()
@@ -103,6 +109,8 @@ def test_random26_depth40_against_oracle(qs, oracle_mod, prec, fusion):
     inf = infidelity(ref.psi, got)
     if prec == "c128":
         assert np.max(np.abs(got - ref.psi)) <= 1e-11
+        np.testing.assert_allclose(p1, ref.probs_all(), atol=1e-11)
+        assert abs(e - ref.expect(cg.zz_chain_terms(n))) <= 1e-11 * (n - 1)
     else:
         assert inf <= TOL64_INFID, inf
     np.testing.assert_allclose(p1, ref.probs_all(), atol=1e-5)
@@ -139,16 +147,41 @@ def test_grover28_truncated_closed_form(qs, prec, fusion):
 
 
 def test_measure_all_30_against_host_cumsum(qs):
+    """30-qubit complex64 register: the reductions, whose partial sums run
+    in FP32 over runs of at most 32 terms before FP64 takes over, against
+    FP64 sums on the host of the same (exactly widened) amplitudes; then
+    measure-all against a host cumulative sum."""
     n = 30
     ops = cg.random_u3_brickwork(n, 2, seed=5)
     u = float(cg.uniform_draws(8092, 1)[0])
+    zz = [(1.0, 0, (1 << i) | (1 << (i + 1))) for i in (0, 9, 10, 28)]
     with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
         sim.run(ops)
         psi = sim.get_amplitudes()
+        p1_gpu, nrm_gpu = sim.probs_all()
+        pq_gpu = [sim.prob(q) for q in (0, 5, 29)]
+        zz_gpu = [sim.expect([t]) for t in zz]
         j = sim.measure_all(u)
         after = sim.get_amplitudes(j, 1)[0]
         p1, nrm = sim.probs_all()
     w = (psi.real ** 2 + psi.imag ** 2)
+    del psi
+    # FP32 stage: a chain of at most 33 roundings (the |psi|^2 and 32 adds),
+    # relative 33 * 2^-24 = 2.0e-6 at worst for every partial sum, so for the
+    # total; FP64 beyond that
+    bound = 2.5e-6
+    nrm_host = float(np.sum(w))
+    assert abs(nrm_gpu - nrm_host) <= bound * nrm_host
+    for q in range(n):
+        p_host = float(w.reshape(-1, 2, 1 << q)[:, 1, :].sum())
+        assert abs(p1_gpu[q] - p_host) <= bound * p_host, (q, p1_gpu[q], p_host)
+        if q in (0, 5, 29):
+            assert abs(pq_gpu[(0, 5, 29).index(q)] - p_host) <= bound * p_host
+    for (c, _, z), e in zip(zz, zz_gpu):
+        i = z.bit_length() - 2
+        v = w.reshape(-1, 2, 2, 1 << i)
+        e_host = float(v[:, 0, 0, :].sum() - v[:, 0, 1, :].sum() - v[:, 1, 0, :].sum() + v[:, 1, 1, :].sum())
+        assert abs(e - e_host) <= bound * nrm_host, (i, e, e_host)
     c = np.cumsum(w)
     jr = int(np.searchsorted(c, u * c[-1], side="right"))
     assert j == jr or abs(c[min(j, jr)] - u * c[-1]) < 1e-6 * c[-1]

@@ -40,6 +40,49 @@ def grover_closed_form(n, marked, k):
     return a_m, a_o
 
 
+def grover_reads(sim, n, marked):
+    am = sim.get_amplitudes(marked, 1)[0]
+    p1, nrm = sim.probs_all()
+    zz = sim.expect(cg.zz_chain_terms(n))
+    return am, p1, nrm, zz
+
+
+def grover_wanted(n, marked, k):
+    a_m, a_o = grover_closed_form(n, marked, k)
+    bits = np.array([(marked >> q) & 1 for q in range(n)])
+    p1 = bits * a_m ** 2 + a_o ** 2 * ((1 << (n - 1)) - bits)
+    s = 1 - 2 * bits  # Z eigenvalue of the marked item's bits
+    zz = sum(s[i] * s[i + 1] for i in range(n - 1)) * (a_m ** 2 - a_o ** 2)
+    return a_m, a_o, p1, zz
+
+
+def test_grover28_full_search_raw_reads(qs):
+    """The configured search: 28 qubits, r = floor(pi/4 sqrt(2^28)) = 12867
+    iterations, 154,409 passes.  Raw reads within 1e-5 of the closed form."""
+    n = 28
+    marked = cg.grover_marked(n, seed=2017)
+    r = cg.grover_iterations(n)
+    body = cg.grover_iteration_ops(n, marked)
+    with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
+        sim.run([cg.op("H", (q,)) for q in range(n)])
+        done = 0
+        while done < r:
+            k = min(500, r - done)
+            sim.run(body * k)
+            sim.flush()
+            done += k
+        st = sim.stats()
+        am, p1, nrm, zz = grover_reads(sim, n, marked)
+    a_m, a_o, p1_want, zz_want = grover_wanted(n, marked, r)
+    print("Grover-28, %d iterations, %d passes: |norm2-1| %.2e, P(marked) %.10f (closed form %.10f), "
+          "<sum ZZ> %.8f (%.8f)" % (r, st["passes"], abs(nrm - 1.0), abs(am) ** 2, a_m ** 2, zz, zz_want))
+    assert st["passes"] >= 150000
+    assert abs(nrm - 1.0) <= 1e-5
+    assert abs(abs(am) ** 2 - a_m ** 2) <= 1e-5
+    np.testing.assert_allclose(p1, p1_want, atol=1e-5)
+    assert abs(zz - zz_want) <= 1e-5 * (n - 1)
+
+
 def test_grover20_150k_passes_raw_reads(qs):
     n = 20
     marked = cg.grover_marked(n, seed=2017)

@@ -118,7 +118,10 @@ def test_learned_planner_end_to_end(qs, oracle_mod):
         assert infidelity(ref.psi, psi_g) <= TOL64_INFID
         print("%s n=%d: greedy %.2f ms, learned %.2f ms (predicted %.2f ms), gain %.2fx"
               % (name, n, 1e3 * t_greedy, 1e3 * t_mlp, pred, t_greedy / t_mlp))
-        # the learned plan must not be clearly worse than greedy fusion
+        # complex64 blocks are HBM-bound like the plain gates, so greedy
+        # fusion is close to optimal here and the network mostly reproduces
+        # it; it must not be clearly worse (its gain is asserted where blocks
+        # are bound by arithmetic, in the double-float test below)
         assert t_mlp <= 1.25 * t_greedy + 2e-3
 
 
@@ -144,3 +147,48 @@ def test_learned_planner_with_permutation_blocks(qs, oracle_mod, prec):
         assert np.max(np.abs(got - ref.psi)) <= 1e-11
     else:
         assert infidelity(ref.psi, got) <= TOL64_INFID
+
+
+def test_learned_planner_gains_on_c128_double_float(qs, oracle_mod):
+    """Where the fused blocks are bound by arithmetic (complex128 in
+    double-float arithmetic: a 5-qubit block costs about nine times the HBM
+    time of its pass), the trained network picks narrower blocks and plain
+    gates and beats greedy fusion, which minimises passes.  Trained on
+    timings of 24-26 qubit circuits, evaluated on a held-out 27-qubit
+    circuit; the learned plan's state matches the oracle."""
+    from paper_1612_08091_gb300 import costmodel
+
+    X, ms = costmodel.collect(sizes=(24, 25, 26), precisions=("c128",), kmaxes=(1, 2, 3, 4, 5), seed=2018,
+                              df=True)
+    params, loss = costmodel.train(X, ms, hidden=32, epochs=300)
+    n = 27
+    ops = cg.random_u3_brickwork(n, 10, seed=2019)
+
+    def wall(fusion, model=None):
+        import torch
+
+        ts = []
+        with qs.Simulator(n, precision="c128", fusion=fusion, c128_df=True) as sim:
+            if model is not None:
+                sim.set_cost_model(*model)
+            for _ in range(4):
+                sim.reset(0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sim.run(ops)
+                sim.flush()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            passes = sim.stats()["passes"] / 4
+            psi = sim.get_amplitudes() if model is not None else None
+        return float(np.median(ts[1:])), passes, psi
+
+    t_greedy, p_greedy, _ = wall("greedy")
+    t_mlp, p_mlp, psi = wall("mlp", (params, 32))
+    gain = t_greedy / t_mlp
+    print("c128 double-float, %d qubits: greedy %.1f ms (%d passes), learned %.1f ms (%d passes), gain %.2fx, "
+          "training loss %.3f" % (n, 1e3 * t_greedy, p_greedy, 1e3 * t_mlp, p_mlp, gain, loss))
+    assert gain > 1.1, gain
+    ref = oracle_mod.OracleSim(n)
+    oracle_mod.run_ops(ref, ops)
+    assert np.max(np.abs(psi - ref.psi)) <= 1e-11
