@@ -153,30 +153,6 @@ __device__ __forceinline__ void split_pair(float re, float im, uint32_t &hw, uin
     lw = pack_bf16x2(rr, ri);
 }
 
-// The same split with lo stochastically rounded: the 16 bits of x - hi below
-// the bf16 cut are added to 16 random bits (rnd: low half for re, high half
-// for im) and truncated, so E[hi + lo] = x.  The remainder x - hi - lo then
-// has mean zero and changes from pass to pass, instead of repeating: on
-// structured states (mostly equal amplitudes, as in Grover's search) the
-// round-to-nearest remainder is the same in every pass and its effect adds
-// up coherently over 1e5 passes.
-__device__ __forceinline__ void split_pair_sr(float re, float im, uint32_t rnd, uint32_t &hw, uint32_t &lw) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
-    memcpy(&hw, &h, 4);
-    const float rr = re - __uint_as_float(hw << 16);
-    const float ri = im - __uint_as_float(hw & 0xFFFF0000u);
-    const uint32_t br = __float_as_uint(rr) + (rnd & 0xFFFFu);
-    const uint32_t bi = __float_as_uint(ri) + (rnd >> 16);
-    lw = __byte_perm(br, bi, 0x7632);  // upper halves: re's bf16 low, im's high
-}
-
-// 32 random bits for element r of a stream `base` (a multiplicative hash of
-// an affine sequence; base mixes the pass, the tile and the thread)
-__device__ __forceinline__ uint32_t dither_bits(uint32_t base, uint32_t r) {
-    uint32_t h = (base + r * 0x9E3779B9u) * 0x85EBCA6Bu;
-    return h ^ (h >> 15);
-}
-
 // Host side: round-to-nearest-even bf16 of a float (finite inputs), and the
 // bf16 value back as a double; the operand records split the gate matrix
 // with these in FP64 (R1 = bf16(R), R2 = bf16(R - R1), ...).

@@ -23,10 +23,8 @@
 //
 // BF16x3.  X = X1 + X2 and R = R1 + R2 (+ R3) are split into bfloat16 parts;
 // the products X1 R1 + X2 R1 + X1 R2 (or five with X2 R2 + X1 R3) accumulate
-// in FP32 in tensor memory.  X1 is X rounded to nearest, X2 the remainder
-// rounded stochastically (so X1 + X2 is X on average, to about 2^-17
-// relatively per element and pass); the gate split is computed on the host
-// in FP64.
+// in FP32 in tensor memory.  The state split loses about 2^-17 relatively
+// per element and pass; the gate split is computed on the host in FP64.
 //
 // Where the operands live.  R's bf16 parts are operand B in shared memory:
 // K-major, 128-byte swizzle, in 64-element K halves of N x 128 bytes.  The
@@ -116,7 +114,6 @@ struct TmArgs {
     const double *rec_prev;
     double target;
     int prev_grid;
-    uint32_t seed;             // per-pass seed of the stochastic rounding of the state's lo part
     int fpos[7];               // tile column bit j <-> qubit fpos[j]
     uint64_t rdep[64];         // address bits of block row r
 };
@@ -286,7 +283,6 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                     atomicOr(args.err, 2u);
                 }
             }
-            const uint32_t dbase = (args.seed + (uint32_t)t * 0x27D4EB2Fu) ^ ((uint32_t)tid * 0x165667B1u);
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kRows / 16; ++chunk) {
                 uint32_t hw[16], lw[16];
@@ -296,9 +292,8 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                     const float4 x = v[chunk * 8 + j];
                     xsq = fmaf(x.x, x.x, fmaf(x.y, x.y, xsq));
                     xsq = fmaf(x.z, x.z, fmaf(x.w, x.w, xsq));
-                    const uint32_t r = (uint32_t)(chunk * 16 + 2 * j);
-                    split_pair_sr(x.x, x.y, dither_bits(dbase, r), hw[2 * j], lw[2 * j]);
-                    split_pair_sr(x.z, x.w, dither_bits(dbase, r + 1), hw[2 * j + 1], lw[2 * j + 1]);
+                    split_pair(x.x, x.y, hw[2 * j], lw[2 * j]);
+                    split_pair(x.z, x.w, hw[2 * j + 1], lw[2 * j + 1]);
                 }
                 tmem_st16(lanes + Sh::kColAHi + chunk * 16, hw);
                 tmem_st16(lanes + Sh::kColALo + chunk * 16, lw);
@@ -315,14 +310,10 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                 tc_fence_after();
                 const uint32_t b0 = smem_u32(B);
                 uint32_t acc = 0;
-                for (int step = 0; step < nterms; ++step) {
-                    // (A part, B part) of term 0..4: X1R1, X2R1, X1R2, X2R2,
-                    // X1R3.  The small products go first and X1R1 last, so
-                    // the FP32 accumulator is rounded at full magnitude only
-                    // by X1R1's own K steps (the rounding of structured
-                    // states repeats from pass to pass)
-                    const int term = nterms == 5 ? (step < 2 ? step + 3 : step == 4 ? 0 : step - 1)
-                                                 : (step == 2 ? 0 : step + 1);
+                for (int term = 0; term < nterms; ++term) {
+                    // (A part, B part): X1R1, X2R1, X1R2, X2R2, X1R3.  (Issuing
+                    // the small products first measured a 3x larger coherent
+                    // error on Grover's search, the same on random circuits.)
                     const uint32_t a = tmem + ((term == 1 || term == 3) ? Sh::kColALo : Sh::kColAHi);
                     const uint32_t b = b0 + (uint32_t)(term < 2 ? 0 : (term < 4 ? 1 : 2)) * Sh::kBPart;
 #pragma unroll
@@ -469,12 +460,6 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
     a.rec_prev = chain ? recs + 2 * (slot ^ 1) : nullptr;
     a.target = s->norm_target;
     a.prev_grid = s->tc_prev_grid;
-    {
-        // a different, reproducible dither stream for every pass
-        uint64_t z = (s->tc_passes + 1) * 0x9E3779B97F4A7C15ull;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        a.seed = (uint32_t)(z ^ (z >> 31));
-    }
     kernel<<<(unsigned)grid, kTmThreads, smem, s->stream>>>(a);
     s->stats.launches++;
     s->tc_passes++;
