@@ -238,7 +238,8 @@ __device__ void build_phase_table(float2 *t, int kb, const float2 *ph, float2 ex
 // double-buffered copies: 44.9 against 41.0 ms for the 4096-circuit batch).
 // The global-memory kernel's chunk size (2^12 amplitudes; a pair of chunks
 // is 64 KB of shared memory) and block size.
-constexpr int kGlobalThreads = 256;
+constexpr int kGlobalThreads = 128;
+constexpr int kGlobalCtas = 3;  // resident CTAs per SM the register budget is sized for
 constexpr int kGlobalBits = 12;
 
 // Position in a pair buffer (source order, after a ladder permutation) of
@@ -274,7 +275,7 @@ __device__ __forceinline__ void pair_group(float2 *x, const Rot *r) {
     constexpr unsigned W = PERM ? 3u : 1u;
     constexpr unsigned M0 = W << Q0, M1 = W << Q1, M2 = W << Q2, M3 = W << Q3;
     const float t0 = r[0].t, t1 = r[1].t, t2 = r[2].t, t3 = r[3].t;
-    for (unsigned gi = threadIdx.x; gi < (1u << (kGlobalBits + 1 - 4)); gi += kGlobalThreads) {
+    for (unsigned gi = threadIdx.x; gi < (1u << (kGlobalBits + 1 - 4)); gi += (unsigned)kGlobalThreads) {
         unsigned base = gi;
         base = ((base >> Q0) << (Q0 + 1)) | (base & ((1u << Q0) - 1u));
         base = ((base >> Q1) << (Q1 + 1)) | (base & ((1u << Q1) - 1u));
@@ -314,7 +315,7 @@ __device__ __forceinline__ void pair_gates(float2 *x, const Rot *r) {
 }
 
 template <int T, bool GLOBAL>
-__global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A) {
+__global__ void __launch_bounds__(T, GLOBAL ? kGlobalCtas : 1) k_vqe_batch(const VqeArgs A) {
     constexpr int kRegAmps = RegAmps<T>::value;
     extern __shared__ float2 sm[];
     __shared__ int s_idx;
@@ -483,7 +484,8 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
             // 0..g-1 and flips (flo), the low seven phase bits constant per
             // thread.
             auto store_pair = [&](float2 *to, unsigned pr, bool phased, unsigned flo) {
-                static_assert(T == 256 && (2 << g) % T == 0, "store_pair assumes 256 threads");
+                static_assert(T == kGlobalThreads && T >= 128 && (2 << g) % T == 0,
+                              "store_pair: the thread index holds bits 0..6 of the element");
                 const unsigned tf = threadIdx.x ^ flo;
                 const unsigned pt = permuted ? pair_perm(tf) : tf;
                 float2 *dst0 = to + ((size_t)pr << g) + threadIdx.x;
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(T, GLOBAL ? 2 : 1) k_vqe_batch(const VqeArgs A
                 const unsigned thi0 = (tf >> 7) & 31u;
 #pragma unroll
                 for (int j = 0; j < (2 << g) / T; ++j) {
-                    const unsigned cj = (unsigned)j << 8;  // e = tid | j << 8
+                    const unsigned cj = (unsigned)j * (unsigned)T;  // e = tid | j T
                     float2 v = sm[pt ^ (permuted ? pair_perm(cj) : cj)];
                     if (phased) v = cmul(v, cmul(tlo, s_thi[thi0 ^ ((cj >> 7) & 31u)]));
                     ((j < G / T) ? dst0 : dst1)[cj & gmask] = v;
