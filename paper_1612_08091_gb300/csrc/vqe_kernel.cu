@@ -138,9 +138,17 @@ __device__ void gates_blocked(float2 *x, int k, const unsigned *mask, const Rot 
         unsigned m0 = mask[g0], m1 = h1 ? mask[g0 + 1] : 0u, m2 = h2 ? mask[g0 + 2] : 0u,
                  m3 = h3 ? mask[g0 + 3] : 0u;
         unsigned used = (m0 & (0u - m0)) | (m1 & (0u - m1)) | (m2 & (0u - m2)) | (m3 & (0u - m3));
-        if (!h1) { m1 = ~used & (used + 1u); used |= m1; }
-        if (!h2) { m2 = ~used & (used + 1u); used |= m2; }
-        if (!h3) { m3 = ~used & (used + 1u); used |= m3; }
+        // padding on the lowest unused bit, at bit 4 or above where one is
+        // free (a pivot in bits 0..3, the bank bits, costs a bank conflict)
+        auto pad = [&]() {
+            const unsigned hi = ~used & ((1u << k) - 1u) & ~15u;
+            const unsigned m = hi ? (hi & (0u - hi)) : (~used & (used + 1u));
+            used |= m;
+            return m;
+        };
+        if (!h1) m1 = pad();
+        if (!h2) m2 = pad();
+        if (!h3) m3 = pad();
         const float t0 = g[g0].t, t1 = h1 ? g[g0 + 1].t : 0.f, t2 = h2 ? g[g0 + 2].t : 0.f,
                     t3 = h3 ? g[g0 + 3].t : 0.f;
         int s0 = __ffs(m0) - 1, s1 = __ffs(m1) - 1, s2 = __ffs(m2) - 1, s3 = __ffs(m3) - 1;
@@ -254,42 +262,69 @@ __host__ __device__ constexpr unsigned pair_perm(unsigned e) {
     return ((par ^ (e >> kGlobalBits)) << kGlobalBits) | gl;
 }
 
-// Order of the pair pass's 12 rotations, taken four at a time.  A group's
-// pivot bits are the same in all lanes' addresses at each access, so a group
-// holding qubits 0..3 (the bank bits of 8-byte elements) would be a 16-way
-// bank conflict; spread as {0,4,5,6} {1,7,8,9} {2,3,10,11} the conflicts are
-// 2-, 2- and 4-way.
+// Order of the pair pass's 12 rotations, taken four at a time, one of the
+// qubits 0..2 in each group (qubits 0..3 decide the shared-memory bank of
+// an 8-byte element; see pair_group for how the groups avoid conflicts).
 __constant__ int kPairOrder[12] = {0, 4, 5, 6, 1, 7, 8, 9, 2, 3, 10, 11};
 
 // One group of the pair pass with compile-time qubits Q0 < Q1 < Q2 < Q3 (a
 // group of kPairOrder): the 2^13-element pair buffer x holds 512 groups of
-// 16 elements, base (zeros at the pivots Q0..Q3) XOR any subset of the masks
-// (PERM ? 3 : 1) << Qj; rotation j uses r[j].t.  PERM: the buffer is in
-// source order after a ladder permutation, where logical qubit k pairs the
-// elements p and p ^ (3 << k); the element whose logical bit k is 0 is the
-// one whose bits 0..k have even parity, which within a group is the base's,
-// so the rotation is applied with t -> -t where the base's parity is odd.
-template <bool PERM, int Q0, int Q1, int Q2, int Q3>
+// 16 elements, base (zeros at the pivots P0 < P1 < P2 < P3) XOR any subset
+// of the masks Mj = (PERM ? 3 : 1) << Qj; rotation j uses r[j].t.  PERM: the
+// buffer is in source order after a ladder permutation, where logical qubit
+// k pairs the elements p and p ^ (3 << k); either of those two bits can be
+// the pivot (Pj = Qj or Qj + 1; the masks restricted to the pivots must be
+// invertible); the element whose logical bit k is 0 is the one whose bits
+// 0..k have even parity, which for rotation j is the base's parity, so the
+// rotation is applied with t -> -t where that parity is odd.
+//
+// Banks.  In each access all lanes use the same subset of masks, so the 16
+// lanes of a half-warp (8-byte elements) hit 16 banks only if their bases
+// differ in all of bits 0..3.  A pivot there is 0 in every base; instead,
+// lanes whose group-index bit (4 - c + i) is set (c = number of pivots
+// below 4) start from base ^ M of the i-th such rotation: the same 16
+// elements in another order, which flips that pivot's bank bit, and that
+// rotation's pair is met with its two elements swapped (t -> -t in those
+// lanes).  The other rotations are unaffected: a mask changes the parity of
+// bits 0..q of no other rotation's base.
+template <bool PERM, int Q0, int Q1, int Q2, int Q3, int P0, int P1, int P2, int P3>
 __device__ __forceinline__ void pair_group(float2 *x, const Rot *r) {
-    static_assert(Q0 < Q1 && Q1 < Q2 && Q2 < Q3, "pivots in ascending order");
+    static_assert(Q0 < Q1 && Q1 < Q2 && Q2 < Q3, "qubits in ascending order");
+    static_assert(P0 < P1 && P1 < P2 && P2 < P3, "pivots in ascending order");
     constexpr unsigned W = PERM ? 3u : 1u;
     constexpr unsigned M0 = W << Q0, M1 = W << Q1, M2 = W << Q2, M3 = W << Q3;
+    static_assert(((M0 >> P0) & 1u) && ((M1 >> P1) & 1u) && ((M2 >> P2) & 1u) && ((M3 >> P3) & 1u),
+                  "each pivot is a bit of its own mask");
+    // restricted to the pivots the masks form a triangular matrix
+    static_assert(!((M0 >> P1) & 1u) && !((M0 >> P2) & 1u) && !((M0 >> P3) & 1u) && !((M1 >> P2) & 1u) &&
+                      !((M1 >> P3) & 1u) && !((M2 >> P3) & 1u) ||
+                  (!((M1 >> P0) & 1u) && !((M2 >> P0) & 1u) && !((M3 >> P0) & 1u) && !((M2 >> P1) & 1u) &&
+                   !((M3 >> P1) & 1u) && !((M3 >> P2) & 1u)),
+                  "masks restricted to the pivots must be invertible");
+    constexpr int c = (P0 < 4) + (P1 < 4) + (P2 < 4) + (P3 < 4);  // pivots in the bank bits
+    static_assert(c <= 2 && (P0 < 4 || c == 0) && (P1 < 4 || c <= 1) && P2 >= 4 && P3 >= 4,
+                  "bank pivots come first");
     const float t0 = r[0].t, t1 = r[1].t, t2 = r[2].t, t3 = r[3].t;
     for (unsigned gi = threadIdx.x; gi < (1u << (kGlobalBits + 1 - 4)); gi += (unsigned)kGlobalThreads) {
         unsigned base = gi;
-        base = ((base >> Q0) << (Q0 + 1)) | (base & ((1u << Q0) - 1u));
-        base = ((base >> Q1) << (Q1 + 1)) | (base & ((1u << Q1) - 1u));
-        base = ((base >> Q2) << (Q2 + 1)) | (base & ((1u << Q2) - 1u));
-        base = ((base >> Q3) << (Q3 + 1)) | (base & ((1u << Q3) - 1u));
+        base = ((base >> P0) << (P0 + 1)) | (base & ((1u << P0) - 1u));
+        base = ((base >> P1) << (P1 + 1)) | (base & ((1u << P1) - 1u));
+        base = ((base >> P2) << (P2 + 1)) | (base & ((1u << P2) - 1u));
+        base = ((base >> P3) << (P3 + 1)) | (base & ((1u << P3) - 1u));
+        // lane-dependent start of the bank-pivot rotations (see above)
+        const bool sw0 = c >= 1 && ((gi >> (4 - c)) & 1u);
+        const bool sw1 = c >= 2 && ((gi >> (5 - c)) & 1u);
+        const unsigned start = base ^ (sw0 ? M0 : 0u) ^ (sw1 ? M1 : 0u);
         float2 v[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            v[k] = x[base ^ ((k & 1) ? M0 : 0u) ^ ((k & 2) ? M1 : 0u) ^ ((k & 4) ? M2 : 0u) ^ ((k & 8) ? M3 : 0u)];
+            v[k] = x[start ^ ((k & 1) ? M0 : 0u) ^ ((k & 2) ? M1 : 0u) ^ ((k & 4) ? M2 : 0u) ^ ((k & 8) ? M3 : 0u)];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int q = j == 0 ? Q0 : j == 1 ? Q1 : j == 2 ? Q2 : Q3;
             float t = j == 0 ? t0 : j == 1 ? t1 : j == 2 ? t2 : t3;
             if (PERM && (__popc(base & ((2u << q) - 1u)) & 1)) t = -t;
+            if ((j == 0 && sw0) || (j == 1 && sw1)) t = -t;
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 if ((k >> j) & 1) continue;
@@ -301,17 +336,19 @@ __device__ __forceinline__ void pair_group(float2 *x, const Rot *r) {
         }
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            x[base ^ ((k & 1) ? M0 : 0u) ^ ((k & 2) ? M1 : 0u) ^ ((k & 4) ? M2 : 0u) ^ ((k & 8) ? M3 : 0u)] = v[k];
+            x[start ^ ((k & 1) ? M0 : 0u) ^ ((k & 2) ? M1 : 0u) ^ ((k & 4) ? M2 : 0u) ^ ((k & 8) ? M3 : 0u)] = v[k];
     }
     __syncthreads();
 }
 
-// The pair pass's 12 rotations (r in kPairOrder) on a pair buffer.
+// The pair pass's 12 rotations (r in kPairOrder) on a pair buffer.  Group
+// {2, 3, 10, 11} takes qubit 3's pivot at bit 4 when PERM allows it, so that
+// it has one pivot in the bank bits, like the other two groups.
 template <bool PERM>
 __device__ __forceinline__ void pair_gates(float2 *x, const Rot *r) {
-    pair_group<PERM, 0, 4, 5, 6>(x, r);
-    pair_group<PERM, 1, 7, 8, 9>(x, r + 4);
-    pair_group<PERM, 2, 3, 10, 11>(x, r + 8);
+    pair_group<PERM, 0, 4, 5, 6, 0, 4, 5, 6>(x, r);
+    pair_group<PERM, 1, 7, 8, 9, 1, 7, 8, 9>(x, r + 4);
+    pair_group<PERM, 2, 3, 10, 11, 2, (PERM ? 4 : 3), 10, 11>(x, r + 8);
 }
 
 template <int T, bool GLOBAL>
@@ -459,9 +496,18 @@ __global__ void __launch_bounds__(T, GLOBAL ? kGlobalCtas : 1) k_vqe_batch(const
                 fence_proxy_async_smem();
                 __syncthreads();
             };
-            auto load_pair = [&](const float2 *from, unsigned pr) {
+            // the two source chunks of destination pair pr
+            auto pair_chunks = [&](unsigned pr, unsigned &ca, unsigned &cb) {
                 const unsigned S = permuted ? ((pr ^ (pr << 1)) & hmask) : pr;
-                const unsigned ca = S, cb = permuted ? S ^ 1u : pr ^ hmask;
+                ca = S;
+                cb = permuted ? S ^ 1u : pr ^ hmask;
+            };
+            // (Bringing the next pair's or tile's data into L2 once a copy
+            // had landed, with cp.async.bulk.prefetch.L2, measured 4 %
+            // slower: 6.5 % more DRAM reads.)
+            auto load_pair = [&](const float2 *from, unsigned pr) {
+                unsigned ca, cb;
+                pair_chunks(pr, ca, cb);
                 before_copies();
                 if (threadIdx.x == 0) {
                     mbar_expect_tx(s_bar, 16u * G);
