@@ -6,6 +6,7 @@
 // tmem_block_kernel.cu, diag_kernels.cu, perm_kernels.cu,
 // reduce_kernels.cu).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <cmath>
@@ -152,6 +153,18 @@ int execute_item(qsim *s, const PlanItem &it) {
     const auto h0 = std::chrono::steady_clock::now();
     int rc;
     size_t ev0 = 0, ev1 = 0;
+    // with profiling on, an NVTX range per planned item (visible in a
+    // timeline profiler next to its kernel)
+    struct Range {
+        bool on;
+        Range(bool o, const PlanItem &it) : on(o) {
+            if (on) nvtxRangePushA(!it.fused ? "gate" : it.diag_block ? "diag block" : it.perm_block ? "perm block"
+                                                                                            : "dense block");
+        }
+        ~Range() {
+            if (on) nvtxRangePop();
+        }
+    } range(s->profiling, it);
     // a non-unitary gate changes the norm: no correction across it
     bool unitary = true;
     for (int gi : it.members) unitary = unitary && s->queue[gi].unitary;

@@ -304,3 +304,20 @@ def test_errors_leave_state_unchanged(qs):
         assert e.value.status == "EZEROPROB"
         a = sim.get_amplitudes()
         assert a[0] == 1 and np.count_nonzero(a) == 1
+
+
+def test_create_limits(qs):
+    """A register whose state cannot be allocated is refused with ENOMEM
+    (36 qubits of complex128: 1 TiB, more than the device holds), sizes
+    outside 1..36 with EINVAL; the device stays usable."""
+    with pytest.raises(qs.QsimError) as e:
+        qs.Simulator(36, precision="c128", torch_memory=False)
+    assert e.value.status == "ENOMEM"
+    for bad in (0, 37, 40):
+        with pytest.raises(qs.QsimError) as e:
+            qs.Simulator(bad, precision="c64", torch_memory=False)
+        assert e.value.status == "EINVAL"
+    with make(qs, 4, "c128") as sim:
+        sim.apply(np.array([[0, 1], [1, 0]], dtype=np.complex128), [2])
+        a = sim.get_amplitudes()
+    assert a[4] == 1 and np.count_nonzero(a) == 1
