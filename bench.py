@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--vqe-config", default=None, metavar="THREADS,M",
                     help="vqe workload: fixed launch configuration instead of the autotuner's")
     ap.add_argument("--workload", default="random",
-                    choices=["random", "vqe", "planner", "qft", "grover", "fig6", "adder", "plain"],
+                    choices=["random", "vqe", "planner", "qft", "grover", "fig6", "adder", "plain", "sharded"],
                     help="random: the headline line; vqe / planner: secondary measurements")
     return ap.parse_args()
 
@@ -958,6 +958,84 @@ def run_plain(args):
     return 0
 
 
+def run_sharded(args):
+    """The headline circuit (32 qubits, depth 40, complex64 fused) on a
+    register split into 2 shards of 31 qubits on one GPU: the exchange
+    planner moves the top qubit into the shards whenever a gate targets it
+    (sim_swap_halves), the shards run their own fused queues.  Reported
+    beside the same circuit on one handle, with the exchange kernel timed on
+    its own (CUDA events, median of 3) against the HBM roofline (it reads and
+    writes half of each shard)."""
+    import torch
+
+    import paper_1612_08091_gb300 as q
+    from paper_1612_08091_gb300.sharded import ShardedSimulator
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n, g = args.n, 1
+    ops, terms, u = workload(n, args.depth)
+    upd = amp_updates(ops, n)
+    peak, peak_kind = measured_peaks()
+
+    def timed(run):
+        ts = []
+        for _ in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(ts[args.warmup:])
+
+    with q.Simulator(n, precision="c64", fusion="greedy", stream=stream) as one:
+        def run_one():
+            one.reset(0)
+            one.run(ops)
+            one.flush()
+        t_one = timed(run_one)
+        p1_one, _ = one.probs_all()
+    torch.cuda.empty_cache()
+    with ShardedSimulator(n, global_qubits=g, precision="c64", fusion="greedy", stream=stream) as sh:
+        def run_sh():
+            sh.reset(0)
+            sh.run(ops)
+            sh.flush()
+        t_sh = timed(run_sh)
+        ex = sh.exchanges / (args.warmup + args.steps)
+        p1_sh, nrm = sh.probs_all()
+        # the exchange kernel alone: one swap of the top qubit with local 30
+        a, b = sh.shards[0], sh.shards[1]
+        ts = []
+        for _ in range(4):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            a.swap_halves(b, n - g - 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t_swap = statistics.median(ts[1:])
+    torch.cuda.empty_cache()
+    swap_bytes = 2.0 * 2 * 8 * 2.0 ** (n - g - 1)  # half of each shard read and written
+    out = {"metric": "sharded register: 2 shards on one GPU", "value": upd / t_sh, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_sh, "higher_is_better": True,
+           "dtype": "c64", "data": "synthetic",
+           "config": {"workload": workload_name(n, args.depth) + " (circuit only)", "shards": 1 << g,
+                      "exchanges_per_run": ex, "fusion": "greedy", "kmax": args.kmax},
+           "single_handle": {"ms": 1e3 * t_one, "value": upd / t_one},
+           "exchange_kernel": {"ms": 1e3 * t_swap, "bytes": swap_bytes, "GB/s": swap_bytes / t_swap / 1e9,
+                               "frac": swap_bytes / t_swap / 1e9 / peak, "peak_source": peak_kind,
+                               "what": "sim_swap_halves of two 31-qubit complex64 shards on qubit 30: "
+                                       "half of each shard read and written"},
+           "check": {"max_p1_difference_vs_single_handle": float(np.max(np.abs(np.asarray(p1_sh) - p1_one))),
+                     "norm2": nrm}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -968,6 +1046,8 @@ def main():
         return run_planner(args)
     if args.workload == "plain":
         return run_plain(args)
+    if args.workload == "sharded":
+        return run_sharded(args)
     if args.workload in ("qft", "grover", "fig6", "adder"):
         return run_circuit(args)
     return run_ours(args)

@@ -227,7 +227,10 @@ int sim_state_ptr(qsim *s, void **dev_ptr);
  * exchanges the local qubit `qubit` with the global qubit j.  Both handles
  * must have the same n, precision and device; both queues are flushed first.
  * Runs on a's stream, ordered after b's queued work and before b's later
- * work.  QSIM_EINVAL for a == b or mismatched handles. */
+ * work, and waits for it: the kernel also sums |psi|^2 of what left each
+ * shard (FP64), so that shards whose norms were known keep known norms for
+ * the complex64 norm control.  QSIM_EINVAL for a == b or mismatched
+ * handles. */
 int sim_swap_halves(qsim *a, qsim *b, int qubit);
 
 /* The projection step of a measurement (Sec. 4, listing 1; Appendix A.1)
@@ -235,8 +238,11 @@ int sim_swap_halves(qsim *a, qsim *b, int qubit);
  * qubits[j] == bits[j] for all j < m are multiplied by `scale`, all others
  * set to 0 (m = 0: every amplitude is multiplied by scale; scale 0 clears
  * the register).  A sharded register projects each shard with the scale
- * 1/sqrt(p) of the outcome's probability p summed over all shards. */
-int sim_project(qsim *s, const int *qubits, int m, const int *bits, double scale);
+ * 1/sqrt(p) of the outcome's probability p summed over all shards.
+ * kept_norm2: sum |psi_i|^2 over the kept amplitudes before scaling, if the
+ * caller knows it (the complex64 norm control then steers to scale^2 times
+ * it), else any negative value. */
+int sim_project(qsim *s, const int *qubits, int m, const int *bits, double scale, double kept_norm2);
 
 /* Run subsequent work on another cudaStream_t (after the current stream's
  * queued work, which this call waits for).  Not in the paper. */

@@ -98,7 +98,7 @@ def load():
         "sim_batch_destroy": [P],
         "sim_get_kernel_times": [P, ctypes.POINTER(KernelTime), I, IP],
         "sim_swap_halves": [P, P, I],
-        "sim_project": [P, IP, I, IP, D],
+        "sim_project": [P, IP, I, IP, D, D],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -254,13 +254,14 @@ class Simulator:
         self._check(self.lib.sim_collapse(self.h, q, m, b, ctypes.byref(p)), "sim_collapse")
         return p.value
 
-    def project(self, qubits, bits, scale):
+    def project(self, qubits, bits, scale, kept_norm2=-1.0):
         """Keep the amplitudes with qubits[j] == bits[j], multiplied by
-        `scale`; zero the rest (sim_project)."""
+        `scale`; zero the rest (sim_project).  kept_norm2: their squared
+        norm before scaling if known (else negative)."""
         q, m = _ints(qubits)
         b, _ = _ints(bits)
-        self._check(self.lib.sim_project(self.h, q if m else None, m, b if m else None, float(scale)),
-                    "sim_project")
+        self._check(self.lib.sim_project(self.h, q if m else None, m, b if m else None, float(scale),
+                                         float(kept_norm2)), "sim_project")
 
     def swap_halves(self, other, qubit):
         """Exchange amplitude i + 2^qubit of this handle with amplitude i of

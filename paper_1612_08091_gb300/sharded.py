@@ -93,6 +93,89 @@ class ExchangePlanner:
             out.append(steps)
         return out
 
+    def schedule(self, gates):
+        """Order a list of gates ((targets, controls) in logical qubits) for
+        execution with as few exchanges as the greedy rule finds, keeping
+        the order of any two gates that share a qubit.  Gates whose targets
+        are local run as soon as every earlier gate on their qubits has run;
+        only when every remaining ready gate needs a global target is an
+        exchange made: the global target of the earliest such gate comes in,
+        and the local position given up is the one whose logical qubit is
+        next needed as a target furthest ahead in program order.  Long runs
+        of gates then sit between exchanges, and the shards fuse them into
+        blocks.  Returns a list of ("x", G, l) and ("g", index) steps and
+        leaves the layout as after the last step."""
+        ng = len(gates)
+        for k, (t, _) in enumerate(gates):
+            if len(t) > self.nl:
+                raise ValueError("gate %d needs %d local qubits, the shards have %d" % (k, len(t), self.nl))
+        per_q = [[] for _ in range(self.n)]  # program-order gate indices on each qubit
+        tuses = [[] for _ in range(self.n)]  # ... where the qubit is a target
+        for k, (t, c) in enumerate(gates):
+            for q in set(t) | set(c):
+                per_q[q].append(k)
+            for q in t:
+                tuses[q].append(k)
+        head = [0] * self.n  # next pending position in per_q[q]
+        tnext = [0] * self.n  # next pending position in tuses[q]
+        done = [False] * ng
+
+        def is_ready(k):
+            t, c = gates[k]
+            return all(per_q[q][head[q]] == k for q in set(t) | set(c))
+
+        out = []
+        ready = sorted({per_q[q][0] for q in range(self.n) if per_q[q] and is_ready(per_q[q][0])})
+        import heapq
+        heap = list(ready)
+        heapq.heapify(heap)
+        waiting = []  # ready gates blocked on a global target
+        remaining = ng
+        while remaining:
+            progressed = False
+            while heap:
+                k = heapq.heappop(heap)
+                t, c = gates[k]
+                if not all(self.is_local(q) for q in t):
+                    waiting.append(k)
+                    continue
+                out.append(("g", k))
+                done[k] = True
+                remaining -= 1
+                progressed = True
+                for q in set(t) | set(c):
+                    head[q] += 1
+                    if head[q] < len(per_q[q]):
+                        nk = per_q[q][head[q]]
+                        if is_ready(nk):
+                            heapq.heappush(heap, nk)
+                for q in t:
+                    tnext[q] += 1
+            if not remaining:
+                break
+            # every ready gate waits for a global target: bring in the
+            # earliest one's
+            waiting = sorted(set(w for w in waiting if not done[w]))
+            k = waiting[0]
+            t, _ = gates[k]
+            q = next(q for q in t if not self.is_local(q))
+            best, best_next = None, -1
+            for l in range(self.nl):
+                v = self.at[l]
+                if v in t:
+                    continue
+                u = tuses[v]
+                nxt = u[tnext[v]] if tnext[v] < len(u) else ng + 1
+                if nxt > best_next:
+                    best, best_next = l, nxt
+            G = self.pos[q]
+            self.exchange(G, best)
+            out.append(("x", G, best))
+            for w in waiting:
+                heapq.heappush(heap, w)
+            waiting = []
+        return out
+
     def restore(self):
         """Exchanges (G, l) and then local position swaps (a, b) that bring
         every logical qubit back to its own position."""
@@ -268,15 +351,15 @@ class ShardedSimulator:
         if not q:
             return
         plan = self.planner
-        uses = [set(t) for _, t, _ in q]
-        # replay the plan step by step so each gate sees the layout of its step
-        schedule = ExchangePlanner(self.n, self.g)
-        schedule.pos, schedule.at = list(plan.pos), list(plan.at)
-        steps = schedule.plan(uses)
-        for (m, t, c), ex in zip(q, steps):
-            for G, l in ex:
-                self._exchange(G, l)
-                plan.exchange(G, l)
+        # replay the schedule step by step so each gate sees its layout
+        sched = ExchangePlanner(self.n, self.g)
+        sched.pos, sched.at = list(plan.pos), list(plan.at)
+        for step in sched.schedule([(t, c) for _, t, c in q]):
+            if step[0] == "x":
+                self._exchange(step[1], step[2])
+                plan.exchange(step[1], step[2])
+                continue
+            m, t, c = q[step[1]]
             pt = [plan.pos[x] for x in t]
             shards, lc = shard_targets(plan, c)
             for s in shards:
@@ -333,9 +416,11 @@ class ShardedSimulator:
         p = self.planner.pos[qubit]
         for s, sh in enumerate(self.shards):
             if p < self.nl:
-                sh.project((p,), (b,), scale)
+                kept = p1s[s][p] if b else norms[s] - p1s[s][p]
+                sh.project((p,), (b,), scale, max(kept, 0.0))
             else:
-                sh.project((), (), scale if ((s >> (p - self.nl)) & 1) == b else 0.0)
+                keep = ((s >> (p - self.nl)) & 1) == b
+                sh.project((), (), scale if keep else 0.0, norms[s])
         return b, pb / norm
 
     def measure_all(self, u):

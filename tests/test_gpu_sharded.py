@@ -115,3 +115,35 @@ def test_swap_halves_and_project_calls(qs, oracle_mod):
         with qs.Simulator(n - 1, precision="c128") as c:
             with pytest.raises(qs.QsimError):
                 a.swap_halves(c, 0)
+
+
+def test_sharded_c64_long_circuit_keeps_the_norm(qs, oracle_mod):
+    """A depth-40 brickwork on 2 shards of a 20-qubit complex64 register,
+    flushed after every layer so that the top qubit is exchanged in every
+    layer (some 40 exchanges; unflushed, the scheduler needs only a few).
+    Each exchange passes the shards' exact norms on to their block passes'
+    norm control, so the norm stays at 1 instead of taking a new, slightly
+    drifted target after every exchange."""
+    from paper_1612_08091_gb300.sharded import ShardedSimulator
+
+    n = 20
+    ops = cg.random_u3_brickwork(n, 40, seed=8091)
+    ref = oracle_mod.OracleSim(n)
+    oracle_mod.run_ops(ref, ops)
+    with ShardedSimulator(n, global_qubits=1, precision="c64", fusion="greedy") as sim:
+        k = 0
+        for layer in range(40):
+            cnt = n + len(range(layer % 2, n - 1, 2))
+            sim.run(ops[k:k + cnt])
+            sim.flush()
+            k += cnt
+        assert k == len(ops)
+        p1, nrm = sim.probs_all()
+        ex = sim.exchanges
+        got = sim.get_amplitudes()
+    print("sharded c64, 20 qubits depth 40: %d exchanges, |norm2-1| %.2e, infidelity %.2e"
+          % (ex, abs(nrm - 1.0), infidelity(ref.psi, got)))
+    assert ex >= 20
+    assert abs(nrm - 1.0) <= 2e-6
+    assert infidelity(ref.psi, got) <= TOL64_INFID
+    np.testing.assert_allclose(p1, ref.probs_all(), atol=1e-5)

@@ -35,7 +35,7 @@ class OracleShard:
     def expect(self, terms):
         return self.o.expect(terms)
 
-    def project(self, qubits, bits, scale):
+    def project(self, qubits, bits, scale, kept_norm2=-1.0):
         idx = np.arange(1 << self.n)
         keep = np.ones(1 << self.n, dtype=bool)
         for q, b in zip(qubits, bits):
@@ -121,6 +121,45 @@ def test_planner_keeps_targets_local_and_is_no_worse_than_lru():
     # restoring the layout gives the identity
     ex, sw = p.restore()
     assert p.pos == list(range(n)) and p.at == list(range(n))
+
+
+def test_schedule_reorders_only_commuting_gates(oracle_mod):
+    """ExchangePlanner.schedule: every gate once, targets local at their
+    step, the order of gates sharing a qubit kept (so the reordered circuit,
+    run on the whole register, gives the same state), and on the 32-qubit
+    brickwork far fewer exchanges than keeping program order."""
+    from paper_1612_08091_gb300.sharded import ExchangePlanner
+
+    n, g = 9, 2
+    ops = mixed_circuit(n, 80, seed=5)
+    p = ExchangePlanner(n, g)
+    trace = ExchangePlanner(n, g)
+    order = []
+    for step in p.schedule([(op.targets, op.controls) for op in ops]):
+        if step[0] == "x":
+            trace.exchange(step[1], step[2])
+            continue
+        k = step[1]
+        assert all(trace.is_local(q) for q in ops[k].targets)
+        order.append(k)
+    assert sorted(order) == list(range(len(ops)))
+    for a in range(len(order)):
+        for b in range(a + 1, len(order)):
+            ka, kb = order[a], order[b]
+            qa = set(ops[ka].targets) | set(ops[ka].controls)
+            qb = set(ops[kb].targets) | set(ops[kb].controls)
+            if qa & qb:
+                assert ka < kb
+    ref = oracle_mod.OracleSim(n)
+    oracle_mod.run_ops(ref, ops)
+    re = oracle_mod.OracleSim(n)
+    oracle_mod.run_ops(re, [ops[k] for k in order])
+    np.testing.assert_allclose(re.psi, ref.psi, atol=1e-12)
+    bw = cg.random_u3_brickwork(32, 40, seed=8091)
+    steps = ExchangePlanner(32, 1).schedule([(op.targets, op.controls) for op in bw])
+    in_order = sum(len(v) for v in ExchangePlanner(32, 1).plan([set(op.targets) for op in bw]))
+    ex = sum(1 for st in steps if st[0] == "x")
+    assert ex <= 4 < in_order, (ex, in_order)
 
 
 @pytest.mark.parametrize("g", [1, 2, 3])
@@ -215,9 +254,11 @@ def _rank_main(rank, world, port, outq):
 
     ops = mixed_circuit(n, 50, seed=77)
     steps = ExchangePlanner(n, 1)
-    for op, ex in zip(ops, steps.plan([set(op.targets) for op in ops])):
-        for G, l in ex:
-            exchange(G, l)
+    for st in steps.schedule([(op.targets, op.controls) for op in ops]):
+        if st[0] == "x":
+            exchange(st[1], st[2])
+            continue
+        op = ops[st[1]]
         shards, lc = shard_targets(plan, op.controls)
         if rank in shards:
             shard.apply(gates.gate_matrix(op.kind, op.params), [plan.pos[t] for t in op.targets], lc)
