@@ -71,3 +71,27 @@ def test_noalloc_probs_match_oracle_and_sim_probs_all(prec, tol, oracle_mod):
     assert fn(dummy.data_ptr(), 37, precision, dummy.data_ptr(), None) == 9  # ENOTSUP
     assert fn(None, 5, precision, dummy.data_ptr(), None) == 1  # EINVAL
     assert fn(dummy.data_ptr(), 5, 3, dummy.data_ptr(), None) == 1
+
+
+def test_noalloc_probs_33_qubits_basis_state():
+    """Qubits 32 and above (their partial sums take a second per-lane
+    accumulator): a 33-qubit complex64 register (64 GiB) in a basis state
+    with bit 32 set; every probability is exactly 0 or 1."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1612_08091_gb300 as q
+
+    fn = _noalloc(q.load())
+    n = 33
+    basis = (1 << 32) | (1 << 20) | (1 << 5) | 1
+    out = torch.full((n + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    with q.Simulator(n, precision="c64") as sim:
+        sim.reset(basis)
+        ptr = sim.state_ptr()
+        assert fn(ptr, n, 1, out.data_ptr(), torch.cuda.current_stream().cuda_stream) == 0
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+    assert got[0] == 1.0
+    np.testing.assert_array_equal(got[1:], [(basis >> k) & 1 for k in range(n)])
+    torch.cuda.empty_cache()
