@@ -28,6 +28,7 @@ machine with one GPU per shard the same schedule would move the exchanged
 halves between devices; here all shards share one device.
 """
 import bisect
+import heapq
 
 import numpy as np
 
@@ -125,14 +126,10 @@ class ExchangePlanner:
             return all(per_q[q][head[q]] == k for q in set(t) | set(c))
 
         out = []
-        ready = sorted({per_q[q][0] for q in range(self.n) if per_q[q] and is_ready(per_q[q][0])})
-        import heapq
-        heap = list(ready)
-        heapq.heapify(heap)
+        heap = sorted({per_q[q][0] for q in range(self.n) if per_q[q] and is_ready(per_q[q][0])})
         waiting = []  # ready gates blocked on a global target
         remaining = ng
         while remaining:
-            progressed = False
             while heap:
                 k = heapq.heappop(heap)
                 t, c = gates[k]
@@ -142,7 +139,6 @@ class ExchangePlanner:
                 out.append(("g", k))
                 done[k] = True
                 remaining -= 1
-                progressed = True
                 for q in set(t) | set(c):
                     head[q] += 1
                     if head[q] < len(per_q[q]):
