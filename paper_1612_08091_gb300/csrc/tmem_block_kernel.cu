@@ -116,6 +116,7 @@ struct TmArgs {
     int prev_grid;
     int fpos[7];               // tile column bit j <-> qubit fpos[j]
     uint64_t rdep[64];         // address bits of block row r
+    uint64_t qoff[4];          // W = 16: address bits of column 4q + i relative to column 4q
 };
 
 // 32-byte global accesses (one whole sector per thread): four adjacent
@@ -131,6 +132,20 @@ __device__ __forceinline__ void st_v8(float2 *p, const float4 &a, const float4 &
                  : "memory");
 }
 
+// 16 consecutive fp32 columns of this warp's 32 TMEM lanes, waited for
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // D(tmem) (+)= A(tmem) * B(smem)^T, M = 128, K = 16
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
@@ -142,12 +157,27 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
         : "memory");
 }
 
+// Stage slot of half-slot s (16 bytes: rows 2s, 2s+1 of a 16-row line) of
+// tile column c within its warp's 4 KB stage (32 columns x 8 half-slots):
+// s XOR a column-dependent pattern, so that both the lanes reading their own
+// column and the quads reading one column's line hit 8 different 16-byte
+// bank groups per 8 lanes.
+__device__ __forceinline__ unsigned stage_slot(unsigned c, unsigned s) {
+    return s ^ (((c >> 2) & 1u) | ((c & 3u) << 1));
+}
+
 // W: amplitudes per global access.  W = 2: qubit 0 is in S, so rows r and
 // r+1 (r even) are adjacent amplitudes and move as one 16-byte access.  W = 4:
 // qubits 0 and 1 are in S, rows 4j..4j+3 are adjacent and move as one
 // 32-byte access; the tile columns are then at least 4 amplitudes apart, and
 // narrower accesses would use half a sector per instruction.  W = 1: 8-byte
-// accesses, the columns being adjacent amplitudes.
+// accesses, the columns being adjacent amplitudes.  W = 16: qubits 0..3 are
+// in S, so each 16-row line of a column is 128 contiguous bytes, but the
+// lanes' columns lie 512 (K = 6) or 256 (K = 5) bytes apart and a warp
+// access with one column per lane touches 32 lines; instead the four lanes of
+// a quad read one column's line together (32 bytes each: 8 lines per warp
+// access) and a transpose through a 4 KB per-warp shared-memory stage gives
+// each lane its own column before the split, and back before the stores.
 template <int K, int W>
 __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tmem(const TmArgs args) {
     using Sh = TmShape<K>;
@@ -159,6 +189,8 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
     double *s_red = (double *)(bars + 4);  // [4 warps][2]
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    // W = 16: this warp's stage (32 columns x 8 half-slots of 16 bytes)
+    float4 *ws = (float4 *)((unsigned char *)bars + kTmExtra) + warp * 256;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -213,12 +245,26 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
 #pragma unroll
         for (int j = 0; j < 7; ++j)
             if ((tid >> j) & 1) coff |= 1ull << args.fpos[j];
+        // W = 16: this lane's quad and place in it; the quad's first column
+        // and the steps to the other three
+        const unsigned lane = (unsigned)tid & 31u, k4 = lane & 3u, q4 = lane >> 2;
+        const uint64_t coffq = coff - args.qoff[k4];
+        const unsigned fl = stage_slot(lane, 0);  // this lane's stage pattern
         const int nterms = args.nsplit == 3 ? 5 : 3;
 
         float4 v[Sh::kRows / 2];  // rows 2j, 2j+1 of this column: (re, im, re, im)
         auto load_tile = [&](uint64_t tt) {
             const float2 *p = args.psi + insert_zeros(tt, args.vspec) + coff;
-            if constexpr (W == 4) {
+            if constexpr (W == 16) {
+                // quad layout: v[8m + 2i + h] = half h of rows 16m + 4k4 ..
+                // 16m + 4k4 + 3 of the quad's column i
+                const float2 *pq = args.psi + insert_zeros(tt, args.vspec) + coffq + 4 * k4;
+#pragma unroll
+                for (int m = 0; m < Sh::kRows / 16; ++m)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        ld_v8(pq + args.qoff[i] + args.rdep[16 * m], v[8 * m + 2 * i], v[8 * m + 2 * i + 1]);
+            } else if constexpr (W == 4) {
 #pragma unroll
                 for (int j = 0; j < Sh::kRows / 4; ++j) ld_v8(p + args.rdep[4 * j], v[2 * j], v[2 * j + 1]);
             } else {
@@ -234,7 +280,8 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
             }
         };
         auto epilogue = [&](uint64_t tt) {
-            float2 *p = args.psi + insert_zeros(tt, args.vspec) + coff;
+            float2 *const pb = args.psi + insert_zeros(tt, args.vspec);
+            float2 *p = pb + coff;
             // four FP32 partial sums (chains of 2^K / 2 terms): the rounding
             // of a long chain is systematic when many amplitudes are equal;
             // FP64 across tiles (an FP64 add per 16 rows measured 1.2 %
@@ -242,6 +289,33 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
             float ssq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kN / 32; ++chunk) {
+                if constexpr (W == 16) {
+                    // own column's line (read in two halves of 8 rows, to
+                    // hold fewer registers) -> stage -> quad layout ->
+                    // 32-byte stores, four lanes per 128-byte line
+                    __syncwarp();
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        float d[16];  // rows 16 chunk + 8 half .. + 7
+                        tmem_ld16(lanes + Sh::kColD + chunk * 32 + half * 16, d);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) ssq[q & 3] = fmaf(d[q], d[q], ssq[q & 3]);
+#pragma unroll
+                        for (int s2 = 0; s2 < 4; ++s2)
+                            ws[lane * 8 + ((4 * half + s2) ^ fl)] =
+                                make_float4(d[4 * s2] * scale, d[4 * s2 + 1] * scale, d[4 * s2 + 2] * scale,
+                                            d[4 * s2 + 3] * scale);
+                    }
+                    __syncwarp();
+                    float2 *pq = pb + coffq + 4 * k4 + args.rdep[16 * chunk];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const unsigned c = 4 * q4 + i;
+                        const float4 a0 = ws[c * 8 + stage_slot(c, 2 * k4)];
+                        const float4 a1 = ws[c * 8 + stage_slot(c, 2 * k4 + 1)];
+                        st_v8(pq + args.qoff[i], a0, a1);
+                    }
+                } else {
                 float d[32];  // rows 16 chunk .. 16 chunk + 15, (re, im) interleaved
                 tmem_ld32(lanes + Sh::kColD + chunk * 32, d);
 #pragma unroll
@@ -263,6 +337,7 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
                         p[args.rdep[r]] = make_float2(o.x, o.y);
                         p[args.rdep[r + 1]] = make_float2(o.z, o.w);
                     }
+                }
                 }
             }
             nrm_out += (double)((ssq[0] + ssq[1]) + (ssq[2] + ssq[3]));
@@ -288,6 +363,20 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kRows / 16; ++chunk) {
                 uint32_t hw[16], lw[16];
+                if constexpr (W == 16) {
+                    // quad layout -> stage -> this lane's own column, rows
+                    // 16 chunk .. 16 chunk + 15 in v[8 chunk .. 8 chunk + 7]
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const unsigned c = 4 * q4 + i;
+                        ws[c * 8 + stage_slot(c, 2 * k4)] = v[8 * chunk + 2 * i];
+                        ws[c * 8 + stage_slot(c, 2 * k4 + 1)] = v[8 * chunk + 2 * i + 1];
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int s2 = 0; s2 < 8; ++s2) v[8 * chunk + s2] = ws[lane * 8 + (s2 ^ fl)];
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float4 x = v[chunk * 8 + j];
@@ -404,9 +493,13 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
             if ((r >> j) & 1) d |= 1ull << qubits[j];
         a.rdep[r] = d;
     }
+    for (int i = 0; i < 4; ++i)
+        a.qoff[i] = ((i & 1) ? 1ull << a.fpos[0] : 0ull) + ((i & 2) ? 1ull << a.fpos[1] : 0ull);
     // amplitudes per global access (see k_block_tmem)
-    const int W = (qubits[0] == 0 && qubits[1] == 1) ? 4 : (qubits[0] == 0 ? 2 : 1);
-    const int wi = W == 4 ? 2 : W - 1;
+    // the W = 16 stage does not fit beside a three-part gate operand
+    const bool low4 = qubits[0] == 0 && qubits[1] == 1 && qubits[2] == 2 && qubits[3] == 3;
+    const int W = (low4 && nsplit == 2) ? 16 : (qubits[0] == 0 && qubits[1] == 1) ? 4 : (qubits[0] == 0 ? 2 : 1);
+    const int wi = W == 16 ? 3 : W == 4 ? 2 : W - 1;
 
     std::vector<unsigned char> rec;
     build_operand(m, K, nsplit, rec);
@@ -414,10 +507,12 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
     int rc = stage_operand(s, rec.data(), rec.size(), &dev_rec);
     if (rc) return rc;
 
-    auto kernel = W == 4 ? k_block_tmem<K, 4> : (W == 2 ? k_block_tmem<K, 2> : k_block_tmem<K, 1>);
+    auto kernel = W == 16 ? k_block_tmem<K, 16>
+                          : W == 4 ? k_block_tmem<K, 4> : (W == 2 ? k_block_tmem<K, 2> : k_block_tmem<K, 1>);
     const int dev = s->device;
     if (dev < 0 || dev >= 64) return QSIM_ENOTSUP;
-    static int smem_for[3][64][4] = {{{0}}};  // [access width][device][nsplit]: dynamic shared memory to request
+    static int smem_for[4][64][4] = {{{0}}};  // [access width][device][nsplit]: dynamic shared memory to request
+    static int smem_attr[4][64] = {{0}};      // [access width][device]: the kernel's shared-memory limit set so far
     int &smem = smem_for[wi][dev][nsplit];
     if (!smem) {
         // At most kCtasPerSm CTAs per SM, as many as the tensor memory holds
@@ -431,12 +526,16 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         if (e != cudaSuccess) return cuda_err(s, e, "tmem block kernel attributes");
-        int bytes = 1024 + nsplit * Sh::kBPart + kTmExtra;
+        int bytes = 1024 + nsplit * Sh::kBPart + kTmExtra + (W == 16 ? kTmThreads / 32 * 4096 : 0);
         const int cap = Sh::kCtasPerSm;
         const int by_regs = regs_sm / (fa.numRegs * kTmThreads);
         if (by_regs > cap && smem_sm / (bytes + 1024) > cap) bytes = smem_sm / (cap + 1) - 1024 + 64;
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return cuda_err(s, e, "tmem block kernel attribute");
+        // the limit is per kernel, shared by both operand sizes: only raise it
+        if (bytes > smem_attr[wi][dev]) {
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return cuda_err(s, e, "tmem block kernel attribute");
+            smem_attr[wi][dev] = bytes;
+        }
         if (getenv("QSIM_DEBUG"))
             fprintf(stderr, "qsim: k_block_tmem<%d,%d> regs %d smem %d (registers allow %d CTAs/SM, cap %d)\n", K, W,
                     fa.numRegs, bytes, by_regs, cap);
