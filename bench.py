@@ -175,7 +175,8 @@ TRAFFIC_KERNEL = {"block_tc": "k_block_tmem5", "block_tc6": "k_block_tmem6"}
 def kernel_traffic(kernel, n):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.json), scaled from the captured register size to n
-    (the block kernels' traffic is proportional to 2^n).  None if there is
+    (the block kernels' traffic is proportional to 2^n); with n None, the
+    capture's DRAM bytes per algorithmic byte.  None if there is
     no capture or the kernel's sources changed since it was taken (SHA-256
     over the listed source files, in order)."""
     import hashlib
@@ -192,6 +193,8 @@ def kernel_traffic(kernel, n):
         return None
     if h.hexdigest() != rec["sha256"]:
         return None
+    if n is None:  # the captured DRAM bytes per algorithmic byte
+        return rec["bytes_per_launch"] / rec["alg_bytes_per_launch"]
     return rec["bytes_per_launch"] * 2.0 ** (n - rec["n"])
 
 
@@ -622,6 +625,9 @@ def run_vqe(args):
     m = cfg[1]
     hbm = float(sum(8.0 * (1 << c["n"]) * (4 * c["L"] + 4) for c in circuits if c["n"] > m))
     peak, peak_kind = measured_peaks()
+    # DRAM bytes: the ncu capture's ratio to the algorithmic bytes (the
+    # global-memory kernel's traffic grows with the state passes it makes)
+    ratio = kernel_traffic("k_vqe_batch_global", None)
     out = {"metric": "variational batch throughput", "value": upd / t, "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
            "dtype": "c64", "data": "synthetic",
@@ -637,7 +643,8 @@ def run_vqe(args):
                                  "frac": None if not t_glob else hbm / t_glob / 1e9 / peak},
                "timing": "each class alone as its own batch, same launch configuration"},
            "roofline": {"bound": "hbm", "achieved": hbm / t / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": hbm / t / 1e9 / peak, "peak_source": peak_kind, "traffic": None,
+                        "frac": hbm / t / 1e9 / peak, "peak_source": peak_kind,
+                        "traffic": None if ratio is None else ratio * hbm,
                         "bytes_per_step": hbm,
                         "what": "global-memory traffic of the circuits above the shared-memory size (n > %d): "
                                 "4L + 4 state passes each; the rest stays on chip" % m},

@@ -130,6 +130,30 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *w) {
         "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
         : "memory");
 }
+// 16 lanes x 16 consecutive 32-bit columns (shape 16x256b, two
+// repetitions of 8 columns).  Thread t of the warp holds, for repetition
+// rep, columns 8 rep + 2 (t & 3) and + 1 of lane (t >> 2) in w[4 rep],
+// w[4 rep + 1] and the same columns of lane (t >> 2) + 8 in w[4 rep + 2],
+// w[4 rep + 3]: the four threads of a quad share two lanes.
+__device__ __forceinline__ void tmem_st16x256b_x2(uint32_t taddr, const uint32_t *w) {
+    asm volatile("tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(w[0]),
+                 "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+// The same fragment with four repetitions (32 columns), read and waited for
+__device__ __forceinline__ void tmem_ld16x256b_x4(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tcgen05_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_half, float hi_half) {

@@ -132,20 +132,6 @@ __device__ __forceinline__ void st_v8(float2 *p, const float4 &a, const float4 &
                  : "memory");
 }
 
-// 16 consecutive fp32 columns of this warp's 32 TMEM lanes, waited for
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // D(tmem) (+)= A(tmem) * B(smem)^T, M = 128, K = 16
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
@@ -157,15 +143,6 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
         : "memory");
 }
 
-// Stage slot of half-slot s (16 bytes: rows 2s, 2s+1 of a 16-row line) of
-// tile column c within its warp's 4 KB stage (32 columns x 8 half-slots):
-// s XOR a column-dependent pattern, so that both the lanes reading their own
-// column and the quads reading one column's line hit 8 different 16-byte
-// bank groups per 8 lanes.
-__device__ __forceinline__ unsigned stage_slot(unsigned c, unsigned s) {
-    return s ^ (((c >> 2) & 1u) | ((c & 3u) << 1));
-}
-
 // W: amplitudes per global access.  W = 2: qubit 0 is in S, so rows r and
 // r+1 (r even) are adjacent amplitudes and move as one 16-byte access.  W = 4:
 // qubits 0 and 1 are in S, rows 4j..4j+3 are adjacent and move as one
@@ -174,10 +151,16 @@ __device__ __forceinline__ unsigned stage_slot(unsigned c, unsigned s) {
 // accesses, the columns being adjacent amplitudes.  W = 16: qubits 0..3 are
 // in S, so each 16-row line of a column is 128 contiguous bytes, but the
 // lanes' columns lie 512 (K = 6) or 256 (K = 5) bytes apart and a warp
-// access with one column per lane touches 32 lines; instead the four lanes of
-// a quad read one column's line together (32 bytes each: 8 lines per warp
-// access) and a transpose through a 4 KB per-warp shared-memory stage gives
-// each lane its own column before the split, and back before the stores.
+// access with one column per lane touches 32 lines.  Instead the four lanes
+// of a quad read one column's line together (32 bytes each: 8 lines per
+// warp access) and move it to and from tensor memory with the 16x256b
+// shape, in which a quad shares a TMEM lane and each of its threads holds
+// two adjacent 32-bit columns per 8.  Thread k of a quad holds rows 4k..4k+3
+// of each 16-row line; the host orders the gate operand's K (input rows)
+// and N (output rows) to match: A column 16G + 8h + 2k + e holds row
+// 16G + 4k + 2h + e, and D columns 2j, 2j + 1 with j = 16G + 4h + k hold
+// output row 16G + 4k + h.  Tile column 32w + q + 8i (warp w, quad q) is
+// TMEM lane 32w + q + 8i as in the other widths.
 template <int K, int W>
 __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tmem(const TmArgs args) {
     using Sh = TmShape<K>;
@@ -189,8 +172,6 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
     double *s_red = (double *)(bars + 4);  // [4 warps][2]
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    // W = 16: this warp's stage (32 columns x 8 half-slots of 16 bytes)
-    float4 *ws = (float4 *)((unsigned char *)bars + kTmExtra) + warp * 256;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -245,11 +226,13 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
 #pragma unroll
         for (int j = 0; j < 7; ++j)
             if ((tid >> j) & 1) coff |= 1ull << args.fpos[j];
-        // W = 16: this lane's quad and place in it; the quad's first column
-        // and the steps to the other three
+        // W = 16: this lane's place k4 in its quad q4; the address bits of
+        // the quad's first column 32 warp + q4 (the others: + qoff[i])
         const unsigned lane = (unsigned)tid & 31u, k4 = lane & 3u, q4 = lane >> 2;
-        const uint64_t coffq = coff - args.qoff[k4];
-        const unsigned fl = stage_slot(lane, 0);  // this lane's stage pattern
+        uint64_t coffq = 0;
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+            if ((((tid & ~31) | (int)q4) >> j) & 1) coffq |= 1ull << args.fpos[j];
         const int nterms = args.nsplit == 3 ? 5 : 3;
 
         float4 v[Sh::kRows / 2];  // rows 2j, 2j+1 of this column: (re, im, re, im)
@@ -257,7 +240,7 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
             const float2 *p = args.psi + insert_zeros(tt, args.vspec) + coff;
             if constexpr (W == 16) {
                 // quad layout: v[8m + 2i + h] = half h of rows 16m + 4k4 ..
-                // 16m + 4k4 + 3 of the quad's column i
+                // 16m + 4k4 + 3 of tile column 32 warp + q4 + 8i
                 const float2 *pq = args.psi + insert_zeros(tt, args.vspec) + coffq + 4 * k4;
 #pragma unroll
                 for (int m = 0; m < Sh::kRows / 16; ++m)
@@ -290,30 +273,22 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kN / 32; ++chunk) {
                 if constexpr (W == 16) {
-                    // own column's line (read in two halves of 8 rows, to
-                    // hold fewer registers) -> stage -> quad layout ->
-                    // 32-byte stores, four lanes per 128-byte line
-                    __syncwarp();
+                    // output rows 16 chunk + 4k4 .. + 3 of tile columns
+                    // 32 warp + q4 + 8i: 32-byte stores, four lanes per line
+                    float2 *pq = pb + coffq + 4 * k4 + args.rdep[16 * chunk];
 #pragma unroll
-                    for (int half = 0; half < 2; ++half) {
-                        float d[16];  // rows 16 chunk + 8 half .. + 7
-                        tmem_ld16(lanes + Sh::kColD + chunk * 32 + half * 16, d);
+                    for (int b2 = 0; b2 < 2; ++b2) {
+                        float d[16];  // d[4 rho + 2c + a]: row 16 chunk + 4k4 + rho of column i = 2 b2 + c
+                        tmem_ld16x256b_x4(lanes + ((uint32_t)(16 * b2) << 16) + Sh::kColD + chunk * 32, d);
 #pragma unroll
                         for (int q = 0; q < 16; ++q) ssq[q & 3] = fmaf(d[q], d[q], ssq[q & 3]);
 #pragma unroll
-                        for (int s2 = 0; s2 < 4; ++s2)
-                            ws[lane * 8 + ((4 * half + s2) ^ fl)] =
-                                make_float4(d[4 * s2] * scale, d[4 * s2 + 1] * scale, d[4 * s2 + 2] * scale,
-                                            d[4 * s2 + 3] * scale);
-                    }
-                    __syncwarp();
-                    float2 *pq = pb + coffq + 4 * k4 + args.rdep[16 * chunk];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const unsigned c = 4 * q4 + i;
-                        const float4 a0 = ws[c * 8 + stage_slot(c, 2 * k4)];
-                        const float4 a1 = ws[c * 8 + stage_slot(c, 2 * k4 + 1)];
-                        st_v8(pq + args.qoff[i], a0, a1);
+                        for (int c = 0; c < 2; ++c)
+                            st_v8(pq + args.qoff[2 * b2 + c],
+                                  make_float4(d[2 * c] * scale, d[2 * c + 1] * scale, d[4 + 2 * c] * scale,
+                                              d[5 + 2 * c] * scale),
+                                  make_float4(d[8 + 2 * c] * scale, d[9 + 2 * c] * scale, d[12 + 2 * c] * scale,
+                                              d[13 + 2 * c] * scale));
                     }
                 } else {
                 float d[32];  // rows 16 chunk .. 16 chunk + 15, (re, im) interleaved
@@ -362,33 +337,44 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
             float xsq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int chunk = 0; chunk < Sh::kRows / 16; ++chunk) {
-                uint32_t hw[16], lw[16];
                 if constexpr (W == 16) {
-                    // quad layout -> stage -> this lane's own column, rows
-                    // 16 chunk .. 16 chunk + 15 in v[8 chunk .. 8 chunk + 7]
-                    __syncwarp();
+                    // lanes 32 warp + 16 b2 + q4 + 8c (tile column i = 2 b2 + c),
+                    // A columns 16 chunk + 8h + 2k4 + e = rows 16 chunk + 4k4 + 2h + e
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const unsigned c = 4 * q4 + i;
-                        ws[c * 8 + stage_slot(c, 2 * k4)] = v[8 * chunk + 2 * i];
-                        ws[c * 8 + stage_slot(c, 2 * k4 + 1)] = v[8 * chunk + 2 * i + 1];
+                    for (int b2 = 0; b2 < 2; ++b2) {
+                        uint32_t hw[8], lw[8];
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const float4 x = v[8 * chunk + 2 * (2 * b2 + c) + h];
+                                xsq[0] = fmaf(x.x, x.x, xsq[0]);
+                                xsq[1] = fmaf(x.y, x.y, xsq[1]);
+                                xsq[2] = fmaf(x.z, x.z, xsq[2]);
+                                xsq[3] = fmaf(x.w, x.w, xsq[3]);
+                                split_pair(x.x, x.y, hw[4 * h + 2 * c], lw[4 * h + 2 * c]);
+                                split_pair(x.z, x.w, hw[4 * h + 2 * c + 1], lw[4 * h + 2 * c + 1]);
+                            }
+                        const uint32_t l16 = lanes + ((uint32_t)(16 * b2) << 16) + chunk * 16;
+                        tmem_st16x256b_x2(l16 + Sh::kColAHi, hw);
+                        tmem_st16x256b_x2(l16 + Sh::kColALo, lw);
                     }
-                    __syncwarp();
+                } else {
+                    // this lane's own column: A columns 16 chunk + j = rows
+                    uint32_t hw[16], lw[16];
 #pragma unroll
-                    for (int s2 = 0; s2 < 8; ++s2) v[8 * chunk + s2] = ws[lane * 8 + (s2 ^ fl)];
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 x = v[chunk * 8 + j];
+                        xsq[0] = fmaf(x.x, x.x, xsq[0]);
+                        xsq[1] = fmaf(x.y, x.y, xsq[1]);
+                        xsq[2] = fmaf(x.z, x.z, xsq[2]);
+                        xsq[3] = fmaf(x.w, x.w, xsq[3]);
+                        split_pair(x.x, x.y, hw[2 * j], lw[2 * j]);
+                        split_pair(x.z, x.w, hw[2 * j + 1], lw[2 * j + 1]);
+                    }
+                    tmem_st16(lanes + Sh::kColAHi + chunk * 16, hw);
+                    tmem_st16(lanes + Sh::kColALo + chunk * 16, lw);
                 }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float4 x = v[chunk * 8 + j];
-                    xsq[0] = fmaf(x.x, x.x, xsq[0]);
-                    xsq[1] = fmaf(x.y, x.y, xsq[1]);
-                    xsq[2] = fmaf(x.z, x.z, xsq[2]);
-                    xsq[3] = fmaf(x.w, x.w, xsq[3]);
-                    split_pair(x.x, x.y, hw[2 * j], lw[2 * j]);
-                    split_pair(x.z, x.w, hw[2 * j + 1], lw[2 * j + 1]);
-                }
-                tmem_st16(lanes + Sh::kColAHi + chunk * 16, hw);
-                tmem_st16(lanes + Sh::kColALo + chunk * 16, lw);
             }
             nrm_in += (double)((xsq[0] + xsq[1]) + (xsq[2] + xsq[3]));
             tcgen05_wait_st();
@@ -448,15 +434,23 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
 }
 
 // The B operand image: the nsplit bf16 parts of R = real form of U (D = 2^K
-// rows), each N rows (output index 2r+a) x N K elements (input index 2r'+b)
+// rows), each N rows (output index 2j+a) x N K elements (input index 2j'+b)
 // in K halves of 64 elements; within a half, row `row` is 128 bytes at
-// row * 128 with its 16-byte chunks XOR-swizzled by row & 7.
-void build_operand(const cd *U, int K, int nsplit, std::vector<unsigned char> &rec) {
+// row * 128 with its 16-byte chunks XOR-swizzled by row & 7.  Output j is
+// block row orow(j) and input j' block row irow(j'): the identity, or for
+// the quad fragments of W = 16 (see k_block_tmem) orow(16G + 4h + k) =
+// 16G + 4k + h and irow(16G + 8h + 2k + e) = 16G + 4k + 2h + e.
+int quad_out_row(int j) { return (j & ~15) | ((j & 3) << 2) | ((j >> 2) & 3); }
+int quad_in_row(int j) { return (j & ~15) | (((j >> 1) & 3) << 2) | (((j >> 3) & 1) << 1) | (j & 1); }
+
+void build_operand(const cd *U, int K, int nsplit, bool quad, std::vector<unsigned char> &rec) {
     const int D = 1 << K, N = 2 * D, half = N * 128, part = (N / 64) * half;
     rec.assign((size_t)nsplit * part, 0);
     for (int row = 0; row < N; ++row)
         for (int k = 0; k < N; ++k) {
-            const cd u = U[(row >> 1) * D + (k >> 1)];
+            const int ro = quad ? quad_out_row(row >> 1) : row >> 1;
+            const int ri = quad ? quad_in_row(k >> 1) : k >> 1;
+            const cd u = U[ro * D + ri];
             const int a = row & 1, b = k & 1;
             double rem = a == 0 ? (b == 0 ? u.real() : -u.imag()) : (b == 0 ? u.imag() : u.real());
             const int kb = (k & 63) * 2;
@@ -493,16 +487,16 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
             if ((r >> j) & 1) d |= 1ull << qubits[j];
         a.rdep[r] = d;
     }
+    // W = 16: tile columns 32w + q + 8i lie qoff[i] from 32w + q
     for (int i = 0; i < 4; ++i)
-        a.qoff[i] = ((i & 1) ? 1ull << a.fpos[0] : 0ull) + ((i & 2) ? 1ull << a.fpos[1] : 0ull);
+        a.qoff[i] = ((i & 1) ? 1ull << a.fpos[3] : 0ull) + ((i & 2) ? 1ull << a.fpos[4] : 0ull);
     // amplitudes per global access (see k_block_tmem)
-    // the W = 16 stage does not fit beside a three-part gate operand
     const bool low4 = qubits[0] == 0 && qubits[1] == 1 && qubits[2] == 2 && qubits[3] == 3;
-    const int W = (low4 && nsplit == 2) ? 16 : (qubits[0] == 0 && qubits[1] == 1) ? 4 : (qubits[0] == 0 ? 2 : 1);
+    const int W = low4 ? 16 : (qubits[0] == 0 && qubits[1] == 1) ? 4 : (qubits[0] == 0 ? 2 : 1);
     const int wi = W == 16 ? 3 : W == 4 ? 2 : W - 1;
 
     std::vector<unsigned char> rec;
-    build_operand(m, K, nsplit, rec);
+    build_operand(m, K, nsplit, W == 16, rec);
     unsigned char *dev_rec = nullptr;
     int rc = stage_operand(s, rec.data(), rec.size(), &dev_rec);
     if (rc) return rc;
@@ -526,7 +520,7 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         if (e != cudaSuccess) return cuda_err(s, e, "tmem block kernel attributes");
-        int bytes = 1024 + nsplit * Sh::kBPart + kTmExtra + (W == 16 ? kTmThreads / 32 * 4096 : 0);
+        int bytes = 1024 + nsplit * Sh::kBPart + kTmExtra;
         const int cap = Sh::kCtasPerSm;
         const int by_regs = regs_sm / (fa.numRegs * kTmThreads);
         if (by_regs > cap && smem_sm / (bytes + 1024) > cap) bytes = smem_sm / (cap + 1) - 1024 + 64;

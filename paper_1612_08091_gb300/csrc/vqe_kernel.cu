@@ -465,11 +465,14 @@ __global__ void __launch_bounds__(T, GLOBAL ? kGlobalCtas : 1) k_vqe_batch(const
             // is bounded; on time-out the CTA raises the error flag and
             // stops.
             constexpr int g = kGlobalBits;
-            const int h = n - g, lowrun = g - h;  // h >= 1 and lowrun >= 0 (n <= 2g)
+            // the top-qubit pass takes tiles of the whole pair buffer, 2^(g+1)
+            // amplitudes: 2^h runs of 2^lowrun (h >= 1, lowrun >= 1 for n <= 2g)
+            const int h = n - g, lowrun = g + 1 - h;
             float2 *src = A.gbuf + (size_t)blockIdx.x * 2 * A.gstride;
             float2 *dst = src + A.gstride;
             const unsigned G = 1u << g, nchunks = 1u << h, hmask = nchunks - 1u, gmask = G - 1u;
             const unsigned run_bytes = 8u << lowrun;  // a high-pass tile is 2^h runs of 2^lowrun amplitudes
+            const unsigned ntiles = nchunks / 2, GT = 2u * G;
             float2 *const s_ttop = sm + ((size_t)2 << g);  // phases of the top h qubits, after the pair buffer
             for (unsigned i = threadIdx.x; i < N; i += T) src[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
             __syncthreads();
@@ -555,12 +558,12 @@ __global__ void __launch_bounds__(T, GLOBAL ? kGlobalCtas : 1) k_vqe_batch(const
             // to sm[top << lowrun]
             auto load_tile = [&](const float2 *from, unsigned t) {
                 if (run_bytes < 16) {  // runs below the bulk-copy granule: plain loads
-                    for (unsigned e = threadIdx.x; e < G; e += T) sm[e] = from[tile_index(t, e)];
+                    for (unsigned e = threadIdx.x; e < GT; e += T) sm[e] = from[tile_index(t, e)];
                     __syncthreads();
                     return true;
                 }
                 before_copies();
-                if (threadIdx.x == 0) mbar_expect_tx(s_bar, 8u * G);
+                if (threadIdx.x == 0) mbar_expect_tx(s_bar, 8u * GT);
                 __syncthreads();
                 for (unsigned top = threadIdx.x; top < nchunks; top += T) {
                     bulk_copy(sm + (top << lowrun), from + ((size_t)t << lowrun) + ((size_t)top << g), run_bytes,
@@ -575,7 +578,7 @@ __global__ void __launch_bounds__(T, GLOBAL ? kGlobalCtas : 1) k_vqe_batch(const
                 build_phase_table(s_thi, g - 7, s_ph + 7, make_float2(1.f, 0.f));
                 build_phase_table(s_ttop, h, s_ph + g, make_float2(1.f, 0.f));
                 // the pair pass's rotations in kPairOrder; the top-qubit
-                // pass's masks (tile bits lowrun..g-1)
+                // pass's masks (tile bits lowrun..g)
                 if (threadIdx.x < (unsigned)g) s_rotp[threadIdx.x] = s_rot[kPairOrder[threadIdx.x]];
                 if (threadIdx.x < (unsigned)h) s_mask[g + threadIdx.x] = 1u << (lowrun + threadIdx.x);
                 __syncthreads();
@@ -595,14 +598,14 @@ __global__ void __launch_bounds__(T, GLOBAL ? kGlobalCtas : 1) k_vqe_batch(const
                 }
                 // high pass on dst, in place: RY on the top qubits, then
                 // their RZ phases on the way out
-                for (unsigned t = 0; t < nchunks && !failed; ++t) {
+                for (unsigned t = 0; t < ntiles && !failed; ++t) {
                     if (!load_tile(dst, t)) {
                         failed = true;
                         break;
                     }
-                    gates_blocked(sm, g, s_mask + g, s_rot + g, h);
+                    gates_blocked(sm, g + 1, s_mask + g, s_rot + g, h);
                     const unsigned fhi = s_flip >> g;  // flips of the top qubits
-                    for (unsigned e = threadIdx.x; e < G; e += T) {
+                    for (unsigned e = threadIdx.x; e < GT; e += T) {
                         const unsigned ef = e ^ (fhi << lowrun);
                         dst[tile_index(t, e)] = cmul(sm[ef], s_ttop[ef >> lowrun]);
                     }
@@ -640,12 +643,12 @@ __global__ void __launch_bounds__(T, GLOBAL ? kGlobalCtas : 1) k_vqe_batch(const
                 }
                 store_pair(dst, pr, false, 0u);
             }
-            for (unsigned t = 0; t < nchunks && !failed; ++t) {
+            for (unsigned t = 0; t < ntiles && !failed; ++t) {
                 if (!load_tile(dst, t)) {
                     failed = true;
                     break;
                 }
-                for (int q = g; q < n; ++q) xf += x_chunk(sm, g, lowrun + (q - g));
+                for (int q = g; q < n; ++q) xf += x_chunk(sm, g + 1, lowrun + (q - g));
                 __syncthreads();
             }
             zz = (double)zf;

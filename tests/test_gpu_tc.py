@@ -37,6 +37,8 @@ PLACEMENTS = [
     (16, (0, 1, 14, 8, 3)),       # unsorted target order
     (15, (4, 5, 6, 7)),           # 4 qubits, padded to 5
     (14, (13, 0, 7)),             # 3 qubits: CUDA-core block
+    (15, (0, 1, 2, 3, 10)),       # qubits 0..3 (quad fragments), 8 tiles
+    (14, (2, 0, 3, 1)),           # 4 qubits padded to {0..4}: quad fragments
 ]
 
 

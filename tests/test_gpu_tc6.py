@@ -38,6 +38,8 @@ PLACEMENTS = [
     (15, (0, 3, 6, 9, 12, 14)),      # spread, with qubit 0
     (16, (2, 5, 6, 7, 13, 15)),      # spread, without qubit 0
     (17, (16, 0, 9, 4, 12, 1)),      # unsorted target order
+    (16, (0, 1, 2, 3, 4, 9)),        # qubits 0..3 (quad fragments), 8 tiles
+    (17, (3, 0, 12, 2, 1, 5)),       # qubits 0..3, unsorted, 16 tiles
 ]
 
 
