@@ -866,6 +866,14 @@ def run_circuit(args):
             check = {"norm2": nrm}
     torch.cuda.empty_cache()
     no_perm = None
+    no_prod = None
+    if w == "grover":
+        # the same iterations with the one-qubit layers as 6-qubit blocks
+        with q.Simulator(n, precision="c64", fusion="greedy", stream=stream, product_passes=False) as sim:
+            t_np = timed(sim, ops, args.steps)
+            no_prod = {"ms": 1e3 * t_np, "passes": sim.stats()["passes"] / (args.warmup + args.steps),
+                       "value": upd / t_np, "what": "greedy 6-qubit blocks only (product_passes=False)"}
+        torch.cuda.empty_cache()
     if w == "adder":
         # the same circuit with dense blocks only (no permutation blocks)
         with q.Simulator(n, precision="c64", fusion="greedy", stream=stream, perm_blocks=False) as sim:
@@ -894,6 +902,8 @@ def run_circuit(args):
            "check": check}
     if no_perm is not None:
         out["dense_blocks_only"] = no_perm
+    if no_prod is not None:
+        out["blocks_only"] = no_prod
     if full_iters:
         out["config"]["extrapolated_full_search_s"] = t_fused * full_iters / iters
     print(json.dumps(out), flush=True)

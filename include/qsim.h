@@ -99,6 +99,10 @@ typedef struct qsim_opts {
     int no_permutation_blocks; /* non-zero: the greedy and learned planners form no
                                permutation blocks (runs of X / CNOT / Toffoli / SWAP
                                executed as one emulated-permutation pass) */
+    int no_product_passes;  /* non-zero: the greedy planner (complex64, n >= 12) forms no
+                               product passes (a layer of one-qubit gates on more than
+                               kmax qubits between wider gates, applied 12 qubits per
+                               pass) */
 } qsim_opts;
 
 /* A Pauli-sum term c * P.  Qubit q of P is X if bit q is set in xmask only,
@@ -268,7 +272,8 @@ int sim_reset_stats(qsim *s);
  * (6-qubit blocks), "block_dense" (blocks on CUDA cores), "block_diag"
  * (diagonal blocks), "permute", "permute_cycles" and "permute_cycles_bulk"
  * (sim_apply_permutation: tiled through shared memory, or along the cycles
- * of f through registers or through the bulk-copy engine). */
+ * of f through registers or through the bulk-copy engine), "product" (layers
+ * of one-qubit gates, 12 qubits per pass). */
 typedef struct qsim_kernel_time {
     char name[24];
     uint64_t launches;

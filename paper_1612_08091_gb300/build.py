@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqsim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "planner.cpp", "gate_kernels.cu", "reduce_kernels.cu", "tmem_block_kernel.cu", "noalloc.cu", "vqe_kernel.cu", "mlp_kernels.cu", "diag_kernels.cu", "perm_kernels.cu", "shard_kernels.cu", "selftest.cu"]
+SOURCES = ["api.cpp", "planner.cpp", "gate_kernels.cu", "reduce_kernels.cu", "tmem_block_kernel.cu", "noalloc.cu", "vqe_kernel.cu", "mlp_kernels.cu", "diag_kernels.cu", "perm_kernels.cu", "shard_kernels.cu", "product_kernel.cu", "selftest.cu"]
 
 
 def _nvcc():

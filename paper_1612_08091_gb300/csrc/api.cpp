@@ -90,7 +90,7 @@ double gate_bytes(const qsim *s, const GateRec &g) {
 
 const char *kClassName[KC_COUNT] = {"gate_dense", "gate_phase", "gate_diag",  "gate_x",  "block_tc",
                                     "block_dense", "block_diag", "block_tc6", "permute", "permute_cycles",
-                                    "permute_cycles_bulk"};
+                                    "permute_cycles_bulk", "product"};
 
 int harvest(qsim *s) {
     if (s->pending.empty()) return QSIM_OK;
@@ -158,8 +158,12 @@ int execute_item(qsim *s, const PlanItem &it) {
     struct Range {
         bool on;
         Range(bool o, const PlanItem &it) : on(o) {
-            if (on) nvtxRangePushA(!it.fused ? "gate" : it.diag_block ? "diag block" : it.perm_block ? "perm block"
-                                                                                            : "dense block");
+            if (on)
+                nvtxRangePushA(!it.fused        ? "gate"
+                               : it.diag_block  ? "diag block"
+                               : it.perm_block  ? "perm block"
+                               : it.prod_block  ? "product"
+                                                : "dense block");
         }
         ~Range() {
             if (on) nvtxRangePop();
@@ -184,6 +188,12 @@ int execute_item(qsim *s, const PlanItem &it) {
         cls = KC_BLOCK_DIAG;
         rc = launch_block_diag(s, it.dmask, it.dtab.data());
         bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n);
+    } else if (it.prod_block) {
+        int npasses = 0;
+        cls = KC_PRODUCT;
+        rc = launch_product(s, it.qmask_prod, it.pm.data(), &npasses);
+        bytes = 2.0 * (double)amp_bytes(s) * std::ldexp(1.0, s->n) * npasses;
+        s->stats.passes += npasses > 0 ? npasses - 1 : 0;  // one is counted below
     } else if (it.perm_block) {
         int qubits[64], m = 0, kind = 0;
         for (int b = 0; b < s->n; ++b)
@@ -266,9 +276,10 @@ int flush(qsim *s) {
     } else {
         // greedy: each block is launched as soon as it is formed, so the
         // host's planning of the next blocks overlaps the device's work
+        const bool prod = s->prod_passes && s->prec == QSIM_C64 && s->n >= 12;
         rc = plan_greedy_each(
             s->queue, s->n, block_kmax(s), [s](PlanItem &it) { return execute_item(s, it); }, kMaxDiagQubits, true,
-            s->perm_blocks ? perm_min_width(s->prec, block_kmax(s)) : 0);
+            s->perm_blocks ? perm_min_width(s->prec, block_kmax(s)) : 0, prod ? block_kmax(s) + 1 : 0);
     }
     s->queue.clear();
     return rc;
@@ -351,6 +362,7 @@ int sim_create(int n, int precision, const qsim_opts *opts, qsim **out) {
     s->norm_tracking = o.no_norm_tracking == 0;
     s->c128_df = o.c128_double_float != 0;
     s->perm_blocks = o.no_permutation_blocks == 0;
+    s->prod_passes = o.no_product_passes == 0;
     s->stream = (cudaStream_t)o.stream;
     if (o.device >= 0) {
         if (cudaSetDevice(o.device) != cudaSuccess) {

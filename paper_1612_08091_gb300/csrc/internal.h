@@ -44,6 +44,9 @@ struct PlanItem {
     bool perm_block = false;  // fused block of permutation gates: amplitudes only move
     uint64_t pmask = 0;       // qubits of a permutation block (up to kMaxPermQubits)
     std::vector<uint64_t> ptab;  // f over the 2^popc(pmask) register values (bit j = j-th qubit of pmask)
+    bool prod_block = false;  // one-qubit gates on many qubits: a product of 2x2 matrices
+    uint64_t qmask_prod = 0;  // its qubits
+    std::vector<cd> pm;       // the 2x2 matrix of each of its qubits (ascending), row-major
     int gate = -1;
     int k = 0;              // fused block width
     int qubits[6] = {0, 0, 0, 0, 0, 0};  // sorted ascending; bit j of the block index
@@ -87,6 +90,7 @@ struct qsim {
     bool norm_tracking = true;  // each block pass scales its outputs back to the norm target
     bool c128_df = false;       // complex128 gates and blocks in double-float arithmetic
     bool perm_blocks = true;    // the planners may form permutation blocks
+    bool prod_passes = true;    // the greedy planner may form product passes (complex64)
     // norm control of the tensor-core block passes (tmem_block_kernel.cu):
     // norm_chain: the previous block pass's record describes the current
     // state (false after a reset, a measurement, host-set amplitudes or a
@@ -116,7 +120,7 @@ struct qsim {
 
 enum KernelClass {
     KC_DENSE = 0, KC_PHASE, KC_DIAG, KC_X, KC_BLOCK_TC, KC_BLOCK_DENSE, KC_BLOCK_DIAG, KC_BLOCK_TC6, KC_PERMUTE,
-    KC_PERMUTE_CYCLES, KC_PERMUTE_BULK, KC_COUNT
+    KC_PERMUTE_CYCLES, KC_PERMUTE_BULK, KC_PRODUCT, KC_COUNT
 };
 static_assert(KC_COUNT <= 16, "class_time holds 16 kernel classes");
 constexpr int kMaxDiagQubits = 12;
@@ -159,6 +163,14 @@ int launch_block_dense(qsim *s, const int *qubits, int k, const cd *m);
 int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, uint64_t qmask, uint64_t cmask,
                        int *kind);
 
+// A product of one-qubit gates on the qubits of qmask (complex64): mats
+// holds each qubit's 2x2 matrix, ascending, row-major; one pass per 12
+// qubits (product_kernel.cu).
+int launch_product(qsim *s, uint64_t qmask, const cd *mats, int *npasses);
+// u = c [[s00, s01], [s10, s11]] with c > 0, real signs s = +-1 and s00 s11
+// = -s01 s10 (products of H and X), to 1e-12 relative: the matrices a
+// product pass takes (planner.cpp)
+bool butterfly2(const cd *u);
 // Diagonal block: psi_i *= d[bits of i on dmask] (diag_kernels.cu).
 int launch_block_diag(qsim *s, uint64_t dmask, const cd *d);
 int launch_set_basis(qsim *s, uint64_t basis);
@@ -190,13 +202,18 @@ void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out)
 // diag_k: widest diagonal block (0 disables diagonal blocks); matrices:
 // build each fused block's matrix or diagonal table (false: members and
 // qubits only, for comparing plans); perm_min: narrowest permutation block
-// worth a pass of its own (0 disables permutation blocks; see perm_min_width)
+// worth a pass of its own (0 disables permutation blocks; see perm_min_width);
+// prod_min: fewest qubits of a product pass (0 disables them): a run of
+// uncontrolled one-qubit gates on at least prod_min qubits, each of whose
+// wires continues with a gate on more than kmax qubits (or ends) and has a
+// butterfly2 matrix (wires whose product is the identity drop out), becomes
+// one product item (only with matrices)
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out,
-                 int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0);
+                 int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0, int prod_min = 0);
 // The same plan handed to emit item by item as it is formed (so execution
 // overlaps planning); a non-zero return of emit stops planning and is returned.
 int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
-                     int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0);
+                     int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0, int prod_min = 0);
 // The narrowest permutation block the executor runs as its own pass:
 // complex128 dense blocks are bound by arithmetic, so any permutation block
 // of two or more gates is cheaper; complex64 dense blocks are HBM-bound like

@@ -15,7 +15,10 @@
 // fits in kmax, and repeats until nothing more fits.  The block's matrix is
 // the ordered product of its gates, each embedded in the block's qubits, in
 // FP64.  Gates on more than kmax qubits (e.g. a many-controlled Z) run alone
-// with their specialised plain kernel.
+// with their specialised plain kernel.  Between such gates, a layer of
+// one-qubit gates on more than kmax qubits (Grover's H and X layers, paper
+// Appendix A) has nothing to fuse with: it becomes a product item, the 2x2
+// product of each wire's gates, executed 12 qubits per pass.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -174,6 +177,24 @@ void block_matrix(const std::vector<GateRec> &q, PlanItem &it) {
     const auto t0 = std::chrono::steady_clock::now();
     if (it.diag_block) {
         it.dtab = diag_table(q, it.members, it.dmask);
+    } else if (it.prod_block) {
+        // per wire (ascending) the ordered product of its one-qubit gates
+        std::vector<int> col(64, -1);
+        int k = 0;
+        for (int b = 0; b < 64; ++b)
+            if ((it.qmask_prod >> b) & 1ull) col[b] = k++;
+        it.pm.assign((size_t)4 * k, cd(0.0, 0.0));
+        for (int j = 0; j < k; ++j) it.pm[4 * j] = it.pm[4 * j + 3] = 1.0;
+        for (int gi : it.members) {
+            const GateRec &g = q[gi];
+            if (col[g.targets[0]] < 0) continue;  // a wire whose product is the identity
+            cd *M = &it.pm[4 * (size_t)col[g.targets[0]]];
+            const cd a = M[0], b = M[1], c = M[2], d = M[3];
+            M[0] = g.m[0] * a + g.m[1] * c;
+            M[1] = g.m[0] * b + g.m[1] * d;
+            M[2] = g.m[2] * a + g.m[3] * c;
+            M[3] = g.m[2] * b + g.m[3] * d;
+        }
     } else if (it.perm_block) {
         it.ptab = perm_table(q, it.members, it.pmask);
     } else {
@@ -186,6 +207,16 @@ void block_matrix(const std::vector<GateRec> &q, PlanItem &it) {
 }
 
 int perm_min_width(int prec, int kmax) { return prec == QSIM_C128 ? 1 : kmax + 1; }
+
+bool butterfly2(const cd *u) {
+    const double c = std::abs(u[0]);
+    if (!(c > 0.0) || !std::isfinite(c)) return false;
+    for (int e = 0; e < 4; ++e)
+        if (std::abs(u[e].imag()) > 1e-12 * c || std::abs(std::abs(u[e].real()) - c) > 1e-12 * c) return false;
+    const double s = (u[0].real() > 0) == (u[3].real() > 0) ? 1.0 : -1.0;  // s00 s11
+    const double t = (u[1].real() > 0) == (u[2].real() > 0) ? 1.0 : -1.0;  // s01 s10
+    return s == -t;
+}
 
 bool perm_map(const GateRec &g, std::vector<uint8_t> &pmap) {
     const int T = 1 << g.t;
@@ -213,7 +244,7 @@ bool perm_map(const GateRec &g, std::vector<uint8_t> &pmap) {
 }
 
 int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
-                     int diag_k, bool matrices, int perm_min) {
+                     int diag_k, bool matrices, int perm_min, int prod_min) {
     const size_t G = q.size();
     if (G == 0) return 0;
     // per-wire gate lists in program order
@@ -349,6 +380,68 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
             }
             for (auto r = dm.rbegin(); r != dm.rend(); ++r) untake(*r);
         }
+        auto one_qubit = [&](int gi) { return q[gi].t == 1 && q[gi].controls.empty(); };
+        if (prod_min > 0 && matrices && one_qubit(seed)) {
+            // a product item: every ready uncontrolled one-qubit gate, wire
+            // by wire in program order, on the wires whose next gate is
+            // wider than kmax (or that end); worth it on prod_min wires
+            std::vector<int> pr;
+            uint64_t P = 0;
+            for (bool again = true; again;) {
+                again = false;
+                for (int b = 0; b < n; ++b)
+                    while (front[b] < wire[b].size() && one_qubit(wire[b][front[b]])) {
+                        const int gi = wire[b][front[b]];
+                        take(gi);
+                        pr.push_back(gi);
+                        P |= 1ull << b;
+                        again = true;
+                    }
+            }
+            for (int b = 0; b < n; ++b) {
+                if (!((P >> b) & 1ull) || front[b] >= wire[b].size()) continue;
+                if (popc(qmask(q[wire[b][front[b]]])) > kmax) continue;
+                // this wire continues into a gate a dense block can take: its
+                // one-qubit gates stay for that block
+                for (auto r = pr.rbegin(); r != pr.rend(); ++r)
+                    if (q[*r].targets[0] == b) untake(*r);
+                pr.erase(std::remove_if(pr.begin(), pr.end(), [&](int gi) { return q[gi].targets[0] == b; }),
+                         pr.end());
+                P &= ~(1ull << b);
+            }
+            if (popc(P) >= prod_min) {
+                PlanItem it;
+                it.fused = true;
+                it.prod_block = true;
+                it.qmask_prod = P;
+                it.ngates = (int)pr.size();
+                it.members = pr;
+                it.amp_updates = (double)pr.size() * (double)(1ull << n);
+                block_matrix(q, it);
+                // the pass takes butterfly matrices only; identity wires drop out
+                uint64_t keep = 0;
+                bool ok = true;
+                for (int b = 0, k = 0; b < n; ++b) {
+                    if (!((P >> b) & 1ull)) continue;
+                    const cd *M = &it.pm[4 * (size_t)k++];
+                    const bool ident = std::abs(M[0] - 1.0) <= 1e-12 && std::abs(M[1]) <= 1e-12 &&
+                                       std::abs(M[2]) <= 1e-12 && std::abs(M[3] - 1.0) <= 1e-12;
+                    if (butterfly2(M))
+                        keep |= 1ull << b;
+                    else if (!ident)
+                        ok = false;
+                }
+                if (ok && popc(keep) >= prod_min) {
+                    if (keep != P) {
+                        it.qmask_prod = keep;
+                        block_matrix(q, it);
+                    }
+                    if (const int rc = emit(it)) return rc;
+                    continue;
+                }
+            }
+            for (auto r = pr.rbegin(); r != pr.rend(); ++r) untake(*r);
+        }
         if (popc(qmask(q[seed])) > kmax) {
             PlanItem it;
             it.fused = false;
@@ -422,7 +515,7 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
 }
 
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out, int diag_k,
-                 bool matrices, int perm_min) {
+                 bool matrices, int perm_min, int prod_min) {
     out.clear();
     plan_greedy_each(
         q, n, kmax,
@@ -430,7 +523,7 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
             out.push_back(std::move(it));
             return 0;
         },
-        diag_k, matrices, perm_min);
+        diag_k, matrices, perm_min, prod_min);
 }
 
 // ---------------------------------------------------------------------------
@@ -458,6 +551,11 @@ void item_features(const PlanItem &it, const std::vector<GateRec> &q, int n, int
         f[5] = it.ngates / 32.f;
         f[8] = 1.f;
         mask = it.dmask;
+    } else if (it.fused && it.prod_block) {
+        f[2] = 1.f;
+        f[4] = __builtin_popcountll(it.qmask_prod) / 5.f;
+        f[5] = it.ngates / 32.f;
+        mask = it.qmask_prod;
     } else if (it.fused && it.perm_block) {
         f[2] = 1.f;
         f[4] = it.k / 5.f;

@@ -40,7 +40,8 @@ class Opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("fusion", ctypes.c_int), ("kmax", ctypes.c_int),
                 ("device", ctypes.c_int), ("tc_terms", ctypes.c_int), ("no_tensor_cores", ctypes.c_int),
                 ("no_norm_tracking", ctypes.c_int), ("c128_double_float", ctypes.c_int),
-                ("no_permutation_blocks", ctypes.c_int)]
+                ("no_permutation_blocks", ctypes.c_int),
+                ("no_product_passes", ctypes.c_int)]
 
 
 class Pauli(ctypes.Structure):
@@ -134,7 +135,8 @@ class Simulator:
     """An n-qubit register on the GPU behind the libqsim C ABI."""
 
     def __init__(self, n, precision="c128", fusion="none", kmax=6, device=None, stream=None, torch_memory=True,
-                 tc_terms=3, tensor_cores=True, norm_tracking=True, c128_df=False, perm_blocks=True):
+                 tc_terms=3, tensor_cores=True, norm_tracking=True, c128_df=False, perm_blocks=True,
+                 product_passes=True):
         import torch
 
         if not torch.cuda.is_available():
@@ -154,6 +156,7 @@ class Simulator:
         opts.no_norm_tracking = 0 if norm_tracking else 1
         opts.c128_double_float = 1 if c128_df else 0
         opts.no_permutation_blocks = 0 if perm_blocks else 1
+        opts.no_product_passes = 0 if product_passes else 1
         self._keep = []
         if torch_memory:
             ws = ctypes.c_size_t()

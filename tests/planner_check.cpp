@@ -14,6 +14,13 @@
 //     program order on every qubit; a permutation block holds only
 //     permutation gates on at most 12 qubits, is at least perm_min wide, and
 //     its table is the permutation of the embedded matrix product.
+//  4. product items on circuits of one-qubit layers (H and X on each wire,
+//     sometimes a general gate) between wide multi-controlled gates: every
+//     gate once, in program order on every qubit; a product item holds only
+//     uncontrolled one-qubit gates on at least prod_min qubits, each of its
+//     wires continues with a gate wider than kmax (or ends), its matrix of
+//     each wire is the ordered product of that wire's member gates and is
+//     c times a +-1 matrix with orthogonal rows (M M^T = 2 c^2 I).
 #include <algorithm>
 #include <cstdio>
 #include <random>
@@ -311,11 +318,147 @@ int check_perm_plans() {
     return bad == 0 && blocks > 0 ? 0 : 1;
 }
 
+GateRec h_gate(int b) {
+    GateRec g;
+    g.t = 1;
+    g.targets[0] = b;
+    g.tmask = 1ull << b;
+    const double h = std::sqrt(0.5);
+    g.m = {h, h, h, -h};
+    g.kind = GK_DENSE;
+    g.perm = perm_map(g, g.pmap);
+    return g;
+}
+
+GateRec x_gate(int b) {
+    GateRec g;
+    g.t = 1;
+    g.targets[0] = b;
+    g.tmask = 1ull << b;
+    g.m = {0.0, 1.0, 1.0, 0.0};
+    g.kind = GK_X;
+    g.perm = perm_map(g, g.pmap);
+    return g;
+}
+
+int check_product_plans() {
+    int bad = 0, items = 0;
+    for (int trial = 0; trial < 60; ++trial) {
+        const int n = 10 + trial % 7, kmax = 2 + trial % 5, prod_min = kmax + 1;
+        std::vector<int> all(n);
+        for (int i = 0; i < n; ++i) all[i] = i;
+        std::vector<GateRec> q;
+        for (int layer = 0; layer < 8; ++layer) {
+            const int r = (int)(rng() % 4);
+            if (r == 0) {
+                // a gate on every qubit: one target, all others as controls
+                std::shuffle(all.begin(), all.end(), rng);
+                GateRec g = random_gate(std::vector<int>(all.begin(), all.begin() + 1), (int)(rng() % 3));
+                for (int j = 1; j < n; ++j) {
+                    g.controls.push_back(all[j]);
+                    g.cmask |= 1ull << all[j];
+                }
+                q.push_back(g);
+            } else if (r == 3) {
+                // a two-qubit gate a dense block can take
+                std::shuffle(all.begin(), all.end(), rng);
+                q.push_back(random_gate(std::vector<int>(all.begin(), all.begin() + 2), 0));
+            } else {
+                // one-qubit gates on a random subset of the wires: an H with
+                // X before and after at random, and in one layer of six a
+                // general gate on one wire
+                const bool general = rng() % 6 == 0;
+                for (int b = 0; b < n; ++b) {
+                    if (rng() % 4 == 0) continue;
+                    if (rng() % 2) q.push_back(x_gate(b));
+                    q.push_back(general && b == 0 ? random_gate(std::vector<int>{b}, 0) : h_gate(b));
+                    if (rng() % 2) q.push_back(x_gate(b));
+                }
+            }
+        }
+        const int G = (int)q.size();
+        std::vector<PlanItem> plan;
+        plan_greedy(q, n, kmax, plan, kMaxDiagQubits, true, 0, prod_min);
+        std::vector<int> order, seen(G, 0);
+        for (const PlanItem &it : plan)
+            for (int gi : it.members) {
+                order.push_back(gi);
+                seen[gi]++;
+            }
+        for (int gi = 0; gi < G; ++gi)
+            if (seen[gi] != 1) ++bad;
+        std::vector<int> at(G);
+        for (size_t i = 0; i < order.size(); ++i) at[order[i]] = (int)i;
+        for (int a = 0; a < G; ++a)
+            for (int b = a + 1; b < G; ++b)
+                if (((q[a].tmask | q[a].cmask) & (q[b].tmask | q[b].cmask)) && at[a] > at[b]) {
+                    bool both_diag_same_block = false;
+                    for (const PlanItem &it : plan)
+                        if (it.diag_block && std::count(it.members.begin(), it.members.end(), a) &&
+                            std::count(it.members.begin(), it.members.end(), b))
+                            both_diag_same_block = true;
+                    if (!both_diag_same_block) ++bad;
+                }
+        for (const PlanItem &it : plan) {
+            if (!it.prod_block) continue;
+            ++items;
+            if (__builtin_popcountll(it.qmask_prod) < prod_min) ++bad;
+            std::vector<int> wires;
+            for (int b = 0; b < n; ++b)
+                if ((it.qmask_prod >> b) & 1ull) wires.push_back(b);
+            if (it.pm.size() != 4 * wires.size()) {
+                ++bad;
+                continue;
+            }
+            // members on a wire outside the item: their product is the identity
+            for (int b = 0; b < n; ++b) {
+                if ((it.qmask_prod >> b) & 1ull) continue;
+                std::vector<cd> ref = {1.0, 0.0, 0.0, 1.0};
+                for (int gi : it.members)
+                    if (q[gi].targets[0] == b) ref = matmul(q[gi].m, ref, 2);
+                if (std::abs(ref[0] - 1.0) > 1e-12 || std::abs(ref[1]) > 1e-12 || std::abs(ref[2]) > 1e-12 ||
+                    std::abs(ref[3] - 1.0) > 1e-12)
+                    ++bad;
+            }
+            for (int gi : it.members)
+                if (q[gi].t != 1 || !q[gi].controls.empty()) ++bad;
+            for (size_t w = 0; w < wires.size(); ++w) {
+                const int b = wires[w];
+                std::vector<cd> ref = {1.0, 0.0, 0.0, 1.0};
+                int last = -1;
+                for (int gi : it.members) {
+                    const GateRec &g = q[gi];
+                    if (g.targets[0] != b) continue;
+                    ref = matmul(g.m, ref, 2);
+                    last = std::max(last, gi);
+                }
+                for (int e = 0; e < 4; ++e)
+                    if (std::abs(it.pm[4 * w + e] - ref[e]) > 1e-12) ++bad;
+                // c times a +-1 matrix with orthogonal rows
+                const cd *M = &it.pm[4 * w];
+                const double c = std::abs(M[0]);
+                for (int e = 0; e < 4; ++e)
+                    if (std::abs(M[e].imag()) > 1e-12 || std::abs(std::abs(M[e].real()) - c) > 1e-12) ++bad;
+                if (std::abs(M[0].real() * M[2].real() + M[1].real() * M[3].real()) > 1e-12) ++bad;
+                // the wire's next gate after the item is wider than kmax, or none
+                for (int gi = last + 1; gi < G; ++gi)
+                    if (((q[gi].tmask | q[gi].cmask) >> b) & 1ull) {
+                        if (__builtin_popcountll(q[gi].tmask | q[gi].cmask) <= kmax) ++bad;
+                        break;
+                    }
+            }
+        }
+    }
+    printf("product items: %d items, %d violations over 60 random circuits\n", items, bad);
+    return bad == 0 && items > 0 ? 0 : 1;
+}
+
 }  // namespace
 
 int main() {
     const int a = check_block_matrix();
     const int b = check_plans();
     const int c = check_perm_plans();
-    return a | b | c;
+    const int d = check_product_plans();
+    return a | b | c | d;
 }

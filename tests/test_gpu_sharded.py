@@ -77,11 +77,12 @@ def test_sharded_register_against_oracle(qs, oracle_mod, g, prec, fusion):
         sim.run(ops[:n])
         oracle_mod.run_ops(ref, ops[:n])
         u = 0.5772156649
+        c = np.cumsum(np.abs(ref.psi) ** 2)  # before the oracle's collapse
         j = sim.measure_all(u)
         jr = ref.measure_all(u)
         if j != jr:
-            psi = sim.get_amplitudes()
-            c = np.cumsum(np.abs(ref.psi) ** 2)
+            # neighbouring outcomes where u * norm lies on their boundary
+            assert abs(j - jr) == 1, (j, jr)
             assert abs(c[min(j, jr)] - u * c[-1]) < (1e-12 if prec == "c128" else 1e-6)
         after = sim.get_amplitudes()
         assert abs(abs(after[j]) - 1.0) <= tol and np.count_nonzero(after) == 1
