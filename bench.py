@@ -827,10 +827,26 @@ def run_circuit(args):
             ts.append(e0.elapsed_time(e1) / 1e3)
         return statistics.median(ts[args.warmup:])
 
+    classes = None
     with q.Simulator(n, precision="c64", fusion="greedy", stream=stream) as sim:
         t_fused = timed(sim, ops, args.steps)
         # the register holds the last timed run's result; passes per run
         passes = sim.stats()["passes"] / (args.warmup + args.steps)
+        if t_fused < 10.0:
+            # one more run with events around every launch: time and HBM
+            # bandwidth (algorithmic bytes) per kernel class
+            peak, _ = measured_peaks()
+            sim.reset(basis)
+            sim.set_profiling(True)
+            sim.run(ops)
+            sim.flush()
+            kt = sim.kernel_times()
+            sim.set_profiling(False)
+            classes = {k: {"launches": v["launches"], "ms": v["total_ms"],
+                           "GB/s": v["alg_bytes"] / v["total_ms"] / 1e6 if v["total_ms"] else None,
+                           "frac": v["alg_bytes"] / v["total_ms"] / 1e6 / peak if v["total_ms"] else None}
+                       for k, v in kt.items()}
+            # the register again holds the circuit's result for the checks below
         check = {}
         if w == "qft":
             rng = np.random.default_rng(SEED + 1)
@@ -904,6 +920,8 @@ def run_circuit(args):
         out["dense_blocks_only"] = no_perm
     if no_prod is not None:
         out["blocks_only"] = no_prod
+    if classes is not None:
+        out["classes"] = classes
     if full_iters:
         out["config"]["extrapolated_full_search_s"] = t_fused * full_iters / iters
     print(json.dumps(out), flush=True)
