@@ -22,21 +22,23 @@
 // tensor-core blocks.)
 //
 // A tile is 32 KB of shared memory, double-buffered: the next tile arrives
-// by 8-byte cp.async copies while this one is processed (64 KB per CTA,
-// three CTAs per SM).  256 threads hold 16 amplitudes each in three layouts
+// by 16-byte cp.async copies (two amplitudes, bypassing L1) while this one
+// is processed (64 KB per CTA, three CTAs per SM).  256 threads hold 16 amplitudes each in three layouts
 // (tile index e, bits 0..11):
 //   A  e = i | tid << 4:                              registers = tile bits 0..3
 //   B  e = (tid & 15) | i << 4 | (tid >> 4) << 8:     registers = tile bits 4..7
 //   C  e = tid | i << 8:                              registers = tile bits 8..11
-// The copies and the stores (layout C) put the lanes on tile bits 0..4
-// (address bits 0..3 plus one more: 128-byte runs at least).  Element e sits
-// at shared position e ^ ((e >> 4) & 15): bits 0..3 (the 8-byte bank pair)
-// XOR bits 4..7, so the copies and each layout meet 16 different bank pairs
-// per half-warp.  (A padded layout, rows of 16 with a pitch of 17, needs
-// no address arithmetic per access but measured 5 % slower: 68 KB per CTA
-// leave less L1 for the copies.)  The global addresses of a thread's 16
-// copies and stores step through tile bits 8..11 in Gray-code order, one
-// 64-bit add each.
+// The copies (e = 2 tid + i << 9, 16 bytes each) and the stores (layout C)
+// put the lanes on the lowest tile bits (address bits 0..3 and more:
+// 128-byte runs at least).  Element e sits at shared position
+// e ^ ((e >> 4) & 7) << 1: bits 1..3 XOR bits 4..6, bit 0 kept, so an
+// amplitude pair stays one aligned 16-byte slot; the 16-byte copies and
+// layout-A accesses meet 8 different slots per quarter-warp and the 8-byte
+// accesses of layouts B and C 16 different bank pairs per half-warp.  (A
+// padded layout, rows of 16 with a pitch of 17, needs no address
+// arithmetic per access but measured 5 % slower.)  The global addresses of
+// a thread's copies and stores step through the register bits in Gray-code
+// order, one 64-bit add each.
 //
 // Norm control.  A product pass is one step of the same norm chain as the
 // tensor-core block passes (tmem_block_kernel.cu): its inputs' and outputs'
@@ -88,7 +90,7 @@ struct ProdArgs {
 };
 
 // shared-memory position of tile element e
-__device__ __forceinline__ uint32_t swz(uint32_t e) { return e ^ ((e >> 4) & 15u); }
+__device__ __forceinline__ uint32_t swz(uint32_t e) { return e ^ (((e >> 4) & 7u) << 1); }
 
 // Gray code of step k and the bit it changes from step k - 1
 __host__ __device__ constexpr int gray(int k) { return k ^ (k >> 1); }
@@ -127,9 +129,10 @@ __device__ __forceinline__ void stage(float2 (&v)[kPPer], const ProdArgs &A, int
     }
 }
 
-// 8-byte asynchronous copy global -> shared (no register staging)
-__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+// 16-byte asynchronous copy global -> shared (no register staging, not
+// cached in L1)
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
                  "l"(gsrc)
                  : "memory");
 }
@@ -175,7 +178,8 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
     }
     __syncthreads();
     const float out_scale = s_scale * A.cs;  // every output, before its sign
-    const uint64_t off_lo = addr((uint32_t)tid);  // tile bits 0..7 of this thread (copies and stores)
+    const uint64_t off_lo = addr((uint32_t)tid);          // tile bits 0..7 of this thread (stores)
+    const uint64_t off_cp = addr((uint32_t)tid << 1);     // tile bits 1..8 of this thread's copies
     const uint32_t gA = A.gmask & 15u, gB = (A.gmask >> 4) & 15u, gC = (A.gmask >> 8) & 15u;
     // sign of output i (layout C, e = tid | i << 8) in bit i
     uint32_t sgn = 0;
@@ -189,17 +193,22 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
     uint64_t hb[kPRegBits];
 #pragma unroll
     for (int r = 0; r < kPRegBits; ++r) hb[r] = 1ull << A.vspec.pos[8 + r];
+    // tile bits 9..11: the register index of the copies
+    uint64_t cb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) cb[r] = 1ull << A.vspec.pos[9 + r];
     // layouts A (e = i | tid << 4) and B; C and the copies: e = tid | i << 8
     const uint32_t eA = (uint32_t)tid << 4, eB = ((uint32_t)tid & 15u) | (((uint32_t)tid >> 4) << 8);
-    // copies of the tile at `base`: element e = tid | k << 8, k in Gray order
+    // copies of the tile at `base`: elements e, e + 1 with e = 2 tid + k << 9,
+    // k in Gray order
     auto copy_in = [&](uint64_t base, int buf) {
-        const float2 *p = A.psi + base + off_lo;
+        const float2 *p = A.psi + base + off_cp;
         float2 *d = smd + buf * kPTile;
 #pragma unroll
-        for (int k = 0; k < kPPer; ++k) {
+        for (int k = 0; k < kPPer / 2; ++k) {
             const int g = gray(k), b = gray_bit(k);
-            if (b >= 0) p = (gray(k - 1) >> b) & 1 ? p - hb[b] : p + hb[b];
-            cp_async8(d + swz((uint32_t)tid | ((uint32_t)g << 8)), p);
+            if (b >= 0) p = (gray(k - 1) >> b) & 1 ? p - cb[b] : p + cb[b];
+            cp_async16(d + swz(((uint32_t)tid << 1) | ((uint32_t)g << 9)), p);
         }
     };
     double nin = 0.0, nout = 0.0;
@@ -219,7 +228,11 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
         // layout A: input sums, butterflies of tile bits 0..3
         {
 #pragma unroll
-            for (int i = 0; i < kPPer; ++i) v[i] = x[swz(eA | (uint32_t)i)];
+            for (int j = 0; j < kPPer / 2; ++j) {
+                const float4 w = *(const float4 *)(x + swz(eA | 2u * (uint32_t)j));
+                v[2 * j] = make_float2(w.x, w.y);
+                v[2 * j + 1] = make_float2(w.z, w.w);
+            }
             float q[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < kPPer; ++i) q[i & 3] = fmaf(v[i].x, v[i].x, fmaf(v[i].y, v[i].y, q[i & 3]));
@@ -227,7 +240,9 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
             if (gA) {
                 stage(v, A, 0, gA);
 #pragma unroll
-                for (int i = 0; i < kPPer; ++i) x[swz(eA | (uint32_t)i)] = v[i];
+                for (int j = 0; j < kPPer / 2; ++j)
+                    *(float4 *)(x + swz(eA | 2u * (uint32_t)j)) =
+                        make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
             }
             __syncthreads();
         }
