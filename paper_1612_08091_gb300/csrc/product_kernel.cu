@@ -137,8 +137,8 @@ __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// all but this thread's most recent group of copies complete
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// all of this thread's copies complete
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdArgs A) {
     extern __shared__ __align__(16) float2 smd[];  // two tiles of 2^12 amplitudes, padded rows
@@ -217,12 +217,14 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
     if (t < A.ntiles) copy_in(base, 0);
     cp_async_commit();
     for (int it = 0; t < A.ntiles; t += gridDim.x, ++it) {
+        cp_async_wait_all();
+        // every thread's copies of tile t have landed, and every thread is
+        // done with iteration it - 1, whose buffer the next copies refill
+        __syncthreads();
         const uint64_t tn = t + gridDim.x;
         const uint64_t base_n = tn < A.ntiles ? tile_base(tn, A) : 0;
         if (tn < A.ntiles) copy_in(base_n, (it + 1) & 1);  // in flight during this tile's stages
         cp_async_commit();
-        cp_async_wait_prev();
-        __syncthreads();  // every thread's copies of tile t have landed
         float2 *x = smd + (it & 1) * kPTile;
         float2 v[kPPer];
         // layout A: input sums, butterflies of tile bits 0..3
@@ -273,7 +275,6 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
             }
             nout += (double)((q[0] + q[1]) + (q[2] + q[3]));
         }
-        __syncthreads();  // buffer it & 1 is free for the copies of iteration it + 1
         base = base_n;
     }
     // per-CTA sums, fixed order; the outputs' sum before the chain's scale
