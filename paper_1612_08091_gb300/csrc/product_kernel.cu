@@ -41,11 +41,11 @@
 // order, one 64-bit add each.
 //
 // Norm control.  A product pass is one step of the same norm chain as the
-// tensor-core block passes (tmem_block_kernel.cu): its inputs' and outputs'
-// sums of |x|^2 per CTA in FP64 and the scale s' = sqrt(T / (s^2 b * b / a))
-// from the previous pass's record.  C is rounded to FP32 (2^(-k/2) for k
-// gates, exact only for even k) and the FP32 additions round; the control
-// returns the norm to its target after every pass.
+// tensor-core block passes (norm_chain.cuh): its inputs' and outputs' sums
+// of |x|^2 per CTA in FP64 and the scale from the previous pass's record.
+// C is rounded to FP32 (2^(-k/2) for k gates, exact only for even k) and the
+// FP32 additions round; the control returns the norm to its target after
+// every pass.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -53,6 +53,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "norm_chain.cuh"
 
 using namespace qsim_dev;
 
@@ -78,15 +79,7 @@ struct ProdArgs {
     uint32_t fmask;           // F: tile bits whose s10 differs from s00
     float p[kPBits];          // p = s00 s01 of tile bit j
     float cs;                 // C sigma
-    // norm control (see the header comment): this pass's per-CTA sums and
-    // record, the previous pass's; both null start a chain with scale 1 and
-    // target `target` (<= 0: this pass's input norm)
-    double *norm_out;
-    double *rec_out;
-    const double *norm_prev;
-    const double *rec_prev;
-    double target;
-    int prev_grid;
+    qsim_chain::ChainArgs chain;  // norm control (norm_chain.cuh)
 };
 
 // shared-memory position of tile element e
@@ -153,29 +146,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
             if ((e >> j) & 1u) a |= 1ull << A.vspec.pos[j];
         return a;
     };
-    if (tid == 0) {
-        // output scale from the previous pass's sums, the block kernels' rule
-        float sc = 1.0f;
-        double T = A.target;
-        if (A.norm_prev) {
-            double a = 0.0, b = 0.0;
-            for (int i = 0; i < A.prev_grid; ++i) {
-                a += A.norm_prev[i];
-                b += A.norm_prev[kMaxTcGrid + i];
-            }
-            const double sp = A.rec_prev[0], tp = A.rec_prev[1];
-            T = tp > 0.0 ? tp : a;
-            if (T > 0.0 && a > 0.0 && b > 0.0 && sp > 0.0 && a < 1e300 && b < 1e300 && T < 1e300) {
-                const double s2 = (T / (sp * sp * b)) * (a / b);
-                if (s2 > 0.25 && s2 < 4.0) sc = (float)sqrt(s2);
-            }
-        }
-        s_scale = sc;
-        if (blockIdx.x == 0 && A.rec_out) {
-            A.rec_out[0] = (double)sc;
-            A.rec_out[1] = T;
-        }
-    }
+    if (tid == 0) s_scale = qsim_chain::chain_scale(A.chain);  // and the record
     __syncthreads();
     const float out_scale = s_scale * A.cs;  // every output, before its sign
     const uint64_t off_lo = addr((uint32_t)tid);          // tile bits 0..7 of this thread (stores)
@@ -285,14 +256,13 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdAr
         s_red[warp][1] = nout;
     }
     __syncthreads();
-    if (tid == 0 && A.norm_out) {
+    if (tid == 0) {
         double a = 0.0, b = 0.0;
         for (int w = 0; w < kPThreads / 32; ++w) {
             a += s_red[w][0];
             b += s_red[w][1];
         }
-        A.norm_out[blockIdx.x] = a;
-        A.norm_out[kMaxTcGrid + blockIdx.x] = b * (double)A.cs * (double)A.cs;
+        qsim_chain::chain_sums(A.chain, a, b * (double)A.cs * (double)A.cs);
     }
 }
 
@@ -335,17 +305,7 @@ int launch_pass(qsim *s, const int *qubits, const cd *const *mats, int m) {
     uint64_t cap = (uint64_t)s->sms * kPCtasPerSm;
     if (cap > (uint64_t)kMaxTcGrid) cap = kMaxTcGrid;
     const uint64_t grid = a.ntiles < cap ? a.ntiles : cap;
-    // norm chain, shared with the block passes: sums in slot (pass & 1)
-    double *slots = (double *)((char *)s->ws + kWsNorm);
-    double *recs = slots + 4 * kMaxTcGrid;
-    const int slot = (int)(s->tc_passes & 1);
-    const bool chain = s->norm_tracking && s->norm_chain;
-    a.norm_out = slots + slot * 2 * kMaxTcGrid;
-    a.rec_out = recs + 2 * slot;
-    a.norm_prev = chain ? slots + (slot ^ 1) * 2 * kMaxTcGrid : nullptr;
-    a.rec_prev = chain ? recs + 2 * (slot ^ 1) : nullptr;
-    a.target = s->norm_target;
-    a.prev_grid = s->tc_prev_grid;
+    a.chain = qsim_chain::chain_next(s);  // the norm chain of the block passes
     static bool attr_set[64] = {false};
     if (s->device < 0 || s->device >= 64) return QSIM_ENOTSUP;
     if (!attr_set[s->device]) {
@@ -355,9 +315,7 @@ int launch_pass(qsim *s, const int *qubits, const cd *const *mats, int m) {
     }
     k_product<<<(unsigned)grid, kPThreads, kPSmem, s->stream>>>(a);
     s->stats.launches++;
-    s->tc_passes++;
-    s->tc_prev_grid = (int)grid;
-    s->norm_chain = true;
+    qsim_chain::chain_advance(s, (int)grid);
     return cuda_err(s, cudaGetLastError(), "product pass launch");
 }
 

@@ -49,19 +49,12 @@
 // Norm control.  The bf16 split and the FP32 accumulation shrink the norm by
 // a few 1e-7 per pass, and the shrink is systematic on structured states
 // (Grover's search repeats the same blocks on a state whose amplitudes are
-// mostly equal), so uncorrected it adds up over 1e5 passes.  Every pass
-// writes per-CTA FP64 sums of |x|^2 over its inputs (a) and of |y|^2 over its
-// raw outputs (b), and CTA 0 records the scale s it applied and the norm
-// target T.  The next pass knows the norm the previous one left, s^2 b, and
-// its shrink ratio b / a; assuming the same ratio, it scales its outputs by
-//     s' = sqrt(T / (s^2 b * b / a)),
-// which brings the norm back to T after every pass.  Errors therefore do
-// not accumulate: what remains is one pass's change of shrink ratio and the
-// drift of the non-tensor-core passes since the previous block pass, both
-// corrected by the pass after.  T is 1 after a reset or a measurement and the
-// input norm of the first pass otherwise (host-set amplitudes, a
-// non-unitary gate); the host starts a new chain (no previous record, scale
-// 1) at each such point.
+// mostly equal), so uncorrected it adds up over 1e5 passes.  Each pass is a
+// step of the norm chain of norm_chain.cuh: from the previous pass's input
+// and output sums it scales its outputs so that the norm returns to the
+// chain's target.  Errors therefore do not accumulate: what remains is one
+// pass's change of shrink ratio and the drift of the passes outside the
+// chain since the previous one, both corrected by the pass after.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -71,6 +64,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "norm_chain.cuh"
 #include "tc_common.cuh"
 
 using namespace qsim_dev;
@@ -102,18 +96,7 @@ struct TmArgs {
     uint64_t ntiles;           // 2^(n - K - 7)
     InsertSpec vspec;          // the K + 7 positions of V = S u F, ascending
     unsigned int *err;         // error flag
-    // norm control: this pass writes per-CTA sums of |x|^2 (inputs) and
-    // |y|^2 (raw outputs) to norm_out[0..grid) and [kMaxTcGrid..), and CTA 0
-    // writes {scale applied, target} to rec_out; the previous block pass's
-    // sums (norm_prev, prev_grid CTAs) and record (rec_prev) give this
-    // pass's scale; both null start a chain with scale 1 and target
-    // `target` (<= 0: this pass's own input norm)
-    double *norm_out;
-    double *rec_out;
-    const double *norm_prev;
-    const double *rec_prev;
-    double target;
-    int prev_grid;
+    qsim_chain::ChainArgs chain;  // norm control (norm_chain.cuh)
     int fpos[7];               // tile column bit j <-> qubit fpos[j]
     uint64_t rdep[64];         // address bits of block row r
     uint64_t qoff[4];          // W = 16: address bits of column 4q + i relative to column 4q
@@ -176,30 +159,8 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // output scale from the previous pass's sums (fixed summation order,
-        // so every CTA computes the same value) and record
-        float sc = 1.0f;
-        double T = args.target;
-        if (args.norm_prev) {
-            double a = 0.0, b = 0.0;
-            for (int i = 0; i < args.prev_grid; ++i) {
-                a += args.norm_prev[i];
-                b += args.norm_prev[kMaxTcGrid + i];
-            }
-            const double sp = args.rec_prev[0], tp = args.rec_prev[1];
-            T = tp > 0.0 ? tp : a;
-            if (T > 0.0 && a > 0.0 && b > 0.0 && sp > 0.0 && a < 1e300 && b < 1e300 && T < 1e300) {
-                const double s2 = (T / (sp * sp * b)) * (a / b);
-                // a correction this large means the chain was not restarted
-                // where the norm changed; leave the pass unscaled
-                if (s2 > 0.25 && s2 < 4.0) sc = (float)sqrt(s2);
-            }
-        }
-        *s_scale = sc;
-        if (blockIdx.x == 0 && args.rec_out) {
-            args.rec_out[0] = (double)sc;
-            args.rec_out[1] = T;
-        }
+        // output scale from the previous pass's sums, and record
+        *s_scale = qsim_chain::chain_scale(args.chain);
     }
     __syncthreads();
     if (tid == 0) bulk_load(B, args.rec, args.rec_bytes, &bars[0]);
@@ -423,10 +384,9 @@ __global__ void __launch_bounds__(kTmThreads, TmShape<K>::kCtasPerSm) k_block_tm
     }
     tc_fence_before();
     __syncthreads();
-    if (tid == 0 && args.norm_out) {
-        args.norm_out[blockIdx.x] = s_red[0] + s_red[2] + s_red[4] + s_red[6];
-        args.norm_out[kMaxTcGrid + blockIdx.x] = s_red[1] + s_red[3] + s_red[5] + s_red[7];
-    }
+    if (tid == 0)
+        qsim_chain::chain_sums(args.chain, s_red[0] + s_red[2] + s_red[4] + s_red[6],
+                               s_red[1] + s_red[3] + s_red[5] + s_red[7]);
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::kCols) : "memory");
@@ -544,22 +504,10 @@ int launch_tmem(qsim *s, const int *qubits, const cd *m) {
     uint64_t cap = (uint64_t)s->sms * Sh::kCtasPerSm;
     if (cap > (uint64_t)kMaxTcGrid) cap = kMaxTcGrid;
     const uint64_t grid = a.ntiles < cap ? a.ntiles : cap;
-    // norm control: sums in slot (pass & 1), records after both slots
-    double *slots = (double *)((char *)s->ws + kWsNorm);
-    double *recs = slots + 4 * kMaxTcGrid;
-    const int slot = (int)(s->tc_passes & 1);
-    const bool chain = s->norm_tracking && s->norm_chain;
-    a.norm_out = slots + slot * 2 * kMaxTcGrid;
-    a.rec_out = recs + 2 * slot;
-    a.norm_prev = chain ? slots + (slot ^ 1) * 2 * kMaxTcGrid : nullptr;
-    a.rec_prev = chain ? recs + 2 * (slot ^ 1) : nullptr;
-    a.target = s->norm_target;
-    a.prev_grid = s->tc_prev_grid;
+    a.chain = qsim_chain::chain_next(s);
     kernel<<<(unsigned)grid, kTmThreads, smem, s->stream>>>(a);
     s->stats.launches++;
-    s->tc_passes++;
-    s->tc_prev_grid = (int)grid;
-    s->norm_chain = true;
+    qsim_chain::chain_advance(s, (int)grid);
     return cuda_err(s, cudaGetLastError(), "tmem block launch");
 }
 
