@@ -450,6 +450,76 @@ int check_product_plans() {
         }
     }
     printf("product items: %d items, %d violations over 60 random circuits\n", items, bad);
+    // Grover's search (3 iterations on 20 qubits): the first H layer and
+    // every layer between two many-controlled Z are product items; a U3 +
+    // CNOT brickwork (every wire continues into a CNOT) forms none
+    {
+        const int n = 20;
+        const uint64_t marked = 0x5a5a5ull;
+        std::vector<GateRec> q;
+        auto mcz = [&]() {
+            GateRec g;
+            g.t = 1;
+            g.targets[0] = n - 1;
+            g.tmask = 1ull << (n - 1);
+            g.m = {1.0, 0.0, 0.0, -1.0};
+            g.kind = GK_DIAG1;
+            g.diag = true;
+            for (int c = 0; c < n - 1; ++c) {
+                g.controls.push_back(c);
+                g.cmask |= 1ull << c;
+            }
+            g.perm = perm_map(g, g.pmap);
+            return g;
+        };
+        for (int b = 0; b < n; ++b) q.push_back(h_gate(b));
+        for (int it = 0; it < 3; ++it) {
+            for (int b = 0; b < n; ++b)
+                if (!((marked >> b) & 1)) q.push_back(x_gate(b));
+            q.push_back(mcz());
+            for (int b = 0; b < n; ++b)
+                if (!((marked >> b) & 1)) q.push_back(x_gate(b));
+            for (int b = 0; b < n; ++b) q.push_back(h_gate(b));
+            for (int b = 0; b < n; ++b) q.push_back(x_gate(b));
+            q.push_back(mcz());
+            for (int b = 0; b < n; ++b) q.push_back(x_gate(b));
+            for (int b = 0; b < n; ++b) q.push_back(h_gate(b));
+        }
+        std::vector<PlanItem> plan;
+        plan_greedy(q, n, 6, plan, kMaxDiagQubits, true, perm_min_width(QSIM_C64, 6), 7);
+        int prod = 0, plain = 0;
+        for (const PlanItem &it : plan) {
+            if (it.prod_block && __builtin_popcountll(it.qmask_prod) == n) ++prod;
+            if (!it.fused) ++plain;
+        }
+        const bool grover_ok = prod == 7 && plain == 6 && plan.size() == 13;
+        std::vector<GateRec> bw;
+        for (int l = 0; l < 10; ++l) {
+            for (int b = 0; b < n; ++b) {
+                GateRec g = random_gate(std::vector<int>{b}, 0);
+                g.controls.clear();
+                g.cmask = 0;
+                bw.push_back(g);
+            }
+            for (int b = l % 2; b + 1 < n; b += 2) {
+                GateRec g = x_gate(b + 1);
+                g.controls.push_back(b);
+                g.cmask = 1ull << b;
+                g.perm = perm_map(g, g.pmap);
+                bw.push_back(g);
+            }
+        }
+        std::vector<PlanItem> pbw, pbw0;
+        plan_greedy(bw, n, 6, pbw, kMaxDiagQubits, true, perm_min_width(QSIM_C64, 6), 7);
+        plan_greedy(bw, n, 6, pbw0, kMaxDiagQubits, true, perm_min_width(QSIM_C64, 6), 0);
+        int bw_prod = 0;
+        for (const PlanItem &it : pbw) bw_prod += it.prod_block;
+        const bool bw_ok = bw_prod == 0 && pbw.size() == pbw0.size();
+        printf("Grover 20 qubits, 3 iterations: %d items (%d full-width product, %d plain); brickwork: %zu items, "
+               "%d product (%zu without product passes)\n",
+               (int)plan.size(), prod, plain, pbw.size(), bw_prod, pbw0.size());
+        if (!grover_ok || !bw_ok) ++bad;
+    }
     return bad == 0 && items > 0 ? 0 : 1;
 }
 
