@@ -145,3 +145,31 @@ def test_grover_search_with_product_passes(qs):
     assert abs(a - want) <= 1e-5, (a, want)
     assert abs(abs(a) ** 2 - math.sin((2 * r + 1) * theta) ** 2) <= 1e-5
     assert abs(nrm - 1.0) <= 1e-6, nrm
+
+
+def test_product_and_block_passes_share_the_norm_chain(qs, oracle_mod):
+    """Product passes and tensor-core block passes alternate in one norm
+    chain: H / X layers between many-controlled Z gates, then a U3 + CNOT
+    brickwork segment (blocks), repeated; the state against the oracle and
+    the raw norm at 1."""
+    n = 18
+    ops = []
+    for rep in range(3):
+        ops += layered(n, tuple(range(n)), seed=100 + rep, layers=2)
+        bw = cg.random_u3_brickwork(n, 3, seed=200 + rep)
+        ops += bw
+        ops.append(cg.op("Z", (n - 1,), tuple(range(n - 1))))
+    psi = cg.random_state(n, seed=22)
+    ref = oracle_mod.OracleSim(n, psi=psi)
+    oracle_mod.run_ops(ref, ops)
+    with qs.Simulator(n, precision="c64", fusion="greedy", kmax=6) as sim:
+        sim.set_amplitudes(psi)
+        sim.set_profiling(True)
+        sim.run(ops)
+        got = sim.get_amplitudes()
+        kt = sim.kernel_times()
+        p1, nrm = sim.probs_all()
+    assert kt.get("product", {}).get("launches", 0) >= 3 and kt.get("block_tc6", {}).get("launches", 0) >= 3, kt
+    assert infidelity(ref.psi, got) <= TOL64_INFID
+    np.testing.assert_allclose(p1, ref.probs_all(), atol=1e-5)
+    assert abs(nrm - 1.0) <= 1e-5, nrm
