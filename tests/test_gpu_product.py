@@ -52,6 +52,7 @@ CASES = [
     (21, tuple(range(12, 21))),                      # only qubits above it: 8 + 1, runs of 16 and 2^11
     (21, (0, 1, 2) + tuple(range(12, 21))),          # low qubits folded into the last high pass
     (22, (1, 4, 6, 8, 10, 11, 13, 15, 16, 18, 19, 20, 21)),  # low pass and one high pass
+    (13, (0, 1, 2, 3, 4, 5, 12)),                    # one pass, the top qubit folded with the low ones, 2 tiles
 ]
 
 
