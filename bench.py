@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--vqe-config", default=None, metavar="THREADS,M",
                     help="vqe workload: fixed launch configuration instead of the autotuner's")
     ap.add_argument("--workload", default="random",
-                    choices=["random", "vqe", "planner", "qft", "grover", "fig6", "adder", "plain", "sharded"],
+                    choices=["random", "vqe", "planner", "qft", "grover", "fig7", "adder", "plain", "sharded"],
                     help="random: the headline line; vqe / planner: secondary measurements")
     return ap.parse_args()
 
@@ -769,7 +769,7 @@ def run_circuit(args):
       grover -- Grover search on 28 qubits: 20 iterations timed, the full
                 r = floor(pi/4 sqrt(2^n)) extrapolated; the marked amplitude
                 checked against (-1)^r sin((2r+1) theta) for the 20;
-      fig6   -- the paper's benchmark circuit on 30 qubits: H on all, the
+      fig7   -- the paper's benchmark circuit on 30 qubits: H on all, the
                 controlled-Rz chain, H on all; checked by its norm."""
     import math
 
@@ -1083,7 +1083,7 @@ def main():
         return run_plain(args)
     if args.workload == "sharded":
         return run_sharded(args)
-    if args.workload in ("qft", "grover", "fig6", "adder"):
+    if args.workload in ("qft", "grover", "fig7", "adder"):
         return run_circuit(args)
     return run_ours(args)
 
