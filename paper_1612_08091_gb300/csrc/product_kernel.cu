@@ -23,8 +23,8 @@
 //
 // A tile is 32 KB of shared memory, double-buffered: the next tile arrives
 // by 16-byte cp.async copies (two amplitudes, bypassing L1) while this one
-// is processed (64 KB per CTA, three CTAs per SM).  256 threads hold 16 amplitudes each in three layouts
-// (tile index e, bits 0..11):
+// is processed (64 KB per CTA, three CTAs per SM).  256 threads hold 16
+// amplitudes each in three layouts (tile index e, bits 0..11):
 //   A  e = i | tid << 4:                              registers = tile bits 0..3
 //   B  e = (tid & 15) | i << 4 | (tid >> 4) << 8:     registers = tile bits 4..7
 //   C  e = tid | i << 8:                              registers = tile bits 8..11
@@ -134,7 +134,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) k_product(const ProdArgs A) {
-    extern __shared__ __align__(16) float2 smd[];  // two tiles of 2^12 amplitudes, padded rows
+    extern __shared__ __align__(16) float2 smd[];  // two tiles of 2^12 amplitudes (positions swz(e))
     __shared__ float s_scale;
     __shared__ double s_red[kPThreads / 32][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
