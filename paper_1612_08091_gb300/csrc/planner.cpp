@@ -254,6 +254,7 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
             if ((qmask(q[i]) >> b) & 1ull) wire[b].push_back((int)i);
     std::vector<size_t> front(n, 0);  // position in wire[b] of the next gate
     std::vector<char> done(G, 0);
+    std::vector<int> diag_mark(G, 0);  // scratch of the diagonal-block look-ahead
     size_t remaining = G, next_seed = 0;
 
     auto is_ready = [&](int gi) {
@@ -338,14 +339,36 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
         }
         if (diag_k > 0 && q[seed].diag && popc(qmask(q[seed])) <= diag_k) {
             // a diagonal block: ready diagonal gates commute with each other,
-            // so absorb them (fewest new qubits first) up to diag_k qubits
+            // so absorb them (fewest new qubits first) up to diag_k qubits.
+            // Among gates adding the same number of qubits, take the one
+            // after which the block's qubits can absorb the most pending
+            // diagonal gates: those whose earlier gates on every wire are all
+            // diagonal gates on the block's qubits (a QFT's phase gates from
+            // one group of qubits onto the next: about 36 per 12-qubit block,
+            // where the earliest-first choice chains one control's gates onto
+            // 11 new qubits)
             std::vector<int> dm;
             uint64_t Sd = qmask(q[seed]);
             double frac = touched_fraction(q[seed]);
             take(seed);
             dm.push_back(seed);
+            auto absorbable = [&](uint64_t S) {
+                int c = 0;
+                std::vector<int> seen;
+                for (int b = 0; b < n; ++b) {
+                    if (!((S >> b) & 1ull)) continue;
+                    for (size_t k = front[b]; k < wire[b].size(); ++k) {
+                        const int gi = wire[b][k];
+                        if (!q[gi].diag || (qmask(q[gi]) & ~S)) break;
+                        if (++diag_mark[gi] == popc(qmask(q[gi]))) ++c;
+                        seen.push_back(gi);
+                    }
+                }
+                for (int gi : seen) diag_mark[gi] = 0;
+                return c;
+            };
             for (;;) {
-                int best = -1, best_add = 1 << 30;
+                int best = -1, best_add = 1 << 30, best_gain = -1;
                 for (int b = 0; b < n; ++b) {
                     if (front[b] >= wire[b].size()) continue;
                     const int gi = wire[b][front[b]];
@@ -353,9 +376,12 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
                     const uint64_t m = qmask(q[gi]);
                     const int add = popc(m & ~Sd);
                     if (popc(Sd | m) > diag_k || !is_ready(gi)) continue;
-                    if (add < best_add || (add == best_add && gi < best)) {
+                    if (add > best_add) continue;
+                    const int gain = add > 0 ? absorbable(Sd | m) : 0;
+                    if (add < best_add || gain > best_gain || (gain == best_gain && gi < best)) {
                         best = gi;
                         best_add = add;
+                        best_gain = gain;
                     }
                 }
                 if (best < 0) break;

@@ -21,6 +21,8 @@
 //     wires continues with a gate wider than kmax (or ends), its matrix of
 //     each wire is the ordered product of that wire's member gates and is
 //     c times a +-1 matrix with orthogonal rows (M M^T = 2 c^2 I).
+//  5. the 30-qubit QFT: the phase gates between two groups of 6 qubits go
+//     into one 12-qubit diagonal block (36 gates), 20 items in all.
 #include <algorithm>
 #include <cstdio>
 #include <random>
@@ -523,6 +525,37 @@ int check_product_plans() {
     return bad == 0 && items > 0 ? 0 : 1;
 }
 
+int check_qft_plan() {
+    const int n = 30;
+    std::vector<GateRec> q;
+    for (int j = n - 1; j >= 0; --j) {
+        q.push_back(h_gate(j));
+        for (int k = j - 1; k >= 0; --k) {
+            GateRec g;
+            g.t = 1;
+            g.targets[0] = j;
+            g.tmask = 1ull << j;
+            g.controls.push_back(k);
+            g.cmask = 1ull << k;
+            g.m = {1.0, 0.0, 0.0, std::polar(1.0, M_PI / (double)(1ull << (j - k)))};
+            g.kind = GK_PHASE;
+            g.diag = true;
+            g.perm = perm_map(g, g.pmap);
+            q.push_back(g);
+        }
+    }
+    for (int i = 0; i < n / 2; ++i) q.push_back(swap_gate(std::vector<int>{i, n - 1 - i}));
+    std::vector<PlanItem> plan;
+    plan_greedy(q, n, 6, plan, kMaxDiagQubits, true, perm_min_width(QSIM_C64, 6), 7);
+    int full = 0, seen = 0;
+    for (const PlanItem &it : plan) {
+        if (it.diag_block && it.members.size() == 36) ++full;
+        seen += (int)it.members.size();
+    }
+    printf("QFT 30 qubits: %zu items, %d diagonal blocks of 36 phase gates\n", plan.size(), full);
+    return plan.size() == 20 && full == 10 && seen == (int)q.size() ? 0 : 1;
+}
+
 }  // namespace
 
 int main() {
@@ -530,5 +563,6 @@ int main() {
     const int b = check_plans();
     const int c = check_perm_plans();
     const int d = check_product_plans();
-    return a | b | c | d;
+    const int e = check_qft_plan();
+    return a | b | c | d | e;
 }
