@@ -14,8 +14,11 @@
 // grows by the ready gate that adds the fewest new qubits while it still
 // fits in kmax, and repeats until nothing more fits.  The block's matrix is
 // the ordered product of its gates, each embedded in the block's qubits, in
-// FP64.  Gates on more than kmax qubits (e.g. a many-controlled Z) run alone
-// with their specialised plain kernel.  Between such gates, a layer of
+// FP64.  Runs of diagonal gates become diagonal blocks of up to 12 qubits
+// (grown with a look-ahead: see the diagonal branch) and runs of
+// permutation gates permutation blocks.  Gates on more than kmax qubits
+// (e.g. a many-controlled Z) run alone with their specialised plain
+// kernel.  Between such gates, a layer of
 // one-qubit gates on more than kmax qubits (Grover's H and X layers, paper
 // Appendix A) has nothing to fuse with: it becomes a product item, the 2x2
 // product of each wire's gates, executed 12 qubits per pass.
