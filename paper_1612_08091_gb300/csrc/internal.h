@@ -167,6 +167,8 @@ int launch_permutation(qsim *s, const uint64_t *perm, const int *qubits, int m, 
 // holds each qubit's 2x2 matrix, ascending, row-major; one pass per 12
 // qubits (product_kernel.cu).
 int launch_product(qsim *s, uint64_t qmask, const cd *mats, int *npasses);
+// The passes launch_product makes for the qubits of qmask.
+int product_pass_count(uint64_t qmask);
 // u = c [[s00, s01], [s10, s11]] with c > 0, real signs s = +-1 and s00 s11
 // = -s01 s10 (products of H and X), to 1e-12 relative: the matrices a
 // product pass takes (planner.cpp)
@@ -207,13 +209,17 @@ void plan_none(const std::vector<GateRec> &q, int n, std::vector<PlanItem> &out)
 // uncontrolled one-qubit gates on at least prod_min qubits, each of whose
 // wires continues with a gate on more than kmax qubits (or ends) and has a
 // butterfly2 matrix (wires whose product is the identity drop out), becomes
-// one product item (only with matrices)
+// one product item; tie: how the dense grower chooses among ready gates
+// adding the same number of new qubits (0: the earliest; 1: the one sharing
+// the most qubits with the block, then the earliest)
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out,
-                 int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0, int prod_min = 0);
+                 int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0, int prod_min = 0,
+                 int tie = 0);
 // The same plan handed to emit item by item as it is formed (so execution
 // overlaps planning); a non-zero return of emit stops planning and is returned.
 int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
-                     int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0, int prod_min = 0);
+                     int diag_k = kMaxDiagQubits, bool matrices = true, int perm_min = 0, int prod_min = 0,
+                     int tie = 0);
 // The narrowest permutation block the executor runs as its own pass:
 // complex128 dense blocks are bound by arithmetic, so any permutation block
 // of two or more gates is cheaper; complex64 dense blocks are HBM-bound like

@@ -247,7 +247,7 @@ bool perm_map(const GateRec &g, std::vector<uint8_t> &pmap) {
 }
 
 int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::function<int(PlanItem &)> &emit,
-                     int diag_k, bool matrices, int perm_min, int prod_min) {
+                     int diag_k, bool matrices, int perm_min, int prod_min, int tie) {
     const size_t G = q.size();
     if (G == 0) return 0;
     // per-wire gate lists in program order
@@ -414,7 +414,7 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
             for (auto r = dm.rbegin(); r != dm.rend(); ++r) untake(*r);
         }
         auto one_qubit = [&](int gi) { return q[gi].t == 1 && q[gi].controls.empty(); };
-        if (prod_min > 0 && matrices && one_qubit(seed)) {
+        if (prod_min > 0 && one_qubit(seed)) {
             // a product item: every ready uncontrolled one-qubit gate, wire
             // by wire in program order, on the wires whose next gate is
             // wider than kmax (or that end); worth it on prod_min wires
@@ -506,10 +506,15 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
                     }
                 }
             }
-            // 2) grow by the ready gate adding the fewest new qubits (the
-            // earliest among those: the diagonal blocks' look-ahead measured
-            // 73 against 69 passes on the 32-qubit depth-40 brickwork here)
-            int best = -1, best_new = 1 << 30;
+            // 2) grow by the ready gate adding the fewest new qubits; among
+            // those the earliest (tie 0), or the one sharing the most qubits
+            // with the block (tie 1: a chain gate across the block's edge
+            // before a one-qubit gate on a new wire).  Neither is better
+            // everywhere: the 32-qubit depth-40 brickwork takes 69 passes
+            // with tie 0 and 83 with tie 1, the circuit of the paper's Fig. 7
+            // 12 and 6 (the diagonal blocks' look-ahead applied here: 73 for
+            // the brickwork)
+            int best = -1, best_new = 1 << 30, best_ov = -1;
             for (int b = 0; b < n; ++b) {
                 if (front[b] >= wire[b].size()) continue;
                 const int gi = wire[b][front[b]];
@@ -517,9 +522,11 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
                 const int add = popc(m & ~S);
                 if (add == 0 || popc(S | m) > kmax) continue;
                 if (!is_ready(gi)) continue;
-                if (add < best_new || (add == best_new && gi < best)) {
+                const int ov = tie == 1 ? popc(m & S) : 0;
+                if (add < best_new || (add == best_new && (ov > best_ov || (ov == best_ov && gi < best)))) {
                     best = gi;
                     best_new = add;
+                    best_ov = ov;
                 }
             }
             if (best < 0) {
@@ -550,7 +557,7 @@ int plan_greedy_each(const std::vector<GateRec> &q, int n, int kmax, const std::
 }
 
 void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<PlanItem> &out, int diag_k,
-                 bool matrices, int perm_min, int prod_min) {
+                 bool matrices, int perm_min, int prod_min, int tie) {
     out.clear();
     plan_greedy_each(
         q, n, kmax,
@@ -558,7 +565,7 @@ void plan_greedy(const std::vector<GateRec> &q, int n, int kmax, std::vector<Pla
             out.push_back(std::move(it));
             return 0;
         },
-        diag_k, matrices, perm_min, prod_min);
+        diag_k, matrices, perm_min, prod_min, tie);
 }
 
 // ---------------------------------------------------------------------------

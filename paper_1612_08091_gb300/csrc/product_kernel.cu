@@ -321,6 +321,17 @@ int launch_pass(qsim *s, const int *qubits, const cd *const *mats, int m) {
 
 }  // namespace
 
+int product_pass_count(uint64_t qmask) {
+    const uint64_t low = qmask & ((1ull << kPBits) - 1ull);
+    const int nlo = __builtin_popcountll(low), nhi = __builtin_popcountll(qmask >> kPBits);
+    const int per = kPBits - kPMinRun;
+    const int npass_hi = (nhi + per - 1) / per;
+    const int last = nhi - (npass_hi - 1) * per;
+    const int top_lo = low ? 63 - __builtin_clzll(low) : -1;
+    const bool fold = npass_hi > 0 && (nlo == 0 || top_lo < kPBits - last);
+    return npass_hi + ((nlo > 0 && !fold) ? 1 : 0);
+}
+
 int launch_product(qsim *s, uint64_t qmask, const cd *mats, int *npasses) {
     *npasses = 0;
     if (s->prec != QSIM_C64 || s->n < kPBits) return QSIM_ENOTSUP;

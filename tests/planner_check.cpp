@@ -167,13 +167,18 @@ int check_plans() {
             std::vector<int> pool(all.begin(), all.begin() + width);
             q.push_back(random_gate(pool, (int)(rng() % 3)));
         }
+        // both dense tie rules (0: earliest; 1: most shared qubits)
+        const int tie = trial % 2;
         std::vector<PlanItem> plan;
-        plan_greedy(q, n, kmax, plan);
+        plan_greedy(q, n, kmax, plan, kMaxDiagQubits, true, 0, 0, tie);
         std::vector<PlanItem> streamed;
-        plan_greedy_each(q, n, kmax, [&](PlanItem &it) {
-            streamed.push_back(it);
-            return 0;
-        });
+        plan_greedy_each(
+            q, n, kmax,
+            [&](PlanItem &it) {
+                streamed.push_back(it);
+                return 0;
+            },
+            kMaxDiagQubits, true, 0, 0, tie);
         // executed order: items in order, members in order
         std::vector<int> order, seen(G, 0);
         for (size_t i = 0; i < plan.size(); ++i) {
@@ -553,7 +558,31 @@ int check_qft_plan() {
         seen += (int)it.members.size();
     }
     printf("QFT 30 qubits: %zu items, %d diagonal blocks of 36 phase gates\n", plan.size(), full);
-    return plan.size() == 20 && full == 10 && seen == (int)q.size() ? 0 : 1;
+    const bool qft_ok = plan.size() == 20 && full == 10 && seen == (int)q.size();
+    // the circuit of the paper's Fig. 7: H on all, a controlled-Rz chain, H
+    // on all; tie rule 0 leaves the chain gates across block edges behind
+    std::vector<GateRec> f;
+    for (int b = 0; b < n; ++b) f.push_back(h_gate(b));
+    for (int i = 0; i + 1 < n; ++i) {
+        GateRec g;
+        g.t = 1;
+        g.targets[0] = i + 1;
+        g.tmask = 1ull << (i + 1);
+        g.controls.push_back(i);
+        g.cmask = 1ull << i;
+        const double phi = 0.1 * (i + 1);
+        g.m = {std::polar(1.0, -phi / 2), 0.0, 0.0, std::polar(1.0, phi / 2)};
+        g.kind = GK_DIAG1;
+        g.diag = true;
+        g.perm = perm_map(g, g.pmap);
+        f.push_back(g);
+    }
+    for (int b = 0; b < n; ++b) f.push_back(h_gate(b));
+    std::vector<PlanItem> f0, f1;
+    plan_greedy(f, n, 6, f0, kMaxDiagQubits, true, perm_min_width(QSIM_C64, 6), 7, 0);
+    plan_greedy(f, n, 6, f1, kMaxDiagQubits, true, perm_min_width(QSIM_C64, 6), 7, 1);
+    printf("Fig. 7 circuit, 30 qubits: %zu items with tie rule 0, %zu with tie rule 1\n", f0.size(), f1.size());
+    return qft_ok && f1.size() == 6 && f0.size() > f1.size() ? 0 : 1;
 }
 
 }  // namespace

@@ -79,6 +79,28 @@ def test_random32_depth40_roundtrip_fused(qs):
     _free()
 
 
+def test_fig7_circuit_roundtrip_30(qs):
+    """The paper's benchmark circuit (Fig. 7: H on all, a controlled-Rz
+    chain, H on all) on 30 qubits, then its inverse, each flushed as one
+    short queue: the planner tries both dense tie rules there and launches
+    the one with fewer items (6 passes each way); U U^dag returns |0...0>."""
+    n = 30
+    ops = cg.hadamard_crz_chain(n, 1612)
+    with qs.Simulator(n, precision="c64", fusion="greedy") as sim:
+        sim.reset_stats()
+        sim.run(ops)
+        sim.flush()
+        forward = sim.stats()["passes"]
+        sim.run(cg.inverse_ops(ops))
+        a0 = sim.get_amplitudes(0, 1)[0]
+        p1, nrm = sim.probs_all()
+    assert forward == 6, forward
+    assert 1.0 - abs(a0) ** 2 / nrm <= 2 * TOL64_INFID, 1.0 - abs(a0) ** 2 / nrm
+    assert np.max(p1) <= 2 * TOL64_INFID
+    assert abs(nrm - 1.0) <= 1e-5
+    _free()
+
+
 @pytest.mark.parametrize("df", [False, True])
 def test_random32_roundtrip_plain_c128(qs, df):
     """U U^dag on 32 qubits, complex128, one launch per gate, in FP64 and in
